@@ -1,0 +1,378 @@
+"""Seeded synthetic tight-binding systems: the inputs of a DC-LNO step.
+
+The paper's workloads are DFT solids described by pseudo-atomic orbitals (PAOs)
+and GGA Hamiltonians (Sec. III).  Neither the PAO database nor a DFT code is
+available here, so the systems below stand in for them: every atom carries
+normalised s-type Gaussians, the overlap S is the analytic Gaussian overlap
+and H follows the Wolfsberg-Helmholz rule.  The matrices are stored in the
+paper's atom-pair block form S_{0i,Rj}, H_{0i,Rj} (the M_i x M_j blocks of
+Sec. II.B, between atom i in the central cell and atom j in cell R), as a
+block-sparse-row (BSR) structure keyed by (i, j, R).
+
+This module holds no DC-LNO arithmetic.  It serves both the CUDA path and the
+oracle: geometry, basis, the analytic S and H, and a seeded synthetic density
+matrix used as the input of a single LNO step in tests.
+
+Conventions
+-----------
+* Units: bohr and hartree.
+* ``cell`` rows are the lattice vectors; ``pbc[d]`` says whether direction d
+  is periodic.  A shift R is an integer triple; the image of atom j in cell R
+  sits at ``pos[j] + R @ cell``.
+* BSR: row i holds blocks ``b`` in ``row_ptr[i]:row_ptr[i+1]``, sorted by
+  ``(col[b], shift[b][0], shift[b][1], shift[b][2])``.  Block b is the
+  M_i x M_col row-major matrix starting at element ``blk_off[b]`` of ``S`` and
+  ``H``.
+* Entries of S below ``drop_tol`` (1e-10) are dropped (set to zero, and blocks
+  that become all-zero are removed); H is zero wherever S is.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+DROP_TOL = 1e-10
+WH_K = 1.75  # Wolfsberg-Helmholz constant
+
+
+@dataclasses.dataclass
+class System:
+    name: str
+    pos: np.ndarray          # (N, 3) float64, bohr
+    cell: np.ndarray         # (3, 3) float64, rows = lattice vectors
+    pbc: np.ndarray          # (3,) bool
+    species: np.ndarray      # (N,) int32
+    exps: list               # per atom: (M_i,) Gaussian exponents
+    onsite: list             # per atom: (M_i,) on-site energies, hartree
+    norb: np.ndarray         # (N,) int32, M_i
+    row_ptr: np.ndarray      # (N+1,) int64
+    col: np.ndarray          # (nnzb,) int32
+    shift: np.ndarray        # (nnzb, 3) int8
+    blk_off: np.ndarray      # (nnzb,) int64, element offset of each block
+    S: np.ndarray            # (nval,) float64
+    H: np.ndarray            # (nval,) float64
+    n_electrons: float
+    kT: float
+    r_core: float
+    r_lno: float
+    k_lno: int
+
+    @property
+    def natoms(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.col.shape[0])
+
+    def block(self, arr: np.ndarray, b: int) -> np.ndarray:
+        """Block b of the flat value array ``arr`` as an M_i x M_j view."""
+        i = int(np.searchsorted(self.row_ptr, b, side="right") - 1)
+        mi, mj = int(self.norb[i]), int(self.norb[self.col[b]])
+        o = int(self.blk_off[b])
+        return arr[o:o + mi * mj].reshape(mi, mj)
+
+    def block_rows(self) -> np.ndarray:
+        """Row (atom i) of every block, (nnzb,) int64."""
+        return np.repeat(np.arange(self.natoms), np.diff(self.row_ptr))
+
+
+# --------------------------------------------------------------------------
+# Basis and pair matrices
+# --------------------------------------------------------------------------
+
+def gaussian_overlap(a: np.ndarray, b: np.ndarray, r2: np.ndarray) -> np.ndarray:
+    """Overlap of normalised s-Gaussians (2a/pi)^(3/4) exp(-a r^2).
+
+    S_ab(R) = (2 sqrt(ab)/(a+b))^(3/2) exp(-ab R^2/(a+b)); shapes broadcast.
+    """
+    p = a + b
+    return (2.0 * np.sqrt(a * b) / p) ** 1.5 * np.exp(-(a * b / p) * r2)
+
+
+def overlap_cutoff(min_exp: float, tol: float = DROP_TOL) -> float:
+    """Distance beyond which every overlap entry is below ``tol``.
+
+    The slowest-decaying pair is the most diffuse exponent with itself,
+    exp(-a R^2 / 2), whose prefactor is 1.
+    """
+    return math.sqrt(2.0 * math.log(1.0 / tol) / min_exp)
+
+
+def _image_shifts(cell: np.ndarray, pbc: np.ndarray, rcut: float) -> np.ndarray:
+    vol = abs(np.linalg.det(cell)) if np.all(pbc) else None
+    nmax = []
+    for d in range(3):
+        if not pbc[d]:
+            nmax.append(0)
+            continue
+        e, f = [x for x in range(3) if x != d]
+        area = np.linalg.norm(np.cross(cell[e], cell[f]))
+        height = abs(np.dot(cell[d], np.cross(cell[e], cell[f]))) / area
+        nmax.append(int(math.ceil(rcut / height)))
+    del vol
+    rng = [np.arange(-n, n + 1) for n in nmax]
+    g = np.stack(np.meshgrid(*rng, indexing="ij"), axis=-1).reshape(-1, 3)
+    return g.astype(np.int64)
+
+
+def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
+    """Block-sparse S and H over all (i, j, R) pairs with a kept overlap entry."""
+    from scipy.spatial import cKDTree
+
+    n = pos.shape[0]
+    norb = np.array([len(e) for e in exps], dtype=np.int32)
+    min_exp = min(float(np.min(e)) for e in exps)
+    rcut = overlap_cutoff(min_exp, drop_tol)
+    shifts = _image_shifts(cell, pbc, rcut)
+    imgpos = (pos[None, :, :] + (shifts @ cell)[:, None, :]).reshape(-1, 3)
+    tree = cKDTree(imgpos)
+    uniform = bool(np.all(norb == norb[0]))
+
+    rows_col, rows_shift, rows_S, rows_H, rows_n = [], [], [], [], []
+    for i0 in range(0, n, 256):
+        i1 = min(n, i0 + 256)
+        lists = tree.query_ball_point(pos[i0:i1], rcut * (1 + 1e-12) + 1e-9)
+        for ii, lst in enumerate(lists):
+            i = i0 + ii
+            idx = np.asarray(sorted(lst), dtype=np.int64)
+            j = idx % n
+            sh = shifts[idx // n]
+            d = imgpos[idx] - pos[i]
+            r2 = np.einsum("kd,kd->k", d, d)
+            if uniform:
+                a = exps[i][None, :, None]
+                b = np.stack([exps[jj] for jj in j])[:, None, :]
+                sblk = gaussian_overlap(a, b, r2[:, None, None])
+                sblk[sblk < drop_tol] = 0.0
+                ea = onsite[i][None, :, None]
+                eb = np.stack([onsite[jj] for jj in j])[:, None, :]
+                hblk = WH_K * sblk * 0.5 * (ea + eb)
+                self_mask = (j == i) & np.all(sh == 0, axis=1)
+                for k in np.nonzero(self_mask)[0]:
+                    np.fill_diagonal(hblk[k], onsite[i])
+                keep = np.any(sblk != 0.0, axis=(1, 2))
+                order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], j))
+                order = order[keep[order]]
+                rows_col.append(j[order].astype(np.int32))
+                rows_shift.append(sh[order].astype(np.int8))
+                rows_S.append(sblk[order].reshape(-1))
+                rows_H.append(hblk[order].reshape(-1))
+                rows_n.append(len(order))
+            else:  # ragged basis: per-block loop
+                blocks = []
+                for k in range(len(idx)):
+                    jj = int(j[k])
+                    a = exps[i][:, None]
+                    b = exps[jj][None, :]
+                    sb = gaussian_overlap(a, b, r2[k])
+                    sb[sb < drop_tol] = 0.0
+                    if not np.any(sb != 0.0):
+                        continue
+                    hb = WH_K * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
+                    if jj == i and not np.any(sh[k]):
+                        np.fill_diagonal(hb, onsite[i])
+                    blocks.append((jj, tuple(int(x) for x in sh[k]), sb, hb))
+                blocks.sort(key=lambda t: (t[0],) + t[1])
+                rows_col.append(np.array([t[0] for t in blocks], dtype=np.int32))
+                rows_shift.append(np.array([t[1] for t in blocks], dtype=np.int8).reshape(-1, 3))
+                rows_S.append(np.concatenate([t[2].reshape(-1) for t in blocks]))
+                rows_H.append(np.concatenate([t[3].reshape(-1) for t in blocks]))
+                rows_n.append(len(blocks))
+
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(rows_n)
+    col = np.concatenate(rows_col)
+    shift = np.concatenate(rows_shift).reshape(-1, 3)
+    brow = np.repeat(np.arange(n), rows_n)
+    sizes = norb[brow].astype(np.int64) * norb[col].astype(np.int64)
+    blk_off = np.zeros(len(col), dtype=np.int64)
+    blk_off[1:] = np.cumsum(sizes)[:-1]
+    S = np.concatenate(rows_S)
+    H = np.concatenate(rows_H)
+    return norb, row_ptr, col, shift, blk_off, S, H
+
+
+# --------------------------------------------------------------------------
+# Geometries of the five workloads
+# --------------------------------------------------------------------------
+
+def _sc_lattice(nx, ny, nz, a):
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), -1)
+    return g.reshape(-1, 3).astype(np.float64) * a, g.reshape(-1, 3)
+
+
+def make_system(cfg: int, seed: int | None = None, **over) -> System:
+    """One of the five workloads; keyword overrides replace r_core, r_lno, k_lno.
+
+    1  64-atom simple-cubic 4x4x4, a=2.5, open, 4 s-Gaussians, 2 e/atom.
+    2  1,728-atom rock-salt arrangement on SC 12^3, a=3.0, periodic, jitter 0.05,
+       9 s-Gaussians, 4.5 e/atom (the gapped FP64 workload).
+    3  the same system as 2 (it differs only in the arithmetic precision).
+    4  bcc slab 20x20x10 conventional cells, a=5.4, periodic in x and y,
+       2% seeded vacancies, 9 s-Gaussians, 1 e/atom (metallic, uneven).
+    5  32,000-atom random sequential packing in a periodic cube, two species.
+    """
+    if cfg == 1:
+        pos, _ = _sc_lattice(4, 4, 4, 2.5)
+        n = len(pos)
+        e = np.array([0.2, 0.5, 1.2, 3.0])
+        h = np.array([-0.5, -0.3, 0.1, 0.4])
+        sys = dict(name="cfg1_sc64", pos=pos, cell=np.eye(3) * 10.0,
+                   pbc=np.zeros(3, bool), species=np.zeros(n, np.int32),
+                   exps=[e.copy() for _ in range(n)], onsite=[h.copy() for _ in range(n)],
+                   n_electrons=2.0 * n, kT=0.01, r_core=5.0, r_lno=8.0, k_lno=2)
+    elif cfg in (2, 3):
+        rng = np.random.default_rng(1001 if seed is None else seed)
+        pos, ijk = _sc_lattice(12, 12, 12, 3.0)
+        pos = pos + rng.normal(0.0, 0.05, size=pos.shape)
+        n = len(pos)
+        species = (ijk.sum(1) % 2).astype(np.int32)  # 0 = A (even x+y+z), 1 = B
+        e = np.geomspace(0.1, 5.0, 9)
+        base = np.linspace(-0.6, 0.5, 9)
+        onsite = [base + (-0.3 if s == 0 else 0.3) for s in species]
+        sys = dict(name="cfg2_rocksalt1728", pos=pos, cell=np.eye(3) * 36.0,
+                   pbc=np.ones(3, bool), species=species,
+                   exps=[e.copy() for _ in range(n)], onsite=onsite,
+                   n_electrons=4.5 * n, kT=0.01, r_core=6.0, r_lno=10.0, k_lno=3)
+    elif cfg == 4:
+        rng = np.random.default_rng(1004 if seed is None else seed)
+        a = 5.4
+        g, _ = _sc_lattice(20, 20, 10, a)
+        pos = np.concatenate([g, g + 0.5 * a]).astype(np.float64)
+        order = np.lexsort((pos[:, 2], pos[:, 1], pos[:, 0]))
+        pos = pos[order]
+        vac = rng.choice(len(pos), size=int(round(0.02 * len(pos))), replace=False)
+        pos = np.delete(pos, np.sort(vac), axis=0)
+        n = len(pos)
+        e = np.geomspace(0.1, 5.0, 9)
+        h = np.linspace(-0.4, 0.6, 9)
+        cell = np.diag([20 * a, 20 * a, 10 * a + 60.0])
+        sys = dict(name="cfg4_bccslab", pos=pos, cell=cell,
+                   pbc=np.array([True, True, False]), species=np.zeros(n, np.int32),
+                   exps=[e.copy() for _ in range(n)], onsite=[h.copy() for _ in range(n)],
+                   n_electrons=1.0 * n, kT=0.005, r_core=6.0, r_lno=11.0, k_lno=3)
+    elif cfg == 5:
+        rng = np.random.default_rng(1005 if seed is None else seed)
+        n = 32000
+        L = (n / 0.012) ** (1.0 / 3.0)
+        pos = _rsa(n, L, 3.8, rng)
+        species = np.zeros(n, np.int32)
+        species[rng.permutation(n)[: n // 2]] = 1
+        e = np.geomspace(0.08, 6.0, 13)
+        base = np.linspace(-0.6, 0.5, 13)
+        onsite = [base + (-0.15 if s == 0 else 0.15) for s in species]
+        sys = dict(name="cfg5_rsa32000", pos=pos, cell=np.eye(3) * L,
+                   pbc=np.ones(3, bool), species=species,
+                   exps=[e.copy() for _ in range(n)], onsite=onsite,
+                   n_electrons=5.0 * n, kT=0.01, r_core=6.0, r_lno=10.0, k_lno=4)
+    else:
+        raise ValueError(f"unknown workload {cfg}")
+    sys.update(over)
+    return assemble_system(**sys)
+
+
+def assemble_system(name, pos, cell, pbc, species, exps, onsite, n_electrons, kT,
+                    r_core, r_lno, k_lno) -> System:
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cell = np.asarray(cell, dtype=np.float64)
+    pbc = np.asarray(pbc, dtype=bool)
+    exps = [np.asarray(e, dtype=np.float64) for e in exps]
+    onsite = [np.asarray(h, dtype=np.float64) for h in onsite]
+    norb, row_ptr, col, shift, blk_off, S, H = build_bsr(pos, cell, pbc, exps, onsite)
+    return System(name=name, pos=pos, cell=cell, pbc=pbc,
+                  species=np.asarray(species, np.int32), exps=exps, onsite=onsite,
+                  norb=norb, row_ptr=row_ptr, col=col, shift=shift, blk_off=blk_off,
+                  S=S, H=H, n_electrons=float(n_electrons), kT=float(kT),
+                  r_core=float(r_core), r_lno=float(r_lno), k_lno=int(k_lno))
+
+
+def _rsa(n, L, dmin, rng):
+    """Random sequential addition in a periodic cube with a minimum distance."""
+    nc = max(1, int(L // dmin))
+    cw = L / nc
+    grid: dict = {}
+    pts = np.empty((n, 3))
+    k = 0
+    tries = 0
+    while k < n:
+        tries += 1
+        if tries > 200 * n:
+            raise RuntimeError("random sequential addition jammed")
+        p = rng.uniform(0.0, L, size=3)
+        c = (p // cw).astype(int) % nc
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    key = ((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc)
+                    for q in grid.get(key, ()):
+                        d = pts[q] - p
+                        d -= L * np.round(d / L)
+                        if d @ d < dmin * dmin:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            pts[k] = p
+            grid.setdefault(tuple(c), []).append(k)
+            k += 1
+    return pts
+
+
+def small_lattice(nx, ny, nz, a=2.5, jitter=0.0, seed=7, exps=(0.2, 0.5, 1.2, 3.0),
+                  onsite=(-0.5, -0.3, 0.1, 0.4), e_per_atom=2.0, kT=0.01,
+                  r_core=5.0, r_lno=8.0, k_lno=2, periodic=False, name=None) -> System:
+    """A small open (or periodic) simple-cubic lattice for tests."""
+    pos, _ = _sc_lattice(nx, ny, nz, a)
+    if jitter:
+        pos = pos + np.random.default_rng(seed).normal(0.0, jitter, size=pos.shape)
+    n = len(pos)
+    if periodic:
+        cell, pbc = np.diag([nx * a, ny * a, nz * a]), np.ones(3, bool)
+    else:
+        cell, pbc = np.eye(3) * (max(nx, ny, nz) * a + 10.0), np.zeros(3, bool)
+    return assemble_system(name or f"sc{nx}x{ny}x{nz}", pos, cell, pbc, np.zeros(n, np.int32),
+                           [np.array(exps, float)] * n, [np.array(onsite, float)] * n,
+                           e_per_atom * n, kT, r_core, r_lno, k_lno)
+
+
+def synthetic_density(system: System, seed: int = 11, width: float = 3.0) -> np.ndarray:
+    """A seeded, symmetric density-like matrix in the BSR pattern of S.
+
+    It stands in for the density matrix of the previous SCF step when a test
+    runs one LNO step on a system too large for the oracle to converge.  The
+    on-site block is diag(p) with slowly decreasing populations p (a fixed
+    random permutation-free profile scaled by a seeded factor per atom); the
+    off-site blocks are a seeded symmetric amplitude times exp(-d^2/width^2)
+    times w_alpha w_beta.  Symmetry rho_{0i,Rj} = rho_{0j,-Ri}^T holds by
+    construction.  Only the pattern and the geometry are read from ``system``.
+    """
+    rng = np.random.default_rng(seed)
+    n = system.natoms
+    scale = rng.uniform(0.9, 1.1, size=n)
+    rho = np.zeros_like(system.S)
+    brow = system.block_rows()
+    for b in range(system.nnzb):
+        i, j = int(brow[b]), int(system.col[b])
+        sh = system.shift[b].astype(np.float64)
+        d = system.pos[j] + sh @ system.cell - system.pos[i]
+        r2 = float(d @ d)
+        mi, mj = int(system.norb[i]), int(system.norb[j])
+        o = int(system.blk_off[b])
+        if i == j and not np.any(system.shift[b]):
+            p = 0.9 * np.exp(-0.6 * np.arange(mi))
+            rho[o:o + mi * mj] = np.diag(p * scale[i]).reshape(-1)
+        else:
+            wi = np.exp(-0.4 * np.arange(mi))
+            wj = np.exp(-0.4 * np.arange(mj))
+            amp = 0.05 * math.exp(-r2 / (width * width)) * math.sqrt(scale[i] * scale[j])
+            rho[o:o + mi * mj] = (amp * np.outer(wi, wj)).reshape(-1)
+    return rho

@@ -1,0 +1,184 @@
+"""Pins of the DC-LNO oracle against what the method and the mathematics fix.
+
+* full-cover exactness: a cluster that holds the whole open system reproduces
+  conventional diagonalisation (the DC method is exact in that limit);
+* all-LNO identity: keeping every eigenvector of Lambda makes Eq. (apop_Lambda)
+  exact, so DC-LNO equals plain-PAO DC on the same radius;
+* invariants: sum_mu q_mu = M_i, 2 Tr(rho S) = N(mu), E_band = 2 sum tr(rho H),
+  sum_i tr Lambda_i = N_ele / 2 (Eq. (tr_i));
+* Lambda against the dense product (rho S)_ii; eigenvalue range of Table I;
+* the worked dimension / cost-model numbers of Sec. IV.C and Fig. 7.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def eps_tol(e):
+    """Eigenvalue tolerance: 1e-10 Ha, relative 1e-12 for the large spurious states."""
+    return 1e-10 + 1e-12 * np.abs(e)
+
+
+def test_full_diag_brute_force(cfg1, cfg1_exact):
+    eps = cfg1_exact[0]
+    H, S, _ = O.dense_matrices(cfg1)
+    ref = sl.eigh(H, S, eigvals_only=True)
+    assert np.all(np.abs(eps - ref) <= eps_tol(ref))
+    assert abs(cfg1_exact[3] - cfg1.n_electrons) < 1e-9
+
+
+def test_full_cover_exactness(cfg1, cfg1_exact):
+    eps, C, mu, nmu, rho, e_band = cfg1_exact
+    res = O.dclno_solve(cfg1, {}, 13.5, 13.5, 0)
+    for r in res.values():
+        assert r.cluster.dim == len(eps)
+        assert np.all(np.abs(r.eps - eps) <= eps_tol(eps))
+    mu2, n2, rho2, e2 = O.finish_step(cfg1, res, {}, cfg1.n_electrons, cfg1.kT)
+    assert abs(mu2 - mu) < 1e-9
+    assert np.max(np.abs(rho2 - rho)) < 1e-9
+    assert abs(e2 - e_band) < 1e-9 * abs(e_band)
+
+
+def test_all_lno_identity(cfg1, cfg1_dc0):
+    rho0 = cfg1_dc0[2]
+    lno = O.compute_lnos(cfg1, rho0, 4)
+    V = {i: v[0] for i, v in lno.items()}
+    a = O.dclno_solve(cfg1, V, 5.0, 8.0, 4)
+    b = O.dclno_solve(cfg1, {}, 8.0, 8.0, 0)
+    for i in a:
+        assert a[i].cluster.dim == b[i].cluster.dim
+        assert np.all(np.abs(a[i].eps - b[i].eps) <= eps_tol(b[i].eps))
+        np.testing.assert_allclose(a[i].q, b[i].q, atol=1e-9)
+    mua, na, rhoa, ea = O.finish_step(cfg1, a, V, cfg1.n_electrons, cfg1.kT)
+    mub, nb, rhob, eb = O.finish_step(cfg1, b, {}, cfg1.n_electrons, cfg1.kT)
+    assert abs(mua - mub) < 1e-9
+    assert np.max(np.abs(rhoa - rhob)) < 1e-9
+    assert abs(ea - eb) < 1e-9 * abs(eb)
+
+
+@pytest.fixture(scope="module")
+def lno_step(cfg1, cfg1_dc0):
+    rho0 = cfg1_dc0[2]
+    lno = O.compute_lnos(cfg1, rho0, cfg1.k_lno)
+    V = {i: v[0] for i, v in lno.items()}
+    res = O.dclno_solve(cfg1, V, cfg1.r_core, cfg1.r_lno, cfg1.k_lno)
+    mu, n_mu, rho, e_band = O.finish_step(cfg1, res, V, cfg1.n_electrons, cfg1.kT)
+    return lno, V, res, mu, n_mu, rho, e_band
+
+
+def _pair_trace(s, rho, X):
+    brow = s.block_rows()
+    tot = 0.0
+    for b in range(s.nnzb):
+        i = int(brow[b])
+        mi, mj = int(s.norb[i]), int(s.norb[s.col[b]])
+        o = int(s.blk_off[b])
+        tot += float(np.sum(rho[o:o + mi * mj] * X[o:o + mi * mj]))
+    return tot
+
+
+def test_invariants(cfg1, lno_step):
+    lno, V, res, mu, n_mu, rho, e_band = lno_step
+    for i, r in res.items():
+        assert abs(r.q.sum() - cfg1.norb[i]) < 1e-10
+    assert abs(n_mu - cfg1.n_electrons) <= 1e-10 * cfg1.n_electrons
+    assert abs(2 * _pair_trace(cfg1, rho, cfg1.S) - n_mu) < 1e-9
+    assert abs(2 * _pair_trace(cfg1, rho, cfg1.H) - e_band) < 1e-9 * abs(e_band)
+    lam = O.lambda_blocks(cfg1, rho)
+    assert abs(sum(np.trace(x) for x in lam.values()) - n_mu / 2) < 1e-9
+
+
+def test_lno_quality(cfg1, cfg1_exact, cfg1_dc0, lno_step):
+    """Error per atom against exact diagonalisation: DC-LNO beats plain core-only DC."""
+    e_exact = cfg1_exact[5]
+    e_dc0 = cfg1_dc0[3]
+    e_lno = lno_step[6]
+    n = cfg1.natoms
+    assert abs(e_lno - e_exact) / n < abs(e_dc0 - e_exact) / n < 1e-2
+
+
+def test_lambda_matches_dense_product(mixed_system):
+    import tbsystems
+    s = mixed_system
+    rho = tbsystems.synthetic_density(s, seed=2)
+    H, S, off = O.dense_matrices(s)
+    R = np.zeros_like(S)
+    brow = s.block_rows()
+    for b in range(s.nnzb):
+        i, j = int(brow[b]), int(s.col[b])
+        R[off[i]:off[i + 1], off[j]:off[j + 1]] = s.block(rho, b)
+    P = R @ S
+    lam = O.lambda_blocks(s, rho)
+    for i in range(s.natoms):
+        np.testing.assert_allclose(lam[i], P[off[i]:off[i + 1], off[i]:off[i + 1]], atol=1e-14)
+
+
+def test_lno_eigen_properties(cfg1, lno_step):
+    lno = lno_step[0]
+    s_ii = {}
+    for i in range(cfg1.natoms):
+        b = next(b for b in range(cfg1.row_ptr[i], cfg1.row_ptr[i + 1])
+                 if cfg1.col[b] == i and not np.any(cfg1.shift[b]))
+        s_ii[i] = cfg1.block(cfg1.S, b)
+    lam_blocks = O.lambda_blocks(cfg1, O.plain_dc_density(cfg1, cfg1.r_core)[2])
+    for i, (V, ev, flags) in lno.items():
+        # Table I: populations are dominated by the leading few, all below ~1
+        assert ev.real.max() < 1.05 and ev.real.min() > -0.1
+        np.testing.assert_allclose(V.T @ s_ii[i] @ V, np.eye(V.shape[1]), atol=1e-12)
+        # the span is invariant under Lambda (exact for real selected eigenvalues)
+        L = lam_blocks[i]
+        P = V @ np.linalg.pinv(V)
+        assert np.linalg.norm(L @ V - P @ L @ V) < 1e-10
+        np.testing.assert_allclose(np.sort(ev.real)[::-1], ev.real)
+
+
+def test_lnos_complex_pair_rule():
+    """A selected complex pair contributes its real and imaginary parts; a split pair its real part."""
+    A = np.array([[0.9, 0.0, 0.0], [0.0, 0.5, 0.3], [0.0, -0.3, 0.5]])
+    s_ii = np.eye(3)
+    V, ev, flags = O.lnos(A, s_ii, 3)
+    assert flags & O.dclno_oracle.LNO_COMPLEX_SELECTED and not flags & O.dclno_oracle.LNO_PAIR_SPLIT
+    V2, ev2, flags2 = O.lnos(A, s_ii, 2)
+    assert flags2 & O.dclno_oracle.LNO_PAIR_SPLIT
+    assert abs(ev[0] - 0.9) < 1e-14 and abs(ev[1] - (0.5 + 0.3j)) < 1e-14
+
+
+def test_fermi_and_mu():
+    f = O.fermi(np.array([0.0, 1000.0, -1000.0, 3.0, -3.0]))
+    assert f[0] == 0.5 and f[1] == 0.0 and f[2] == 1.0
+    assert abs(f[3] + f[4] - 1.0) <= 2.3e-16
+    eps = np.array([-1.0, 0.2])
+    mu, n = O.find_mu(eps, np.ones(2), 2.0, 0.05)
+    assert abs(mu - (-0.4)) < 1e-12
+    with pytest.raises(O.NoBracket):
+        O.find_mu(eps, np.ones(2), 4.5, 0.05)
+
+
+def test_worked_dimensions():
+    with open(os.path.join(GOLD, "time_ratio.json")) as fh:
+        g = json.load(fh)
+    for c in g["cases"]:
+        assert O.cluster_dim(c["n_short"], c["n_long"], c["m_pao"], c["m_lno"]) == c["dim"]
+        if "ratio_2dp" in c:
+            r = O.time_ratio(c["m_pao"], c["m_lno"], c["n_short"], c["n_long"])
+            assert round(r, 2) == c["ratio_2dp"]
+
+
+def test_mixed_basis_step(mixed_system):
+    """Ragged basis (M = 3 and 4): the step runs and keeps its invariants."""
+    s = mixed_system
+    mu0, n0, rho0, e0, _ = O.plain_dc_density(s, s.r_core)
+    lno = O.compute_lnos(s, rho0, s.k_lno)
+    V = {i: v[0] for i, v in lno.items()}
+    res = O.dclno_solve(s, V, s.r_core, s.r_lno, s.k_lno)
+    mu, n_mu, rho, e_band = O.finish_step(s, res, V, s.n_electrons, s.kT)
+    assert abs(n_mu - s.n_electrons) < 1e-9
+    assert abs(2 * _pair_trace(s, rho, s.S) - n_mu) < 1e-9
+    assert abs(2 * _pair_trace(s, rho, s.H) - e_band) < 1e-9 * abs(e_band)

@@ -1,0 +1,91 @@
+"""Synthetic tight-binding inputs: symmetry, the drop rule and the analytic overlap."""
+import numpy as np
+import pytest
+
+import tbsystems as T
+
+
+def _mirror_index(s):
+    key = {}
+    brow = s.block_rows()
+    for b in range(s.nnzb):
+        key[(int(brow[b]), int(s.col[b])) + tuple(int(x) for x in s.shift[b])] = b
+    return key, brow
+
+
+@pytest.mark.parametrize("which", ["cfg1", "mixed_system"])
+def test_blocks_symmetric(which, request):
+    s = request.getfixturevalue(which)
+    key, brow = _mirror_index(s)
+    for b in range(s.nnzb):
+        i, j = int(brow[b]), int(s.col[b])
+        mb = key[(j, i) + tuple(-int(x) for x in s.shift[b])]
+        np.testing.assert_array_equal(s.block(s.S, b), s.block(s.S, mb).T)
+        np.testing.assert_array_equal(s.block(s.H, b), s.block(s.H, mb).T)
+
+
+def test_on_site_blocks(mixed_system):
+    s = mixed_system
+    brow = s.block_rows()
+    for b in range(s.nnzb):
+        i = int(brow[b])
+        if int(s.col[b]) == i and not np.any(s.shift[b]):
+            np.testing.assert_allclose(np.diag(s.block(s.S, b)), 1.0, rtol=0, atol=1e-15)
+            np.testing.assert_array_equal(np.diag(s.block(s.H, b)), s.onsite[i])
+
+
+def test_rows_sorted(mixed_system):
+    s = mixed_system
+    for i in range(s.natoms):
+        b0, b1 = s.row_ptr[i], s.row_ptr[i + 1]
+        keys = [(int(s.col[b]),) + tuple(int(x) for x in s.shift[b]) for b in range(b0, b1)]
+        assert keys == sorted(keys)
+
+
+def test_overlap_by_quadrature():
+    """The closed-form Gaussian overlap against a separable numerical integral."""
+    a, b = 0.37, 1.9
+    R = np.array([0.8, -0.3, 1.1])
+    x = np.linspace(-12, 12, 20001)
+    dx = x[1] - x[0]
+    val = 1.0
+    for d in range(3):
+        ga = (2 * a / np.pi) ** 0.25 * np.exp(-a * x ** 2)
+        gb = (2 * b / np.pi) ** 0.25 * np.exp(-b * (x - R[d]) ** 2)
+        val *= np.sum(ga * gb) * dx
+    got = T.gaussian_overlap(np.array(a), np.array(b), np.array(R @ R))
+    assert abs(got - val) < 1e-12
+
+
+def test_drop_rule_and_cutoff(cfg1):
+    s = cfg1
+    nz = s.S[s.S != 0.0]
+    assert np.all(np.abs(nz) >= T.DROP_TOL)
+    assert np.all(s.H[s.S == 0.0] == 0.0)
+    rc = T.overlap_cutoff(0.2)
+    assert abs(T.gaussian_overlap(np.array(0.2), np.array(0.2), np.array(rc ** 2)) - T.DROP_TOL) < 1e-22
+
+
+def test_wolfsberg_helmholz(mixed_system):
+    s = mixed_system
+    brow = s.block_rows()
+    b = next(b for b in range(s.nnzb) if int(s.col[b]) != int(brow[b]))
+    i, j = int(brow[b]), int(s.col[b])
+    want = 1.75 * s.block(s.S, b) * 0.5 * (s.onsite[i][:, None] + s.onsite[j][None, :])
+    np.testing.assert_allclose(s.block(s.H, b), want, rtol=1e-15, atol=0)
+
+
+def test_cfg1_overlap_spd(cfg1):
+    import oracle
+    H, S, _ = oracle.dense_matrices(cfg1)
+    assert np.all(np.linalg.eigvalsh(S) > 0)
+
+
+def test_synthetic_density_symmetric(mixed_system):
+    s = mixed_system
+    rho = T.synthetic_density(s, seed=3)
+    key, brow = _mirror_index(s)
+    for b in range(s.nnzb):
+        i, j = int(brow[b]), int(s.col[b])
+        mb = key[(j, i) + tuple(-int(x) for x in s.shift[b])]
+        np.testing.assert_allclose(s.block(rho, b), s.block(rho, mb).T, rtol=1e-15, atol=0)
