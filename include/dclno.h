@@ -1,0 +1,224 @@
+/*
+ * libdclno -- the data-parallel hot path of the O(N) divide-conquer method
+ * with localized natural orbitals (DC-LNO; Ozaki, Fukuda and Jiang), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * One DC-LNO step (Sec. II.C, steps (i)-(v)):
+ *   dclno_compute_lnos    LNOs of every atom from its block of the occupied-space
+ *                         projector: Lambda_0i = sum_Rj rho_{0i,Rj} S_{Rj,0i}
+ *                         (Eq. (Lambda)), V^-1 Lambda V = lambda (Eq. (eigendecomp)),
+ *                         keep the leading k eigenvectors (Eq. (apop_Lambda)).
+ *   dclno_solve_clusters  for every atom i: H^(i), S^(i) of its truncated cluster in
+ *                         the mixed PAO/LNO basis (Eq. (Hi)); H^(i) c = eps S^(i) c;
+ *                         central-atom weights of the spectral Green function (Eq. (Gi)).
+ *   dclno_find_mu         the common chemical potential that conserves the electron
+ *                         count (Sec. II.C step (iv)).
+ *   dclno_density_matrix  density-matrix rows of every central atom (Eq. (dm) with
+ *                         Eq. (Gi)), kept where S != 0, and the band energy.
+ * dclno_build_clusters fixes the truncated clusters (Fig. 1; short-range region of
+ * radius r_core with PAOs, long-range region up to r_lno with k LNOs per atom).
+ *
+ * Conventions (all calls):
+ *  - Units: bohr and hartree.  Spin-unpolarised: a factor 2 is applied inside
+ *    electron counts and band energies (Sec. II.B, N_ele = 2 tr[rho S]).
+ *  - Matrices of the system are block-sparse rows (BSR) keyed by (i, j, R):
+ *    row i holds blocks row_ptr[i] .. row_ptr[i+1]-1, sorted by (col, shift[0],
+ *    shift[1], shift[2]); block b is the M_i x M_col row-major matrix starting at
+ *    element blk_off[b] of a value array.  These are the paper's blocks
+ *    S_{0i,Rj}, H_{0i,Rj} of Sec. II.B.  Density matrices use the same pattern.
+ *  - Ownership: the caller owns every pointer it passes (host or device as
+ *    stated); the context owns its device workspace.  A context keeps pointers
+ *    to the caller's device H and S until it is destroyed or rebuilt: they must
+ *    stay valid and unchanged in between.
+ *  - Streams: all GPU work is ordered on the stream given to dclno_create (NULL =
+ *    legacy default stream).  Calls that return host scalars synchronise it.
+ *  - Errors: every call returns a dclno_status; on failure dclno_last_error()
+ *    gives a message (with the first failing cluster where there is one).  No
+ *    call prints or aborts.  A context is single-threaded.
+ */
+#ifndef DCLNO_H
+#define DCLNO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DCLNO_OK = 0,
+    DCLNO_ERR_ARG = 1,            /* invalid argument or call order */
+    DCLNO_ERR_CUDA = 2,           /* CUDA runtime error */
+    DCLNO_ERR_OOM = 3,            /* device workspace could not be allocated */
+    DCLNO_ERR_NOT_SPD = 4,        /* a cluster overlap S^(i) is not positive definite */
+    DCLNO_ERR_NO_BRACKET = 5,     /* N_e lies outside [N(mu_lo), N(mu_hi)] */
+    DCLNO_ERR_NOT_CONVERGED = 6,  /* an eigensolver iteration did not converge */
+    DCLNO_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
+    DCLNO_ERR_NO_LNOS = 8         /* solve requested before LNOs were computed */
+} dclno_status;
+
+typedef enum {
+    DCLNO_FP64 = 0,   /* every step in FP64 */
+    DCLNO_MIXED = 1   /* reserved: FP32/TF32 bulk with FP64 refinement */
+} dclno_precision;
+
+/* LNO eigenvalue flags returned by dclno_get_lnos (bit set per atom). */
+#define DCLNO_LNO_COMPLEX_SELECTED 1 /* a selected eigenvalue of Lambda is complex */
+#define DCLNO_LNO_PAIR_SPLIT 2       /* a complex pair straddles the cut; its real part was kept */
+
+typedef struct dclno_ctx dclno_ctx;
+
+typedef struct {
+    int natoms;                /* N */
+    const double *pos;         /* host [N][3], atom positions tau_i */
+    const double *cell;        /* host [3][3], rows are the lattice vectors */
+    const int *pbc;            /* host [3], nonzero = periodic direction */
+    const int *norb;           /* host [N], M_i (1 .. 32) */
+    long long nnzb;            /* number of stored blocks */
+    long long nval;            /* number of stored values (sum of block sizes) */
+    const long long *row_ptr;  /* host [N+1] */
+    const int *col;            /* host [nnzb] */
+    const signed char *shift;  /* host [nnzb][3], cell shift R of each block */
+    const long long *blk_off;  /* host [nnzb] */
+    const double *H;           /* device [nval], Hamiltonian blocks H_{0i,Rj} */
+    const double *S;           /* device [nval], overlap blocks S_{0i,Rj} (symmetric, SPD) */
+} dclno_system;
+
+/*
+ * Create a context bound to `cuda_stream` (a cudaStream_t, or NULL) on the
+ * current CUDA device.  Returns DCLNO_ERR_ARG if out is NULL.
+ */
+dclno_status dclno_create(dclno_ctx **out, void *cuda_stream);
+
+/* Free the context and its device workspace (NULL is a no-op). */
+void dclno_destroy(dclno_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none); ctx may be NULL. */
+const char *dclno_last_error(const dclno_ctx *ctx);
+
+/*
+ * Truncated clusters (Fig. 1; Sec. III region construction with fixed radii).
+ * For every atom i the cluster holds the images (j, R) with
+ * |tau_j + R cell - tau_i| <= r_lno (+1e-9 bohr): those within r_core carry
+ * their M_j PAOs, the others k_lno LNOs.  Members are ordered by distance
+ * descending, so the central atom is last.  The cluster dimension is
+ * n_i = sum_core M_j + k_lno * |LNO members|.  Copies the structure of `sys` to
+ * the device, keeps the device pointers sys->H and sys->S, and allocates the
+ * workspace of the FP64 solver for all clusters at once.
+ * Errors: DCLNO_ERR_ARG (radii, k_lno > M_j, unsorted rows, missing on-site
+ * block), DCLNO_ERR_OOM.
+ */
+dclno_status dclno_build_clusters(dclno_ctx *ctx, const dclno_system *sys,
+                                  double r_core, double r_lno, int k_lno);
+
+/*
+ * LNOs of every atom (Sec. II.B, steps (i)-(iii) of LNO generation):
+ * Lambda_0i = sum_Rj rho_{0i,Rj} S_{Rj,0i} (Eq. (Lambda)) from the device density
+ * matrix `rho` [nval] in the BSR pattern of S; eigenvalues of the nonsymmetric
+ * Lambda_0i by Householder-Hessenberg reduction and Francis double-shift QR;
+ * eigenvectors of the k_lno eigenvalues of largest real part by inverse
+ * iteration.  The kept vectors are returned to the S_ii-orthonormal basis of
+ * their span, each with its largest-magnitude component positive (only the
+ * span enters the cluster problem).  A selected complex pair contributes its
+ * real and imaginary parts; a pair split by the cut contributes its real part.
+ * No-op when k_lno = 0 or r_lno = r_core.
+ */
+dclno_status dclno_compute_lnos(dclno_ctx *ctx, const double *rho);
+
+/*
+ * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
+ * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
+ * implicit QL on the tridiagonal matrix, and the central-atom rows of the
+ * eigenvectors C = L^-T Q Z.  Keeps per cluster the eigenvalues eps_mu,
+ * the weights q_mu = sum_{alpha in i} C_{alpha mu} (S^(i) C)_{alpha mu}
+ * (sum_mu q_mu = M_i) and what dclno_density_matrix needs.
+ * Errors: DCLNO_ERR_NO_LNOS, DCLNO_ERR_NOT_SPD, DCLNO_ERR_NOT_CONVERGED (cluster id
+ * in the message), DCLNO_ERR_ARG for an unsupported precision.
+ */
+dclno_status dclno_solve_clusters(dclno_ctx *ctx, dclno_precision precision);
+
+/*
+ * Common chemical potential (Sec. II.C step (iv)): mu with
+ * N(mu) = 2 sum_i sum_mu f((eps_mu^(i) - mu)/kT) q_mu^(i) = n_electrons,
+ * f(x) = 1/(1+e^x), by device-wide k-section of [min eps - 40 kT, max eps + 40 kT]
+ * to double precision (or |N - N_e| <= 1e-12 N_e).  Writes host scalars
+ * mu_out and nelec_out (= N(mu)); either may be NULL.
+ * Errors: DCLNO_ERR_NO_BRACKET, DCLNO_ERR_ARG (kT <= 0, no solve yet).
+ */
+dclno_status dclno_find_mu(dclno_ctx *ctx, double n_electrons, double kT,
+                           double *mu_out, double *nelec_out);
+
+/*
+ * Density-matrix rows of every central atom at chemical potential mu
+ * (Eq. (dm) with the spectral Green function of Eq. (Gi)):
+ * rho_{0i alpha, Rj beta} = sum_mu f(eps_mu) c_{mu,0i alpha} c_{mu,Rj beta},
+ * with LNO columns returned to PAOs through V_j, written to the device array
+ * rho_out [nval] in the BSR pattern of S (zero for pairs outside the cluster).
+ * eband_out (host, nullable) = 2 sum_i sum_mu f(eps_mu) eps_mu q_mu.
+ */
+dclno_status dclno_density_matrix(dclno_ctx *ctx, double mu, double kT,
+                                  double *rho_out, double *eband_out);
+
+/*
+ * One whole DC-LNO step: compute_lnos(rho_in), solve_clusters(precision),
+ * find_mu, density_matrix(rho_out).  With host_buffers != 0, rho_in and rho_out
+ * are host arrays [nval] copied to and from the context's device buffers inside
+ * the call; otherwise they are device arrays.  mu_out, nelec_out, eband_out are
+ * host scalars (nullable).
+ */
+dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
+                        int host_buffers, dclno_precision precision,
+                        double n_electrons, double kT,
+                        double *mu_out, double *nelec_out, double *eband_out);
+
+/* ---- inspection (tests, benchmarks) ------------------------------------ */
+
+/*
+ * Cluster sizes after dclno_build_clusters: dims_out [N] (host, n_i),
+ * nmembers_out [N] (host, members incl. the centre), both nullable.
+ * total_out (host, nullable) = sum_i n_i.
+ */
+dclno_status dclno_cluster_info(dclno_ctx *ctx, int *dims_out, int *nmembers_out,
+                                long long *total_out);
+
+/*
+ * Spectra after dclno_solve_clusters, cluster by cluster in atom order, each
+ * cluster's n_i eigenvalues in solver order (not sorted): eps_out, q_out are
+ * host arrays of length sum_i n_i (nullable).
+ */
+dclno_status dclno_get_spectrum(dclno_ctx *ctx, double *eps_out, double *q_out);
+
+/*
+ * LNOs after dclno_compute_lnos, atom by atom: V_out [sum_i M_i k] (host, the
+ * M_i x k block of atom i row-major), lam_re/lam_im [sum_i M_i] (host, Lambda
+ * eigenvalues sorted by real part descending), flags [N] (host).  All nullable.
+ */
+dclno_status dclno_get_lnos(dclno_ctx *ctx, double *V_out, double *lam_re,
+                            double *lam_im, int *flags);
+
+/* Number of kernel launches this context has issued so far (for reports). */
+long long dclno_launch_count(const dclno_ctx *ctx);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch (off by default).  dclno_set_profiling(ctx, on) clears the
+ * totals and switches recording on or off.  dclno_kernel_time(ctx, name, ...)
+ * waits for the recorded launches of kernel `name` (e.g. "k_tridiag") and
+ * returns their summed duration in milliseconds and their count (host
+ * scalars, nullable); unknown names give 0.
+ */
+dclno_status dclno_set_profiling(dclno_ctx *ctx, int on);
+
+/*
+ * FP64 throughput of the current device, measured in the call with two short
+ * kernels (about 0.1 s): FP64 fused multiply-add and FP64 tensor-core MMA
+ * (mma.sync m8n8k4), in TFLOP/s (host scalars, nullable).  Used as the
+ * denominators of roofline fractions; allocates and frees a small buffer.
+ */
+dclno_status dclno_measure_fp64_peaks(double *dfma_tflops, double *dmma_tflops);
+dclno_status dclno_kernel_time(dclno_ctx *ctx, const char *name, double *total_ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCLNO_H */

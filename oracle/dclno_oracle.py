@@ -449,6 +449,8 @@ class ClusterResult:
     eps: np.ndarray
     q: np.ndarray
     C: np.ndarray
+    h_norm: float = 0.0  # Frobenius norms of H^(i) and S^(i) (for error bounds in tests)
+    s_norm: float = 0.0
 
 
 def _threads():
@@ -473,7 +475,7 @@ def dclno_solve(system, V: dict, r_core: float, r_lno: float, k_lno: int, atoms=
     def work(cl):
         Hc, Sc = assemble(system, cl, V, bidx)
         eps, q, C = solve_cluster(Hc, Sc, cl)
-        return ClusterResult(cl, eps, q, C)
+        return ClusterResult(cl, eps, q, C, float(np.linalg.norm(Hc)), float(np.linalg.norm(Sc)))
 
     nt = threads or _threads()
     if nt > 1 and len(clusters) > 1:

@@ -1,0 +1,234 @@
+"""ctypes binding of libdclno (include/dclno.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdclno.so")
+
+DCLNO_FP64 = 0
+DCLNO_MIXED = 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_NO_BRACKET",
+                6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_NO_LNOS"}
+
+# every entry point declared in include/dclno.h
+SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clusters", "dclno_compute_lnos",
+           "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
+           "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
+           "dclno_kernel_time", "dclno_measure_fp64_peaks"]
+
+
+class DclnoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dclno_system(ctypes.Structure):
+    _fields_ = [
+        ("natoms", ctypes.c_int),
+        ("pos", ctypes.c_void_p),
+        ("cell", ctypes.c_void_p),
+        ("pbc", ctypes.c_void_p),
+        ("norb", ctypes.c_void_p),
+        ("nnzb", ctypes.c_longlong),
+        ("nval", ctypes.c_longlong),
+        ("row_ptr", ctypes.c_void_p),
+        ("col", ctypes.c_void_p),
+        ("shift", ctypes.c_void_p),
+        ("blk_off", ctypes.c_void_p),
+        ("H", ctypes.c_void_p),
+        ("S", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+
+
+def load_library():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    sigs = {
+        "dclno_create": ([ctypes.POINTER(P), P], I),
+        "dclno_destroy": ([P], None),
+        "dclno_last_error": ([P], ctypes.c_char_p),
+        "dclno_build_clusters": ([P, ctypes.POINTER(dclno_system), D, D, I], I),
+        "dclno_compute_lnos": ([P, P], I),
+        "dclno_solve_clusters": ([P, I], I),
+        "dclno_find_mu": ([P, D, D, P, P], I),
+        "dclno_density_matrix": ([P, D, D, P, P], I),
+        "dclno_step": ([P, P, P, I, I, D, D, P, P, P], I),
+        "dclno_cluster_info": ([P, P, P, P], I),
+        "dclno_get_spectrum": ([P, P, P], I),
+        "dclno_get_lnos": ([P, P, P, P, P], I),
+        "dclno_launch_count": ([P], ctypes.c_longlong),
+        "dclno_set_profiling": ([P, I], I),
+        "dclno_kernel_time": ([P, ctypes.c_char_p, P, P], I),
+        "dclno_measure_fp64_peaks": ([P, P], I),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of SYMBOLS that the built library exports."""
+    lib = load_library()
+    return [s for s in SYMBOLS if hasattr(lib, s)]
+
+
+def measure_fp64_peaks():
+    """(DFMA, DMMA) FP64 TFLOP/s of the current CUDA device, measured now."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = lib.dclno_measure_fp64_peaks(_dptr(a), _dptr(b))
+    if st != 0:
+        raise DclnoError(st, "dclno_measure_fp64_peaks failed")
+    return a.value, b.value
+
+
+def _ptr(x):
+    """Address of a numpy array (host) or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _dptr(v: ctypes.c_double):
+    return ctypes.cast(ctypes.byref(v), ctypes.c_void_p)
+
+
+class Context:
+    """One libdclno context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        self.lib = load_library()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        self._check(self.lib.dclno_create(ctypes.byref(h), ctypes.c_void_p(stream)), None)
+        self.h = h
+        self._keep = []
+        self.natoms = 0
+        self.nval = 0
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            msg = self.lib.dclno_last_error(self.h if h == "self" else None)
+            raise DclnoError(st, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dclno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the five calls of a DC-LNO step
+    def build_clusters(self, pos, cell, pbc, norb, row_ptr, col, shift, blk_off, H, S, r_core, r_lno, k_lno):
+        host = dict(
+            pos=np.ascontiguousarray(pos, dtype=np.float64), cell=np.ascontiguousarray(cell, dtype=np.float64),
+            pbc=np.ascontiguousarray(np.asarray(pbc).astype(np.int32)),
+            norb=np.ascontiguousarray(norb, dtype=np.int32), row_ptr=np.ascontiguousarray(row_ptr, dtype=np.int64),
+            col=np.ascontiguousarray(col, dtype=np.int32), shift=np.ascontiguousarray(shift, dtype=np.int8),
+            blk_off=np.ascontiguousarray(blk_off, dtype=np.int64))
+        nval = int(H.numel())
+        s = dclno_system(natoms=len(host["norb"]), pos=_ptr(host["pos"]), cell=_ptr(host["cell"]),
+                         pbc=_ptr(host["pbc"]), norb=_ptr(host["norb"]), nnzb=len(host["col"]), nval=nval,
+                         row_ptr=_ptr(host["row_ptr"]), col=_ptr(host["col"]), shift=_ptr(host["shift"]),
+                         blk_off=_ptr(host["blk_off"]), H=_ptr(H), S=_ptr(S))
+        self._check(self.lib.dclno_build_clusters(self.h, ctypes.byref(s), float(r_core), float(r_lno), int(k_lno)))
+        self._keep = [H, S]
+        self.natoms = len(host["norb"])
+        self.nval = nval
+        self.norb = host["norb"]
+        self.k_lno = int(k_lno)
+
+    def compute_lnos(self, rho):
+        self._check(self.lib.dclno_compute_lnos(self.h, _ptr(rho)))
+
+    def solve_clusters(self, precision=DCLNO_FP64):
+        self._check(self.lib.dclno_solve_clusters(self.h, int(precision)))
+
+    def find_mu(self, n_electrons, kT):
+        mu, n = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.dclno_find_mu(self.h, float(n_electrons), float(kT), _dptr(mu), _dptr(n)))
+        return mu.value, n.value
+
+    def density_matrix(self, mu, kT, rho_out):
+        e = ctypes.c_double()
+        self._check(self.lib.dclno_density_matrix(self.h, float(mu), float(kT), _ptr(rho_out), _dptr(e)))
+        return e.value
+
+    def step(self, rho_in, rho_out, n_electrons, kT, host_buffers=False, precision=DCLNO_FP64):
+        mu, n, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.dclno_step(self.h, _ptr(rho_in), _ptr(rho_out), int(bool(host_buffers)),
+                                        int(precision), float(n_electrons), float(kT), _dptr(mu), _dptr(n),
+                                        _dptr(e)))
+        return mu.value, n.value, e.value
+
+    # ---- inspection
+    def cluster_info(self):
+        dims = np.zeros(self.natoms, np.int32)
+        nmem = np.zeros(self.natoms, np.int32)
+        tot = ctypes.c_longlong()
+        self._check(self.lib.dclno_cluster_info(self.h, _ptr(dims), _ptr(nmem),
+                                                ctypes.cast(ctypes.byref(tot), ctypes.c_void_p)))
+        return dims, nmem, tot.value
+
+    def spectrum(self):
+        dims, _, tot = self.cluster_info()
+        eps = np.zeros(tot)
+        q = np.zeros(tot)
+        self._check(self.lib.dclno_get_spectrum(self.h, _ptr(eps), _ptr(q)))
+        off = np.concatenate([[0], np.cumsum(dims)])
+        return [(eps[off[i]:off[i + 1]], q[off[i]:off[i + 1]]) for i in range(self.natoms)]
+
+    def lnos(self):
+        k = self.k_lno
+        V = np.zeros(int(np.sum(self.norb)) * k)
+        lre = np.zeros(int(np.sum(self.norb)))
+        lim = np.zeros_like(lre)
+        fl = np.zeros(self.natoms, np.int32)
+        self._check(self.lib.dclno_get_lnos(self.h, _ptr(V), _ptr(lre), _ptr(lim), _ptr(fl)))
+        out = {}
+        vo = mo = 0
+        for i, m in enumerate(self.norb):
+            m = int(m)
+            out[i] = (V[vo:vo + m * k].reshape(m, k), lre[mo:mo + m] + 1j * lim[mo:mo + m], int(fl[i]))
+            vo += m * k
+            mo += m
+        return out
+
+    def launch_count(self):
+        return int(self.lib.dclno_launch_count(self.h))
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.dclno_set_profiling(self.h, int(bool(on))))
+
+    def kernel_time(self, name):
+        """(total milliseconds, launches) of kernel `name` since profiling was switched on."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self._check(self.lib.dclno_kernel_time(self.h, name.encode(), _dptr(ms),
+                                               ctypes.cast(ctypes.byref(n), ctypes.c_void_p)))
+        return ms.value, n.value

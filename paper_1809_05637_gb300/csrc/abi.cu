@@ -1,0 +1,528 @@
+// C-ABI entry points of libdclno and the host-side set-up of a DC-LNO step:
+// truncated clusters, device copies of the system structure, workspace layout.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "dclno_internal.cuh"
+
+dclno_status set_err(dclno_ctx* c, dclno_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                    ") in " + where;
+    if (e == cudaErrorMemoryAllocation) return set_err(c, DCLNO_ERR_OOM, m);
+    return set_err(c, DCLNO_ERR_CUDA, m);
+}
+
+template <class T>
+static void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+static void free_clusters(dclno_ctx* c) {
+    dfree(c->d_norb);
+    dfree(c->d_row_ptr);
+    dfree(c->d_key);
+    dfree(c->d_blk_off);
+    dfree(c->d_onsite);
+    dfree(c->d_voff);
+    dfree(c->d_loff);
+    dfree(c->d_moff);
+    dfree(c->d_cl);
+    dfree(c->d_order);
+    dfree(c->d_mem);
+    dfree(c->d_mem_cl);
+    dfree(c->d_rowblk_member);
+    dfree(c->d_status);
+    dfree(c->d_arena);
+    dfree(c->d_iters);
+    dfree(c->d_eps);
+    dfree(c->d_q);
+    dfree(c->d_V);
+    dfree(c->d_lam_re);
+    dfree(c->d_lam_im);
+    dfree(c->d_Lambda);
+    dfree(c->d_lflags);
+    dfree(c->d_mu_work);
+    dfree(c->d_scalars);
+    dfree(c->d_eband);
+    dfree(c->d_rho_in);
+    dfree(c->d_rho_out);
+    c->built = c->lnos_ready = c->solved = false;
+}
+
+extern "C" dclno_status dclno_create(dclno_ctx** out, void* cuda_stream) {
+    if (!out) return DCLNO_ERR_ARG;
+    *out = nullptr;
+    dclno_ctx* c = new (std::nothrow) dclno_ctx();
+    if (!c) return DCLNO_ERR_OOM;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return DCLNO_ERR_CUDA;
+    }
+    *out = c;
+    return DCLNO_OK;
+}
+
+void prof_collect(dclno_ctx* c) {
+    for (auto& kv : c->prof) {
+        for (auto& ev : kv.second.pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(ev.second) == cudaSuccess && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+                kv.second.ms += ms;
+                kv.second.launches += 1;
+            }
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        kv.second.pending.clear();
+    }
+}
+
+extern "C" void dclno_destroy(dclno_ctx* c) {
+    if (!c) return;
+    prof_collect(c);
+    free_clusters(c);
+    delete c;
+}
+
+extern "C" dclno_status dclno_set_profiling(dclno_ctx* c, int on) {
+    if (!c) return DCLNO_ERR_ARG;
+    prof_collect(c);
+    c->prof.clear();
+    c->prof_on = on != 0;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_kernel_time(dclno_ctx* c, const char* name, double* total_ms, long long* launches) {
+    if (!c || !name) return DCLNO_ERR_ARG;
+    prof_collect(c);
+    auto it = c->prof.find(name);
+    if (total_ms) *total_ms = it == c->prof.end() ? 0.0 : it->second.ms;
+    if (launches) *launches = it == c->prof.end() ? 0 : it->second.launches;
+    return DCLNO_OK;
+}
+
+extern "C" const char* dclno_last_error(const dclno_ctx* c) { return c ? c->err.c_str() : ""; }
+
+extern "C" long long dclno_launch_count(const dclno_ctx* c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Cluster construction
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Cand {
+    double d;
+    int atom;
+    int s0, s1, s2;
+};
+
+// images (j, R) within rmax of atom i: brute force over a cell list of image points
+struct ImageGrid {
+    std::vector<double> px, py, pz;
+    std::vector<int> atom, s0, s1, s2;
+    double lo[3], cw;
+    int nc[3];
+    std::vector<int> head, next;
+
+    void build(const dclno_ctx* c, double rmax) {
+        int nmax[3];
+        for (int d = 0; d < 3; ++d) {
+            if (!c->pbc[d]) {
+                nmax[d] = 0;
+                continue;
+            }
+            const double* a = &c->cell[3 * d];
+            const double* e = &c->cell[3 * ((d + 1) % 3)];
+            const double* f = &c->cell[3 * ((d + 2) % 3)];
+            double cr[3] = {e[1] * f[2] - e[2] * f[1], e[2] * f[0] - e[0] * f[2], e[0] * f[1] - e[1] * f[0]};
+            double area = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            double h = std::fabs(a[0] * cr[0] + a[1] * cr[1] + a[2] * cr[2]) / area;
+            nmax[d] = (int)std::ceil(rmax / h) + 1;
+        }
+        for (int a = -nmax[0]; a <= nmax[0]; ++a)
+            for (int b = -nmax[1]; b <= nmax[1]; ++b)
+                for (int g = -nmax[2]; g <= nmax[2]; ++g)
+                    for (int j = 0; j < c->N; ++j) {
+                        double x[3];
+                        for (int d = 0; d < 3; ++d)
+                            x[d] = c->pos[3 * j + d] + (a * c->cell[d] + b * c->cell[3 + d] + g * c->cell[6 + d]);
+                        px.push_back(x[0]);
+                        py.push_back(x[1]);
+                        pz.push_back(x[2]);
+                        atom.push_back(j);
+                        s0.push_back(a);
+                        s1.push_back(b);
+                        s2.push_back(g);
+                    }
+        double hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = 1e300;
+            hi[d] = -1e300;
+        }
+        for (size_t k = 0; k < px.size(); ++k) {
+            double x[3] = {px[k], py[k], pz[k]};
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], x[d]);
+                hi[d] = std::max(hi[d], x[d]);
+            }
+        }
+        cw = std::max(rmax, 1e-3);
+        for (int d = 0; d < 3; ++d) nc[d] = std::max(1, (int)((hi[d] - lo[d]) / cw) + 1);
+        head.assign((size_t)nc[0] * nc[1] * nc[2], -1);
+        next.assign(px.size(), -1);
+        for (size_t k = 0; k < px.size(); ++k) {
+            int ci = cell_of(px[k], 0), cj = cell_of(py[k], 1), ck = cell_of(pz[k], 2);
+            size_t h = ((size_t)ci * nc[1] + cj) * nc[2] + ck;
+            next[k] = head[h];
+            head[h] = (int)k;
+        }
+    }
+    int cell_of(double x, int d) const {
+        int v = (int)std::floor((x - lo[d]) / cw);
+        return std::min(std::max(v, 0), nc[d] - 1);
+    }
+};
+
+}  // namespace
+
+static dclno_status copy_to_device(dclno_ctx* c, void** dst, const void* src, size_t bytes) {
+    DCLNO_CUDA(c, cudaMalloc(dst, std::max<size_t>(bytes, 16)));
+    if (bytes) DCLNO_CUDA(c, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* sys, double r_core,
+                                             double r_lno, int k_lno) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!sys || sys->natoms <= 0 || !sys->pos || !sys->cell || !sys->pbc || !sys->norb || !sys->row_ptr ||
+        !sys->col || !sys->shift || !sys->blk_off || !sys->H || !sys->S)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters: null or empty system");
+    if (!(r_core >= 0.0) || !(r_lno >= r_core) || k_lno < 0)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters: need 0 <= r_core <= r_lno and k_lno >= 0");
+    DCLNO_CUDA(c, cudaSetDevice(c->device));
+    free_clusters(c);
+
+    const int N = sys->natoms;
+    c->N = N;
+    c->nnzb = sys->nnzb;
+    c->nval = sys->nval;
+    c->norb.assign(sys->norb, sys->norb + N);
+    c->row_ptr.assign(sys->row_ptr, sys->row_ptr + N + 1);
+    c->col.assign(sys->col, sys->col + sys->nnzb);
+    c->blk_off.assign(sys->blk_off, sys->blk_off + sys->nnzb);
+    c->pos.assign(sys->pos, sys->pos + 3 * N);
+    c->cell.assign(sys->cell, sys->cell + 9);
+    for (int d = 0; d < 3; ++d) c->pbc[d] = sys->pbc[d] ? 1 : 0;
+    c->H = sys->H;
+    c->S = sys->S;
+    c->r_core = r_core;
+    c->r_lno = r_lno;
+    c->k_lno = k_lno;
+
+    // ---- validate the structure
+    if (c->row_ptr[0] != 0 || c->row_ptr[N] != c->nnzb)
+        return set_err(c, DCLNO_ERR_ARG, "row_ptr must start at 0 and end at nnzb");
+    for (int i = 0; i < N; ++i) {
+        if (c->norb[i] < 1 || c->norb[i] > DCLNO_MAX_M)
+            return set_err(c, DCLNO_ERR_ARG, "norb must lie in 1..32 (atom " + std::to_string(i) + ")");
+        if (c->row_ptr[i + 1] < c->row_ptr[i]) return set_err(c, DCLNO_ERR_ARG, "row_ptr not monotone");
+    }
+    c->pshift.resize(c->nnzb);
+    std::vector<long long> key(c->nnzb), onsite(N, -1);
+    for (int i = 0; i < N; ++i) {
+        for (long long b = c->row_ptr[i]; b < c->row_ptr[i + 1]; ++b) {
+            int j = c->col[b];
+            if (j < 0 || j >= N) return set_err(c, DCLNO_ERR_ARG, "column index out of range");
+            int s0 = sys->shift[3 * b], s1 = sys->shift[3 * b + 1], s2 = sys->shift[3 * b + 2];
+            c->pshift[b] = pack_shift(s0, s1, s2);
+            key[b] = block_key(j, c->pshift[b]);
+            if (b > c->row_ptr[i] && key[b] <= key[b - 1])
+                return set_err(c, DCLNO_ERR_ARG, "BSR rows must be sorted by (col, shift) without duplicates");
+            long long sz = (long long)c->norb[i] * c->norb[j];
+            if (c->blk_off[b] < 0 || c->blk_off[b] + sz > c->nval)
+                return set_err(c, DCLNO_ERR_ARG, "block offset out of range");
+            if (j == i && s0 == 0 && s1 == 0 && s2 == 0) onsite[i] = b;
+        }
+        if (onsite[i] < 0) return set_err(c, DCLNO_ERR_ARG, "missing on-site block of atom " + std::to_string(i));
+        if (r_lno > r_core && k_lno > 0 && (k_lno > c->norb[i] || c->norb[i] > DCLNO_MAX_M_LNO))
+            return set_err(c, DCLNO_ERR_ARG, "atom " + std::to_string(i) + ": LNOs need k_lno <= M_i <= 16");
+    }
+
+    // ---- clusters: membership by distance, order by distance descending (centre last)
+    ImageGrid g;
+    g.build(c, r_lno);
+    const double tol = 1e-9;
+    c->cl.resize(N);
+    c->mem.clear();
+    std::vector<int> rowblk_member(c->nnzb, -1);
+    std::vector<int> mem_cl;
+    c->has_lno_region = false;
+    long long mat = 0, eig = 0, its = 0;
+    for (int i = 0; i < N; ++i) {
+        const double xi = c->pos[3 * i], yi = c->pos[3 * i + 1], zi = c->pos[3 * i + 2];
+        std::vector<Cand> cand;
+        int ci = g.cell_of(xi, 0), cj = g.cell_of(yi, 1), ck = g.cell_of(zi, 2);
+        for (int a = std::max(ci - 1, 0); a <= std::min(ci + 1, g.nc[0] - 1); ++a)
+            for (int b = std::max(cj - 1, 0); b <= std::min(cj + 1, g.nc[1] - 1); ++b)
+                for (int q = std::max(ck - 1, 0); q <= std::min(ck + 1, g.nc[2] - 1); ++q)
+                    for (int k = g.head[((size_t)a * g.nc[1] + b) * g.nc[2] + q]; k >= 0; k = g.next[k]) {
+                        double dx = g.px[k] - xi, dy = g.py[k] - yi, dz = g.pz[k] - zi;
+                        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+                        if (d <= r_lno + tol) cand.push_back({d, g.atom[k], g.s0[k], g.s1[k], g.s2[k]});
+                    }
+        std::sort(cand.begin(), cand.end(), [](const Cand& u, const Cand& v) {
+            if (u.d != v.d) return u.d > v.d;
+            if (u.atom != v.atom) return u.atom < v.atom;
+            if (u.s0 != v.s0) return u.s0 < v.s0;
+            if (u.s1 != v.s1) return u.s1 < v.s1;
+            return u.s2 < v.s2;
+        });
+        if (cand.empty() || cand.back().atom != i || cand.back().s0 || cand.back().s1 || cand.back().s2)
+            return set_err(c, DCLNO_ERR_ARG, "cluster of atom " + std::to_string(i) + " does not end with its centre");
+        ClusterDesc& d = c->cl[i];
+        d.centre = i;
+        d.nmem = (int)cand.size();
+        d.mbeg = (long long)c->mem.size();
+        int off = 0;
+        std::vector<std::pair<long long, int>> keys;
+        keys.reserve(cand.size());
+        for (size_t m = 0; m < cand.size(); ++m) {
+            const Cand& u = cand[m];
+            int core = (u.d <= r_core + tol) ? 1 : 0;
+            if (r_lno <= r_core || k_lno == 0) core = 1;  // plain PAO DC: no LNO region
+            if (!core) c->has_lno_region = true;
+            MemberDesc md;
+            md.atom = u.atom;
+            md.shift = pack_shift(u.s0, u.s1, u.s2);
+            md.off = off;
+            md.core = core;
+            off += core ? c->norb[u.atom] : k_lno;
+            c->mem.push_back(md);
+            mem_cl.push_back(i);
+            keys.push_back({block_key(u.atom, md.shift), (int)m});
+        }
+        d.n = off;
+        d.ld = (off + 3) & ~3;
+        d.mc = c->norb[i];
+        std::sort(keys.begin(), keys.end());
+        for (long long b = c->row_ptr[i]; b < c->row_ptr[i + 1]; ++b) {
+            auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key[b], -1));
+            if (it != keys.end() && it->first == key[b]) rowblk_member[b] = it->second;
+        }
+        // workspace layout (doubles): A, L (n x ld each), d/e/tau (ld each), W (32 ld), P ([n][2 mc]),
+        // rotation log (2 rot_cap)
+        const long long n = d.n;
+        d.mat_off = mat;
+        mat += 2 * n * d.ld;
+        d.aux_off = mat;
+        mat += 3LL * d.ld + 32LL * d.ld;  // d, e, tau, W: each sub-region starts on a multiple of 4 doubles
+        d.cc_off = mat;
+        mat += 2LL * d.mc * d.ld;
+        d.rot_cap = (int)std::min<long long>(3 * n * n / 2 + 64 * n + 64, 2000000000LL);
+        d.rot_off = mat;
+        mat += 2LL * d.rot_cap;
+        mat = (mat + 31) & ~31LL;  // 256-byte alignment of every cluster's workspace
+        d.it_cap = 8 * (int)n + 64;
+        d.it_off = its;
+        its += 3LL * d.it_cap;
+        d.eig_off = eig;
+        eig += n;
+    }
+    c->total_dim = eig;
+    c->arena_doubles = (size_t)mat;
+    c->order.resize(N);
+    std::iota(c->order.begin(), c->order.end(), 0);
+    std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) { return c->cl[a].n > c->cl[b].n; });
+
+    // ---- LNO storage offsets
+    std::vector<long long> voff(N + 1), loff(N + 1), moff(N + 1);
+    voff[0] = loff[0] = moff[0] = 0;
+    for (int i = 0; i < N; ++i) {
+        voff[i + 1] = voff[i] + (long long)c->norb[i] * k_lno;
+        loff[i + 1] = loff[i] + (long long)c->norb[i] * c->norb[i];
+        moff[i + 1] = moff[i] + c->norb[i];
+    }
+    c->v_total = voff[N];
+    c->l_total = loff[N];
+
+    // ---- device memory
+    size_t free_b = 0, tot_b = 0;
+    DCLNO_CUDA(c, cudaMemGetInfo(&free_b, &tot_b));
+    size_t need = c->arena_doubles * 8 + (size_t)its * 4 + (size_t)c->total_dim * 16 + (size_t)c->nnzb * 32;
+    if (need + (size_t)(1u << 30) > free_b) {
+        free_clusters(c);
+        return set_err(c, DCLNO_ERR_OOM,
+                       "workspace of " + std::to_string(need >> 20) + " MiB does not fit in free device memory");
+    }
+    dclno_status st;
+#define COPY(dst, vec)                                                                        \
+    st = copy_to_device(c, (void**)&(dst), (vec).data(), (vec).size() * sizeof((vec)[0]));   \
+    if (st != DCLNO_OK) {                                                                     \
+        free_clusters(c);                                                                     \
+        return st;                                                                            \
+    }
+    COPY(c->d_norb, c->norb);
+    COPY(c->d_row_ptr, c->row_ptr);
+    COPY(c->d_key, key);
+    COPY(c->d_blk_off, c->blk_off);
+    COPY(c->d_onsite, onsite);
+    COPY(c->d_voff, voff);
+    COPY(c->d_loff, loff);
+    COPY(c->d_moff, moff);
+    COPY(c->d_cl, c->cl);
+    COPY(c->d_order, c->order);
+    COPY(c->d_mem, c->mem);
+    COPY(c->d_mem_cl, mem_cl);
+    COPY(c->d_rowblk_member, rowblk_member);
+#undef COPY
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_status, sizeof(int) * N)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_arena, c->arena_doubles * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_iters, sizeof(int) * std::max<long long>(its, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_eps, sizeof(double) * c->total_dim)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_q, sizeof(double) * c->total_dim)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_V, sizeof(double) * std::max<long long>(c->v_total, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_lam_re, sizeof(double) * moff[N])) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_lam_im, sizeof(double) * moff[N])) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_Lambda, sizeof(double) * std::max<long long>(loff[N], 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_lflags, sizeof(int) * N)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_eband, sizeof(double) * N)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_scalars, sizeof(double) * 64)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_mu_work, sizeof(double) * 4096 * 8)) != cudaSuccess) {
+        free_clusters(c);
+        return cuda_err(c, e, "cudaMalloc (cluster workspace)");
+    }
+    c->built = true;
+    c->lnos_ready = !c->has_lno_region;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_compute_lnos(dclno_ctx* c, const double* rho) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_compute_lnos: build clusters first");
+    if (!c->has_lno_region) {
+        c->lnos_ready = true;
+        return DCLNO_OK;
+    }
+    if (!rho) return set_err(c, DCLNO_ERR_ARG, "dclno_compute_lnos: rho is NULL");
+    dclno_status st = launch_lambda_lno(c, rho);
+    if (st != DCLNO_OK) return st;
+    c->lnos_ready = true;
+    c->solved = false;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_solve_clusters(dclno_ctx* c, dclno_precision prec) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: build clusters first");
+    if (!c->lnos_ready) return set_err(c, DCLNO_ERR_NO_LNOS, "dclno_solve_clusters: compute LNOs first");
+    if (prec != DCLNO_FP64)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: only DCLNO_FP64 is available in this build");
+    dclno_status st = launch_assemble(c);
+    if (st != DCLNO_OK) return st;
+    st = launch_solve_fp64(c);
+    if (st != DCLNO_OK) return st;
+    c->solved = true;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, double* nelec_out) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->solved) return set_err(c, DCLNO_ERR_ARG, "dclno_find_mu: solve clusters first");
+    if (!(kT > 0.0)) return set_err(c, DCLNO_ERR_ARG, "dclno_find_mu: kT must be positive");
+    double mu = 0, nmu = 0;
+    dclno_status st = launch_find_mu(c, ne, kT, &mu, &nmu);
+    if (mu_out) *mu_out = mu;
+    if (nelec_out) *nelec_out = nmu;
+    return st;
+}
+
+extern "C" dclno_status dclno_density_matrix(dclno_ctx* c, double mu, double kT, double* rho_out,
+                                             double* eband_out) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->solved) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix: solve clusters first");
+    if (!(kT > 0.0) || !rho_out) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix: bad kT or rho_out");
+    return launch_density(c, mu, kT, rho_out, eband_out);
+}
+
+extern "C" dclno_status dclno_step(dclno_ctx* c, const double* rho_in, double* rho_out, int host_buffers,
+                                   dclno_precision prec, double ne, double kT, double* mu_out,
+                                   double* nelec_out, double* eband_out) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_step: build clusters first");
+    if (!rho_out || (!rho_in && c->has_lno_region)) return set_err(c, DCLNO_ERR_ARG, "dclno_step: null rho");
+    const double* rin = rho_in;
+    double* rout = rho_out;
+    const size_t bytes = (size_t)c->nval * sizeof(double);
+    if (host_buffers) {
+        if (!c->d_rho_in) DCLNO_CUDA(c, cudaMalloc(&c->d_rho_in, bytes));
+        if (!c->d_rho_out) DCLNO_CUDA(c, cudaMalloc(&c->d_rho_out, bytes));
+        if (rho_in) DCLNO_CUDA(c, cudaMemcpyAsync(c->d_rho_in, rho_in, bytes, cudaMemcpyHostToDevice, c->stream));
+        rin = c->d_rho_in;
+        rout = c->d_rho_out;
+    }
+    dclno_status st = dclno_compute_lnos(c, rin);
+    if (st == DCLNO_OK) st = dclno_solve_clusters(c, prec);
+    double mu = 0;
+    if (st == DCLNO_OK) st = dclno_find_mu(c, ne, kT, &mu, nelec_out);
+    if (st == DCLNO_OK) st = dclno_density_matrix(c, mu, kT, rout, eband_out);
+    if (st != DCLNO_OK) return st;
+    if (mu_out) *mu_out = mu;
+    if (host_buffers) {
+        DCLNO_CUDA(c, cudaMemcpyAsync(rho_out, rout, bytes, cudaMemcpyDeviceToHost, c->stream));
+        DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_cluster_info(dclno_ctx* c, int* dims, int* nmem, long long* total) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_cluster_info: build clusters first");
+    for (int i = 0; i < c->N; ++i) {
+        if (dims) dims[i] = c->cl[i].n;
+        if (nmem) nmem[i] = c->cl[i].nmem;
+    }
+    if (total) *total = c->total_dim;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_get_spectrum(dclno_ctx* c, double* eps, double* q) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->solved) return set_err(c, DCLNO_ERR_ARG, "dclno_get_spectrum: solve clusters first");
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (eps) DCLNO_CUDA(c, cudaMemcpy(eps, c->d_eps, sizeof(double) * c->total_dim, cudaMemcpyDeviceToHost));
+    if (q) DCLNO_CUDA(c, cudaMemcpy(q, c->d_q, sizeof(double) * c->total_dim, cudaMemcpyDeviceToHost));
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_get_lnos(dclno_ctx* c, double* V, double* lre, double* lim, int* flags) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->built || !c->has_lno_region || !c->lnos_ready)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_get_lnos: no LNOs computed");
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    long long msum = 0;
+    for (int i = 0; i < c->N; ++i) msum += c->norb[i];
+    if (V) DCLNO_CUDA(c, cudaMemcpy(V, c->d_V, sizeof(double) * c->v_total, cudaMemcpyDeviceToHost));
+    if (lre) DCLNO_CUDA(c, cudaMemcpy(lre, c->d_lam_re, sizeof(double) * msum, cudaMemcpyDeviceToHost));
+    if (lim) DCLNO_CUDA(c, cudaMemcpy(lim, c->d_lam_im, sizeof(double) * msum, cudaMemcpyDeviceToHost));
+    if (flags) DCLNO_CUDA(c, cudaMemcpy(flags, c->d_lflags, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    return DCLNO_OK;
+}

@@ -1,0 +1,301 @@
+// Internal declarations of libdclno: device descriptors, the context, and the
+// CTA-wide FP64 tile GEMM that the cluster solver's cubic steps share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/dclno.h"
+
+#define DCLNO_MAX_M 32          // largest basis of one atom (M_i)
+#define DCLNO_MAX_M_LNO 16      // largest basis of an atom that carries LNOs
+#define DCLNO_NB 32             // panel width of the blocked FP64 factorisations
+#define DCLNO_SOLVE_THREADS 256 // threads of a per-cluster CTA
+
+// ---------------------------------------------------------------------------
+// Device descriptors
+// ---------------------------------------------------------------------------
+struct ClusterDesc {
+    int centre;         // atom i
+    int n;              // cluster dimension n_i
+    int ld;             // leading dimension of the n x n work matrices (multiple of 4)
+    int nmem;           // members (the centre is the last)
+    long long mbeg;     // first member in the member arrays
+    long long mat_off;  // arena offset (doubles) of the H^(i)/A matrix; S^(i)/L follows at + n*ld
+    long long eig_off;  // offset into eps/q (sum of earlier n)
+    long long cc_off;   // arena offset of the central rows C_c (M_i x n), then P2 (M_i x n)
+    long long rot_off;  // arena offset of the QL rotation log (2 doubles per rotation)
+    long long it_off;   // offset (ints) of the QL sweep headers (3 ints per sweep)
+    long long aux_off;  // arena offset of per-cluster vectors d, e, tau (ld each) and W (32 ld)
+    int rot_cap;        // capacity of the rotation log
+    int it_cap;         // capacity of the sweep headers
+    int mc;             // M of the central atom
+    int pad;
+};
+
+struct MemberDesc {
+    int atom;   // j
+    int shift;  // packed cell shift (see pack_shift)
+    int off;    // first basis function of the member in the cluster basis
+    int core;   // 1 = PAO member (M_j functions), 0 = LNO member (k functions)
+};
+
+// cell shift (three signed bytes) packed into 24 bits of an int
+__host__ __device__ inline int pack_shift(int s0, int s1, int s2) {
+    return ((s0 + 128) << 16) | ((s1 + 128) << 8) | (s2 + 128);
+}
+__host__ __device__ inline void unpack_shift(int p, int& s0, int& s1, int& s2) {
+    s0 = ((p >> 16) & 255) - 128;
+    s1 = ((p >> 8) & 255) - 128;
+    s2 = (p & 255) - 128;
+}
+// BSR search key of a block: (col, packed shift) as one sortable 64-bit integer
+__host__ __device__ inline long long block_key(int col, int pshift) {
+    return ((long long)col << 24) | (long long)pshift;
+}
+
+// Per-cluster status words written by kernels (0 = ok).
+enum : int {
+    ST_OK = 0,
+    ST_NOT_SPD = 1,
+    ST_NOT_CONVERGED = 2,
+    ST_LOG_FULL = 3,
+    ST_BAD_LNO = 4,
+};
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct dclno_ctx {
+    cudaStream_t stream = nullptr;
+    std::string err;
+    long long launches = 0;
+    int device = 0;
+
+    // system (host copies of the structure, device pointers of the values)
+    int N = 0;
+    long long nnzb = 0, nval = 0;
+    std::vector<int> norb;
+    std::vector<long long> row_ptr, blk_off;
+    std::vector<int> col;
+    std::vector<int> pshift;  // packed shifts
+    std::vector<double> pos, cell;
+    int pbc[3] = {0, 0, 0};
+    const double* H = nullptr;
+    const double* S = nullptr;
+    int* d_norb = nullptr;
+    long long* d_row_ptr = nullptr;
+    long long* d_key = nullptr;        // block_key per block
+    long long* d_blk_off = nullptr;
+    long long* d_onsite = nullptr;     // block index of S_ii per atom
+    long long* d_voff = nullptr;       // offset of atom i's LNO block (M_i x k) in d_V
+    long long* d_loff = nullptr;       // offset of atom i's Lambda block (M_i^2)
+    long long* d_moff = nullptr;       // offset of atom i's eigenvalues lambda (M_i)
+
+    // clusters
+    bool built = false;
+    double r_core = 0, r_lno = 0;
+    int k_lno = 0;
+    bool has_lno_region = false;
+    std::vector<ClusterDesc> cl;      // one per atom, atom order
+    std::vector<int> order;           // clusters by decreasing n (scheduling)
+    std::vector<MemberDesc> mem;
+    long long total_dim = 0;
+    ClusterDesc* d_cl = nullptr;
+    int* d_order = nullptr;
+    MemberDesc* d_mem = nullptr;
+    int* d_mem_cl = nullptr;           // cluster of each member (atom order)
+    int* d_rowblk_member = nullptr;    // per block of row i: member of cluster i or -1
+    int* d_status = nullptr;           // per cluster
+    double* d_arena = nullptr;
+    size_t arena_doubles = 0;
+    int* d_iters = nullptr;            // QL sweep headers
+    double* d_eps = nullptr;
+    double* d_q = nullptr;
+
+    // LNOs
+    bool lnos_ready = false;
+    long long v_total = 0, l_total = 0;
+    double* d_V = nullptr;
+    double* d_lam_re = nullptr;
+    double* d_lam_im = nullptr;
+    double* d_Lambda = nullptr;
+    int* d_lflags = nullptr;
+
+    // solve / mu
+    bool solved = false;
+    double* d_mu_work = nullptr;       // k-section partial sums
+    double* d_scalars = nullptr;       // [lo, hi, mu, N, ...]
+    double* d_eband = nullptr;         // per-cluster band energies
+
+    // host-buffer step
+    double* d_rho_in = nullptr;
+    double* d_rho_out = nullptr;
+
+    // optional per-kernel CUDA-event timing (dclno_set_profiling)
+    struct Prof {
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+        double ms = 0.0;
+        long long launches = 0;
+    };
+    bool prof_on = false;
+    std::map<std::string, Prof> prof;
+};
+
+// Event pair around one launch when profiling is on (no-op otherwise).
+struct ProfScope {
+    dclno_ctx* c;
+    const char* name;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(dclno_ctx* ctx, const char* n) : c(ctx), name(n) {
+        if (c->prof_on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+            cudaEventRecord(e0, c->stream);
+    }
+    ~ProfScope() {
+        if (e1) {
+            cudaEventRecord(e1, c->stream);
+            c->prof[name].pending.push_back({e0, e1});
+        }
+    }
+};
+void prof_collect(dclno_ctx* c);
+
+// ---------------------------------------------------------------------------
+// Error helpers
+// ---------------------------------------------------------------------------
+dclno_status set_err(dclno_ctx* c, dclno_status st, const std::string& msg);
+dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where);
+#define DCLNO_CUDA(ctx, call)                                            \
+    do {                                                                 \
+        cudaError_t e__ = (call);                                        \
+        if (e__ != cudaSuccess) return cuda_err((ctx), e__, #call);      \
+    } while (0)
+#define DCLNO_LAUNCHED(ctx)                                              \
+    do {                                                                 \
+        (ctx)->launches++;                                               \
+        cudaError_t e__ = cudaGetLastError();                            \
+        if (e__ != cudaSuccess) return cuda_err((ctx), e__, "launch");   \
+    } while (0)
+
+// kernels' host-side launchers (one per .cu file)
+dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
+dclno_status launch_assemble(dclno_ctx* c);
+dclno_status launch_solve_fp64(dclno_ctx* c);
+dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
+dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One FP64 tensor-core MMA: D(8x8) += A(8x4, row) * B(4x8, col).
+// Fragments (per lane l): a = A[l/4][l%4], b = B[l%4][l/4],
+// c = {C[l/4][2(l%4)], C[l/4][2(l%4)+1]}.
+__device__ __forceinline__ void dmma_8x8x4(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+// Shared-memory tile geometry of cta_gemm_nt: 64 x 64 outputs, K chunks of 32,
+// rows padded to 36 doubles so that the 16 lanes of a half-warp hit distinct banks.
+#define GT_M 64
+#define GT_N 64
+#define GT_K 32
+#define GT_LD 36
+#define GT_SMEM_DOUBLES (2 * 64 * GT_LD)
+
+// C[M x N] -= A[M x K] * B[N x K]^T over the whole CTA (256 threads), all
+// row-major in global memory with leading dimensions lda, ldb, ldc (multiples
+// of 2 doubles, base pointers 16-byte aligned).  With LOWER, only elements with
+// (row + diag) >= col are written and tiles wholly above that line are skipped.
+// smem must hold GT_SMEM_DOUBLES doubles.  Ends with __syncthreads().
+template <bool LOWER>
+__device__ void cta_gemm_nt_sub(double* __restrict__ C, int ldc, const double* __restrict__ A, int lda,
+                                const double* __restrict__ B, int ldb, int M, int N, int K, int diag,
+                                double* smem) {
+    double* As = smem;
+    double* Bs = smem + GT_M * GT_LD;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wr = (warp >> 1) * 16;  // warp's row offset in the tile (0,16,32,48)
+    const int wc = (warp & 1) * 32;   // warp's col offset (0,32)
+    const int fr = lane >> 2, fk = lane & 3;
+    const int tilesM = (M + GT_M - 1) / GT_M, tilesN = (N + GT_N - 1) / GT_N;
+    for (int t = 0; t < tilesM * tilesN; ++t) {
+        const int ti = t / tilesN, tj = t % tilesN;
+        const int r0 = ti * GT_M, c0 = tj * GT_N;
+        if (LOWER && r0 + GT_M - 1 + diag < c0) continue;  // uniform across the CTA
+        double acc[2][4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+        for (int k0 = 0; k0 < K; k0 += GT_K) {
+            // stage A[r0:r0+64, k0:k0+32] and B[c0:c0+64, k0:k0+32] (zero-filled)
+            for (int e = tid; e < GT_M * GT_K / 2; e += blockDim.x) {
+                const int r = e / (GT_K / 2), kk = (e % (GT_K / 2)) * 2;
+                double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+                const int gk = k0 + kk;
+                if (r0 + r < M) {
+                    const double* p = A + (size_t)(r0 + r) * lda + gk;
+                    if (gk + 1 < K) va = *reinterpret_cast<const double2*>(p);
+                    else if (gk < K) va.x = p[0];
+                }
+                if (c0 + r < N) {
+                    const double* p = B + (size_t)(c0 + r) * ldb + gk;
+                    if (gk + 1 < K) vb = *reinterpret_cast<const double2*>(p);
+                    else if (gk < K) vb.x = p[0];
+                }
+                As[r * GT_LD + kk] = va.x;
+                As[r * GT_LD + kk + 1] = va.y;
+                Bs[r * GT_LD + kk] = vb.x;
+                Bs[r * GT_LD + kk + 1] = vb.y;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GT_K; kk += 4) {
+                double a[2], b[4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) a[i] = As[(wr + 8 * i + fr) * GT_LD + kk + fk];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[(wc + 8 * j + fr) * GT_LD + kk + fk];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dmma_8x8x4(acc[i][j][0], acc[i][j][1], a[i], b[j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = r0 + wr + 8 * i + fr;
+            if (r >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = c0 + wc + 8 * j + 2 * fk + h;
+                    if (cc >= N) continue;
+                    if (LOWER && r + diag < cc) continue;
+                    C[(size_t)r * ldc + cc] -= acc[i][j][h];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+#endif  // __CUDACC__

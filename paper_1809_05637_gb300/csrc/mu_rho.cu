@@ -1,0 +1,407 @@
+// Common chemical potential (Sec. II.C step (iv)) and density-matrix rows of the
+// central atoms (Eq. (dm) with the spectral Green function of Eq. (Gi)).
+//
+// mu: device-wide k-section of N(mu) = 2 sum f((eps - mu)/kT) q = N_e over all
+//     clusters' (eps, q) pairs; each pass evaluates KSEC interior points of the
+//     current bracket, a fixed-order reduction picks the sub-interval.
+// rho rows: with G = F C_c^T (n x M_i, F = diag f(eps)), the rows are
+//     rho_c,:^T = L^-T Q Z G: reverse replay of the QL rotations (Z G), the
+//     Householder reflectors from the left (Q .), back substitution with L^T,
+//     then LNO columns are returned to PAOs through V_j and scattered into the
+//     BSR pattern of row i.
+#include <cmath>
+
+#include "dclno_internal.cuh"
+
+#define KSEC 3          // interior points per k-section pass
+#define MU_BLOCKS 1024  // partial-sum blocks per pass
+#define MU_PASSES 40
+
+// f(x) = 1/(1+e^x) without overflow
+__device__ __forceinline__ double fermi(double x) {
+    if (x > 0.0) {
+        if (x > 745.0) return 0.0;
+        const double e = exp(-x);
+        return e / (1.0 + e);
+    }
+    if (x < -745.0) return 1.0;
+    return 1.0 / (1.0 + exp(x));
+}
+
+// scal: [0] lo, [1] hi, [2] mu (result), [3] N(mu), [4] done flag, [5] kT, [6] N_e
+__global__ void k_mu_bracket(long long total, const double* __restrict__ eps, double* __restrict__ part) {
+    __shared__ double mn[256], mx[256];
+    double a = 1e300, b = -1e300;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        a = fmin(a, eps[t]);
+        b = fmax(b, eps[t]);
+    }
+    mn[threadIdx.x] = a;
+    mx[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + s]);
+            mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = mn[0];
+        part[2 * blockIdx.x + 1] = mx[0];
+    }
+}
+
+__global__ void k_mu_init(int nblk, const double* __restrict__ part, double* __restrict__ scal, double kT, double ne) {
+    double a = 1e300, b = -1e300;
+    for (int t = 0; t < nblk; ++t) {
+        a = fmin(a, part[2 * t]);
+        b = fmax(b, part[2 * t + 1]);
+    }
+    scal[0] = a - 40.0 * kT;
+    scal[1] = b + 40.0 * kT;
+    scal[2] = 0.5 * (scal[0] + scal[1]);
+    scal[4] = 0.0;
+    scal[5] = kT;
+    scal[6] = ne;
+}
+
+// partial sums of N at the bracket's end points (first pass) and KSEC interior points
+__global__ void k_mu_partial(long long total, const double* __restrict__ eps, const double* __restrict__ q,
+                             const double* __restrict__ scal, double* __restrict__ part, int with_ends) {
+    if (scal[4] != 0.0) return;
+    const double lo = scal[0], hi = scal[1], kT = scal[5];
+    const int np = KSEC + 2;
+    double mu[KSEC + 2], acc[KSEC + 2];
+#pragma unroll
+    for (int p = 0; p < np; ++p) {
+        mu[p] = lo + (hi - lo) * (double)p / (KSEC + 1);
+        acc[p] = 0.0;
+    }
+    const double inv = 1.0 / kT;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const double e = eps[t], w = q[t];
+#pragma unroll
+        for (int p = 0; p < np; ++p) {
+            if (!with_ends && (p == 0 || p == np - 1)) continue;
+            acc[p] = fma(fermi((e - mu[p]) * inv), w, acc[p]);
+        }
+    }
+    __shared__ double red[KSEC + 2][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int p = 0; p < np; ++p) {
+        double v = warp_sum(acc[p]);
+        if (lane == 0) red[p][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        part[(size_t)blockIdx.x * np + threadIdx.x] = s;
+    }
+}
+
+// fixed-order reduction of the partial sums; narrows [lo, hi]; status in scal[7]
+__global__ void k_mu_update(int nblk, const double* __restrict__ part, double* __restrict__ scal, int first, int last) {
+    if (threadIdx.x != 0) return;
+    const int np = KSEC + 2;
+    if (scal[4] != 0.0) return;
+    const double lo = scal[0], hi = scal[1], ne = scal[6];
+    double N[KSEC + 2];
+    for (int p = 0; p < np; ++p) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * np + p];
+        N[p] = 2.0 * s;
+    }
+    if (first) {
+        scal[8] = N[0];
+        scal[9] = N[np - 1];
+        if (!(N[0] <= ne && ne <= N[np - 1])) {
+            scal[4] = 2.0;  // no bracket
+            return;
+        }
+    }
+    const double tol = 1e-12 * fabs(ne);
+    for (int p = 1; p <= KSEC; ++p) {
+        const double mu = lo + (hi - lo) * (double)p / (KSEC + 1);
+        if (fabs(N[p] - ne) <= tol) {
+            scal[2] = mu;
+            scal[3] = N[p];
+            scal[4] = 1.0;
+            return;
+        }
+    }
+    int p = 1;
+    while (p <= KSEC && N[p] < ne) ++p;  // first interior point with N >= ne
+    const double nlo = lo + (hi - lo) * (double)(p - 1) / (KSEC + 1);
+    const double nhi = lo + (hi - lo) * (double)p / (KSEC + 1);
+    scal[0] = nlo;
+    scal[1] = nhi;
+    const double mid = 0.5 * (nlo + nhi);
+    scal[2] = mid;
+    if (last || !(nlo < mid && mid < nhi)) scal[4] = 3.0;  // bracket exhausted in double precision
+}
+
+// N(mu) at the final mu (exact re-evaluation, one point)
+__global__ void k_mu_final_partial(long long total, const double* __restrict__ eps, const double* __restrict__ q,
+                                   const double* __restrict__ scal, double* __restrict__ part) {
+    const double mu = scal[2], inv = 1.0 / scal[5];
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+        acc = fma(fermi((eps[t] - mu) * inv), q[t], acc);
+    __shared__ double red[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_mu_final(int nblk, const double* __restrict__ part, double* __restrict__ scal) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[b];
+    scal[3] = 2.0 * s;
+}
+
+dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, double* nmu_out) {
+    const long long total = c->total_dim;
+    const int nblk = MU_BLOCKS;
+    {
+        ProfScope ps__(c, "k_mu_bracket");
+        k_mu_bracket<<<nblk, 256, 0, c->stream>>>(total, c->d_eps, c->d_mu_work);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_mu_init");
+        k_mu_init<<<1, 1, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, kT, ne);
+    }
+    DCLNO_LAUNCHED(c);
+    for (int pass = 0; pass < MU_PASSES; ++pass) {
+        {
+            ProfScope ps__(c, "k_mu_partial");
+            k_mu_partial<<<nblk, 256, 0, c->stream>>>(total, c->d_eps, c->d_q, c->d_scalars, c->d_mu_work, pass == 0);
+        }
+        DCLNO_LAUNCHED(c);
+        {
+            ProfScope ps__(c, "k_mu_update");
+            k_mu_update<<<1, 32, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, pass == 0, pass == MU_PASSES - 1);
+        }
+        DCLNO_LAUNCHED(c);
+    }
+    {
+        ProfScope ps__(c, "k_mu_final_partial");
+        k_mu_final_partial<<<nblk, 256, 0, c->stream>>>(total, c->d_eps, c->d_q, c->d_scalars, c->d_mu_work);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_mu_final");
+        k_mu_final<<<1, 32, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars);
+    }
+    DCLNO_LAUNCHED(c);
+    double h[10];
+    DCLNO_CUDA(c, cudaMemcpyAsync(h, c->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h[4] == 2.0) {
+        char b[160];
+        snprintf(b, sizeof b, "dclno_find_mu: N_e = %.17g outside [%.17g, %.17g]", ne, h[8], h[9]);
+        return set_err(c, DCLNO_ERR_NO_BRACKET, b);
+    }
+    *mu_out = h[2];
+    *nmu_out = h[3];
+    return DCLNO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Density-matrix rows
+// ---------------------------------------------------------------------------
+// G[mu][a] = f(eps_mu) C_c[a][mu] (stored [n][mc] in the cluster's W area); band energy
+__global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double* __restrict__ arena,
+                           const double* __restrict__ eps, const double* __restrict__ q, double mu, double kT,
+                           double* __restrict__ eband) {
+    const int ci = blockIdx.x;
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, mc = d.mc;
+    const double* P = arena + d.cc_off;
+    double* G = arena + d.aux_off + 3 * d.ld;
+    const double inv = 1.0 / kT;
+    double eb = 0.0;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const double e = eps[d.eig_off + m];
+        const double f = fermi((e - mu) * inv);
+        eb = fma(f * e, q[d.eig_off + m], eb);
+        for (int a = 0; a < mc; ++a) G[(size_t)m * mc + a] = f * P[(size_t)m * 2 * mc + a];
+    }
+    __shared__ double red[8];
+    eb = warp_sum(eb);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = eb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        eband[ci] = 2.0 * s;
+    }
+}
+
+// G <- Z G: the logged rotations in reverse order acting on rows (i, i+1)
+__global__ void k_replay_rev(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                             double* __restrict__ arena, const int* __restrict__ iters) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= ncl) return;
+    const ClusterDesc d = cls[order[wid]];
+    const int mc = d.mc;
+    if (lane >= mc) return;
+    double* G = arena + d.aux_off + 3 * d.ld;
+    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
+    const int* hdr = iters + d.it_off;
+    const int nsw = hdr[0];
+    for (int k = nsw - 1; k >= 0; --k) {
+        const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
+        if (cnt == 0) continue;
+        // rotations u = cnt-1 .. 0 act on (i, i+1) with i = i0 - u, i increasing
+        int i = i0 - (cnt - 1);
+        double wi = G[(size_t)i * mc + lane];
+        for (int u = cnt - 1; u >= 0; --u, ++i) {
+            const double2 cs = rot[start + u];
+            const double wi1 = G[(size_t)(i + 1) * mc + lane];
+            G[(size_t)i * mc + lane] = fma(cs.x, wi, cs.y * wi1);
+            wi = fma(-cs.y, wi, cs.x * wi1);
+        }
+        G[(size_t)i * mc + lane] = wi;
+    }
+}
+
+// G <- Q G = H_0 H_1 ... H_{n-3} G (reflectors applied from the last one), then
+// X = L^-T G by back substitution; X overwrites G.
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDesc* __restrict__ cls,
+                                                                const int* __restrict__ order,
+                                                                double* __restrict__ arena) {
+    extern __shared__ double sm[];
+    const ClusterDesc d = cls[order[blockIdx.x]];
+    const int n = d.n, ld = d.ld, mc = d.mc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* A = arena + d.mat_off;
+    const double* L = A + (size_t)n * ld;
+    const double* tau = arena + d.aux_off + 2 * ld;
+    double* G = arena + d.aux_off + 3 * ld;
+    double* vsh = sm;           // n
+    double* part = sm + n;      // nw x 32
+    for (int k = n - 3; k >= 0; --k) {
+        const double tk = tau[k];
+        if (tk == 0.0) continue;
+        for (int t = k + 1 + threadIdx.x; t < n; t += blockDim.x) vsh[t] = A[(size_t)t * ld + k];
+        __syncthreads();
+        double u = 0.0;
+        if (lane < mc)
+            for (int t = k + 1 + warp; t < n; t += nw) u = fma(vsh[t], G[(size_t)t * mc + lane], u);
+        part[warp * 32 + lane] = u;
+        __syncthreads();
+        if (lane < mc) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += part[w * 32 + lane];
+            s *= tk;
+            for (int t = k + 1 + warp; t < n; t += nw) G[(size_t)t * mc + lane] = fma(-s, vsh[t], G[(size_t)t * mc + lane]);
+        }
+        __syncthreads();
+    }
+    // L^T X = G: X[t] = G[t] / L[t][t]; then G[s] -= L[t][s] X[t] for s < t
+    for (int t = n - 1; t >= 0; --t) {
+        const double ltt = L[(size_t)t * ld + t];
+        if (threadIdx.x < mc) G[(size_t)t * mc + threadIdx.x] /= ltt;
+        __syncthreads();
+        const double* Lt = L + (size_t)t * ld;
+        for (int e = threadIdx.x; e < t * mc; e += blockDim.x) {
+            const int s = e / mc, a = e % mc;
+            G[(size_t)s * mc + a] = fma(-Lt[s], G[(size_t)t * mc + a], G[(size_t)s * mc + a]);
+        }
+        __syncthreads();
+    }
+}
+
+// scatter the rows of atom i into the BSR pattern; one warp per block of row i
+__global__ void k_rho_scatter(int N, const ClusterDesc* __restrict__ cls, const MemberDesc* __restrict__ mem,
+                              const int* __restrict__ norb, const long long* __restrict__ row_ptr,
+                              const long long* __restrict__ key, const long long* __restrict__ blk_off,
+                              const int* __restrict__ rowblk_member, const long long* __restrict__ voff, int k,
+                              const double* __restrict__ V, const double* __restrict__ arena,
+                              double* __restrict__ rho) {
+    const int i = blockIdx.y;
+    const ClusterDesc d = cls[i];
+    const int mc = d.mc;
+    const double* X = arena + d.aux_off + 3 * d.ld;  // [n][mc]
+    const int lane = threadIdx.x & 31;
+    const long long b0 = row_ptr[i], b1 = row_ptr[i + 1];
+    for (long long b = b0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < b1;
+         b += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const int j = (int)(key[b] >> 24), mj = norb[j];
+        double* out = rho + blk_off[b];
+        const int m = rowblk_member[b];
+        if (m < 0) {
+            for (int e = lane; e < mc * mj; e += 32) out[e] = 0.0;
+            continue;
+        }
+        const MemberDesc md = mem[d.mbeg + m];
+        if (md.core) {
+            for (int e = lane; e < mc * mj; e += 32) {
+                const int a = e / mj, bb = e % mj;
+                out[e] = X[(size_t)(md.off + bb) * mc + a];
+            }
+        } else {
+            const double* Vj = V + voff[j];
+            for (int e = lane; e < mc * mj; e += 32) {
+                const int a = e / mj, bb = e % mj;
+                double s = 0.0;
+                for (int g = 0; g < k; ++g) s = fma(X[(size_t)(md.off + g) * mc + a], Vj[bb * k + g], s);
+                out[e] = s;
+            }
+        }
+    }
+}
+
+dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband_out) {
+    const int N = c->N;
+    int maxn = 0;
+    long long maxrow = 0;
+    for (const auto& d : c->cl) maxn = std::max(maxn, d.n);
+    for (int i = 0; i < N; ++i) maxrow = std::max(maxrow, c->row_ptr[i + 1] - c->row_ptr[i]);
+    {
+        ProfScope ps__(c, "k_rho_prep");
+        k_rho_prep<<<N, 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu, kT, c->d_eband);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_replay_rev");
+        k_replay_rev<<<(N * 32 + 127) / 128, 128, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters);
+    }
+    DCLNO_LAUNCHED(c);
+    const size_t sm = (size_t)(maxn + 32 * (DCLNO_SOLVE_THREADS / 32)) * sizeof(double);
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_rho_qx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+        ProfScope ps__(c, "k_rho_qx");
+        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order, c->d_arena);
+    }
+    DCLNO_LAUNCHED(c);
+    const int wpb = 8;
+    const int bx = (int)std::min<long long>((maxrow + wpb - 1) / wpb, 64);
+    {
+        ProfScope ps__(c, "k_rho_scatter");
+        k_rho_scatter<<<dim3(bx, N), wpb * 32, 0, c->stream>>>(N, c->d_cl, c->d_mem, c->d_norb, c->d_row_ptr, c->d_key,
+                                                          c->d_blk_off, c->d_rowblk_member, c->d_voff, c->k_lno,
+                                                          c->d_V, c->d_arena, rho_out);
+    }
+    DCLNO_LAUNCHED(c);
+    if (eband_out) {
+        std::vector<double> eb(N);
+        DCLNO_CUDA(c, cudaMemcpyAsync(eb.data(), c->d_eband, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+        DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+        double s = 0.0;
+        for (int i = 0; i < N; ++i) s += eb[i];
+        *eband_out = s;
+    }
+    return DCLNO_OK;
+}

@@ -1,0 +1,586 @@
+// FP64 solver of the truncated-cluster eigenproblems H^(i) c = eps S^(i) c
+// (Sec. II.C step (iii)), batched over all clusters.
+//
+//   k_cholesky     S^(i) = L L^T                 blocked right-looking, DMMA trailing updates
+//   k_congruence   A = L^-1 H^(i) L^-T           two blocked right-side triangular solves
+//   k_tridiag      A = Q T Q^T                   blocked Householder (DFMA symv, DMMA rank-2k)
+//   k_ql           T = Z Theta Z^T               implicit QL; rotations logged, not accumulated
+//   k_apply_q_rows P <- P Q                       central rows [L_cc^-T | L_c,:] times Q
+//   k_replay_fwd   P <- P Z                       the logged rotations applied to P's columns
+//   k_weights      q_mu = sum_a (C_c)_{a mu} (S C)_{c a, mu}, eigenvalues out
+//
+// The central atom is the last member of its cluster, so the central rows of
+// C = L^-T Q Z are L_cc^-T (Q Z)_c and those of S C = L Q Z are L_c,: Q Z: both
+// need only the M_i x n strips, never the full eigenvector matrix (Eq. (Gi) is
+// evaluated through these strips).
+#include "dclno_internal.cuh"
+
+#define NB DCLNO_NB
+#define DK_LD 33
+
+// x L_kk^T = h for rows [r0, r1) of M (columns kb .. kb+nb-1), L_kk in smem (lower),
+// reciprocals of its diagonal in invd.
+__device__ static void panel_solve_rows(double* M, int ld, int kb, int nb, int r0, int r1, const double* Dk,
+                                        const double* invd) {
+    for (int r = r0 + (int)threadIdx.x; r < r1; r += blockDim.x) {
+        double x[NB];
+        double* row = M + (size_t)r * ld + kb;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) x[j] = (j < nb) ? row[j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j < nb) {
+                double s = x[j];
+#pragma unroll
+                for (int t = 0; t < j; ++t) s = fma(-x[t], Dk[j * DK_LD + t], s);
+                x[j] = s * invd[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j < nb) row[j] = x[j];
+    }
+}
+
+// load the lower triangle of the factor's diagonal block into smem and form 1/diag
+__device__ static void load_diag_block(const double* L, int ld, int kb, int nb, double* Dk, double* invd) {
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Dk[r * DK_LD + c] = (r < nb && c <= r) ? L[(size_t)(kb + r) * ld + kb + c] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) invd[threadIdx.x] = 1.0 / Dk[threadIdx.x * DK_LD + threadIdx.x];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of S^(i) in place (lower); sets ST_NOT_SPD on a non-positive pivot.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_cholesky(const ClusterDesc* __restrict__ cls,
+                                                                  const int* __restrict__ order,
+                                                                  double* __restrict__ arena,
+                                                                  int* __restrict__ status) {
+    extern __shared__ double sm[];
+    double* Dk = sm;                   // NB x DK_LD
+    double* invd = sm + NB * DK_LD;    // NB
+    double* G = invd + NB;             // GEMM tiles
+    __shared__ int fail;
+    const int ci = order[blockIdx.x];
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, ld = d.ld;
+    double* L = arena + d.mat_off + (size_t)n * ld;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) fail = 0;
+    for (int kb = 0; kb < n; kb += NB) {
+        const int nb = min(NB, n - kb);
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            const int r = e / NB, c = e % NB;
+            Dk[r * DK_LD + c] = (r < nb && c <= r) ? L[(size_t)(kb + r) * ld + kb + c] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int j = 0; j < nb; ++j) {
+                const double djj = Dk[j * DK_LD + j];
+                if (!(djj > 0.0)) {
+                    if (lane == 0) fail = 1;
+                    break;
+                }
+                const double ljj = sqrt(djj), inv = 1.0 / ljj;
+                __syncwarp();
+                if (lane == j) {
+                    Dk[j * DK_LD + j] = ljj;
+                    invd[j] = inv;
+                }
+                if (lane > j && lane < nb) Dk[lane * DK_LD + j] *= inv;
+                __syncwarp();
+                if (lane > j && lane < nb) {
+                    const double lij = Dk[lane * DK_LD + j];
+                    for (int t = j + 1; t <= lane; ++t) Dk[lane * DK_LD + t] -= lij * Dk[t * DK_LD + j];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (fail) {
+            if (threadIdx.x == 0) status[ci] = ST_NOT_SPD;
+            return;
+        }
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            const int r = e / nb, c = e % nb;
+            if (c <= r) L[(size_t)(kb + r) * ld + kb + c] = Dk[r * DK_LD + c];
+        }
+        panel_solve_rows(L, ld, kb, nb, kb + nb, n, Dk, invd);
+        __syncthreads();
+        const int m2 = n - kb - nb;
+        if (m2 > 0) {
+            double* P = L + (size_t)(kb + nb) * ld + kb;
+            cta_gemm_nt_sub<true>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G);
+        }
+    }
+    if (threadIdx.x == 0) status[ci] = ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A = L^-1 H L^-T, lower triangle valid on exit (in place of H^(i)).
+// Y = H L^-T (all rows), transpose, then A = Y^T L^-T restricted to the lower part.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_congruence(const ClusterDesc* __restrict__ cls,
+                                                                    const int* __restrict__ order,
+                                                                    double* __restrict__ arena,
+                                                                    const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    double* Dk = sm;
+    double* invd = sm + NB * DK_LD;
+    double* G = invd + NB;
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, ld = d.ld;
+    double* A = arena + d.mat_off;
+    const double* L = A + (size_t)n * ld;
+    for (int kb = 0; kb < n; kb += NB) {
+        const int nb = min(NB, n - kb);
+        load_diag_block(L, ld, kb, nb, Dk, invd);
+        panel_solve_rows(A, ld, kb, nb, 0, n, Dk, invd);
+        __syncthreads();
+        const int n2 = n - kb - nb;
+        if (n2 > 0) cta_gemm_nt_sub<false>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G);
+    }
+    // in-place transpose
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = 1 + warp; r < n; r += nw) {
+        for (int c = lane; c < r; c += 32) {
+            const double a = A[(size_t)r * ld + c], b = A[(size_t)c * ld + r];
+            A[(size_t)r * ld + c] = b;
+            A[(size_t)c * ld + r] = a;
+        }
+    }
+    __syncthreads();
+    for (int kb = 0; kb < n; kb += NB) {
+        const int nb = min(NB, n - kb);
+        load_diag_block(L, ld, kb, nb, Dk, invd);
+        panel_solve_rows(A, ld, kb, nb, kb, n, Dk, invd);
+        __syncthreads();
+        const int m2 = n - kb - nb;
+        if (m2 > 0) {
+            double* C = A + (size_t)(kb + nb) * ld + kb + nb;
+            cta_gemm_nt_sub<true>(C, ld, A + (size_t)(kb + nb) * ld + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, m2, m2,
+                                  nb, 0, G);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation of the lower triangle of A (blocked, panels of NB).
+// On exit: d (diagonal), e (sub-diagonal), tau; reflector k is (1, A[k+2:, k]) acting
+// on rows k+1.. (A[k+1][k] holds the unit element).
+// ---------------------------------------------------------------------------
+__device__ static double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDesc* __restrict__ cls,
+                                                                 const int* __restrict__ order,
+                                                                 double* __restrict__ arena,
+                                                                 const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, ld = d.ld;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double* A = arena + d.mat_off;
+    double* dv = arena + d.aux_off;  // sub-regions padded to ld (16-byte aligned)
+    double* ev = dv + ld;
+    double* tauv = dv + 2 * ld;
+    double* W = dv + 3 * ld;  // n x NB
+    double* vs = sm;                  // n
+    double* ys = sm + n;              // n
+    double* yw = sm + 2 * n;          // nw x n
+    double* red = yw + (size_t)nw * n;  // 2*NB + 32
+    double* pc = red + 32;            // NB: W^T v
+    double* sc = pc + NB;             // NB: V^T v
+    double* G = sm;                   // GEMM tiles alias the vectors between panels
+
+    for (int e = threadIdx.x; e < nw * n; e += blockDim.x) yw[e] = 0.0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += NB) {
+        const int nb = min(NB, n - c0);
+        for (int j = 0; j < nb; ++j) {
+            const int c = c0 + j;
+            // (1) bring column c up to date with the panel's earlier reflectors
+            if (j > 0) {
+                for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+                    double s = 0.0;
+                    for (int t = 0; t < j; ++t)
+                        s = fma(A[(size_t)r * ld + c0 + t], W[(size_t)c * NB + t],
+                                fma(W[(size_t)r * NB + t], A[(size_t)c * ld + c0 + t], s));
+                    A[(size_t)r * ld + c] -= s;
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) dv[c] = A[(size_t)c * ld + c];
+            if (c >= n - 1) break;
+            // (2) reflector for A[c+1:, c]; alpha is read before the barriers of block_sum,
+            // which thread 0's overwrite of this element with the unit entry follows
+            const double alpha = A[(size_t)(c + 1) * ld + c];
+            double sig = 0.0;
+            for (int r = c + 2 + threadIdx.x; r < n; r += blockDim.x) {
+                const double a = A[(size_t)r * ld + c];
+                sig = fma(a, a, sig);
+            }
+            sig = block_sum(sig, red);
+            double tau = 0.0, beta = alpha, scale = 0.0;
+            if (sig > 0.0) {
+                const double nrm = sqrt(alpha * alpha + sig);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) {
+                double v = (r == c + 1) ? 1.0 : A[(size_t)r * ld + c] * scale;
+                if (r > c + 1) A[(size_t)r * ld + c] = v;
+                vs[r] = v;
+            }
+            if (threadIdx.x == 0) {
+                A[(size_t)(c + 1) * ld + c] = 1.0;
+                ev[c] = beta;
+                tauv[c] = tau;
+            }
+            __syncthreads();
+            // (3) y = A22 v with A22 = A[c+1:, c+1:] (lower storage, not yet updated by this panel)
+            for (int r = c + 1 + warp; r < n; r += nw) {
+                const double* Ar = A + (size_t)r * ld;
+                const double vr = vs[r];
+                double acc = 0.0;
+                double* yr = yw + (size_t)warp * n;
+                for (int t = c + 1 + lane; t <= r; t += 32) {
+                    const double a = Ar[t];
+                    acc = fma(a, vs[t], acc);
+                    if (t < r) yr[t] = fma(a, vr, yr[t]);
+                }
+                acc = warp_sum(acc);
+                if (lane == 0) yr[r] += acc;
+                __syncwarp();  // the next row's lanes update yr[r] too
+            }
+            __syncthreads();
+            for (int t = c + 1 + threadIdx.x; t < n; t += blockDim.x) {
+                double s = 0.0;
+                for (int w = 0; w < nw; ++w) {
+                    s += yw[(size_t)w * n + t];
+                    yw[(size_t)w * n + t] = 0.0;
+                }
+                ys[t] = s;
+            }
+            // panel corrections: pc = W^T v, sc = V^T v over rows c+1..n-1
+            for (int t = warp; t < j; t += nw) {
+                double p = 0.0, q = 0.0;
+                for (int r = c + 1 + lane; r < n; r += 32) {
+                    p = fma(W[(size_t)r * NB + t], vs[r], p);
+                    q = fma(A[(size_t)r * ld + c0 + t], vs[r], q);
+                }
+                p = warp_sum(p);
+                q = warp_sum(q);
+                if (lane == 0) {
+                    pc[t] = p;
+                    sc[t] = q;
+                }
+            }
+            __syncthreads();
+            double dot = 0.0;
+            for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) {
+                double y = ys[r];
+                for (int t = 0; t < j; ++t)
+                    y = fma(-A[(size_t)r * ld + c0 + t], pc[t], fma(-W[(size_t)r * NB + t], sc[t], y));
+                y *= tau;
+                ys[r] = y;
+                dot = fma(y, vs[r], dot);
+            }
+            dot = block_sum(dot, red);
+            const double a2 = -0.5 * tau * dot;
+            for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) W[(size_t)r * NB + j] = fma(a2, vs[r], ys[r]);
+            __syncthreads();
+        }
+        const int m2 = n - c0 - nb;
+        if (m2 > 0) {
+            double* C = A + (size_t)(c0 + nb) * ld + c0 + nb;
+            const double* Vp = A + (size_t)(c0 + nb) * ld + c0;
+            const double* Wp = W + (size_t)(c0 + nb) * NB;
+            cta_gemm_nt_sub<true>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G);
+            cta_gemm_nt_sub<true>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G);
+            for (int e = threadIdx.x; e < nw * n; e += blockDim.x) yw[e] = 0.0;
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Implicit QL (one thread per cluster) on (d, e); rotations are logged as (c, s)
+// per sweep: header = (first rotation, first index i, count) with i decreasing.
+// Header block of a cluster: [nsweeps, (start, i_first, count) x nsweeps].
+// ---------------------------------------------------------------------------
+__global__ void k_ql(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                     double* __restrict__ arena, int* __restrict__ iters, int* __restrict__ status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncl) return;
+    const int ci = order[t];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc dsc = cls[ci];
+    const int n = dsc.n;
+    double* d = arena + dsc.aux_off;
+    double* e = d + dsc.ld;
+    double2* rot = reinterpret_cast<double2*>(arena + dsc.rot_off);
+    int* hdr = iters + dsc.it_off;
+    const double eps = 2.220446049250313e-16;
+    e[n - 1] = 0.0;
+    int nrot = 0, nsw = 0;
+    for (int l = 0; l < n; ++l) {
+        int it = 0;
+        while (true) {
+            int m = l;
+            for (; m < n - 1; ++m) {
+                const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(e[m]) <= eps * dd) break;
+            }
+            if (m == l) break;
+            if (++it > 60) {
+                status[ci] = ST_NOT_CONVERGED;
+                hdr[0] = nsw;
+                return;
+            }
+            if (nsw >= (dsc.it_cap - 1) / 3 || nrot + (m - l) > dsc.rot_cap) {
+                status[ci] = ST_LOG_FULL;
+                hdr[0] = nsw;
+                return;
+            }
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            double s = 1.0, c = 1.0, p = 0.0;
+            const int start = nrot;
+            bool early = false;
+            for (int i = m - 1; i >= l; --i) {
+                const double f = s * e[i], b = c * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    early = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                rot[nrot++] = make_double2(c, s);
+            }
+            hdr[1 + 3 * nsw] = start;
+            hdr[2 + 3 * nsw] = m - 1;
+            hdr[3 + 3 * nsw] = nrot - start;
+            ++nsw;
+            if (!early) {
+                d[l] -= p;
+                e[l] = g;
+                e[m] = 0.0;
+            }
+        }
+    }
+    hdr[0] = nsw;
+}
+
+// ---------------------------------------------------------------------------
+// Central strips: P ([n][2 mc], column t holds the 2 mc values of the strips at t)
+// initialised to R1 = (L^-T)_c,: = [0 | L_cc^-T] and R2 = L_c,:, then P <- P Q.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const ClusterDesc* __restrict__ cls,
+                                                                      const int* __restrict__ order,
+                                                                      double* __restrict__ arena,
+                                                                      const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, ld = d.ld, mc = d.mc, w2 = 2 * mc, c0 = n - mc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* A = arena + d.mat_off;
+    const double* L = A + (size_t)n * ld;
+    const double* tau = arena + d.aux_off + 2 * ld;
+    double* P = arena + d.cc_off;
+    double* Li = sm;              // mc x mc inverse of L_cc
+    double* vsh = sm + DCLNO_MAX_M * DCLNO_MAX_M;  // n
+    double* part = vsh + n;       // nw x 64
+    // L_cc^-1 by forward substitution, one column per thread
+    if (threadIdx.x < mc) {
+        const int col = threadIdx.x;
+        for (int r = 0; r < mc; ++r) {
+            double s = (r == col) ? 1.0 : 0.0;
+            for (int k = col; k < r; ++k) s -= L[(size_t)(c0 + r) * ld + c0 + k] * Li[k * DCLNO_MAX_M + col];
+            Li[r * DCLNO_MAX_M + col] = (r < col) ? 0.0 : s / L[(size_t)(c0 + r) * ld + c0 + r];
+        }
+    }
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < (size_t)n * w2; e += blockDim.x) {
+        const int t = (int)(e / w2), r = (int)(e % w2);
+        double v;
+        if (r < mc) v = (t >= c0) ? Li[(t - c0) * DCLNO_MAX_M + r] : 0.0;  // (L_cc^-T)[r][t-c0] = Li[t-c0][r]
+        else v = (t <= c0 + (r - mc)) ? L[(size_t)(c0 + r - mc) * ld + t] : 0.0;
+        P[e] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const double tk = tau[k];
+        if (tk == 0.0) continue;  // uniform
+        for (int t = k + 1 + threadIdx.x; t < n; t += blockDim.x) vsh[t] = A[(size_t)t * ld + k];
+        __syncthreads();
+        // u_r = sum_t P[t][r] v_t ; warps split t, lanes own rows (two passes if w2 > 32)
+        for (int r0 = 0; r0 < w2; r0 += 32) {
+            const int r = r0 + lane;
+            double u = 0.0;
+            if (r < w2)
+                for (int t = k + 1 + warp; t < n; t += nw) u = fma(P[(size_t)t * w2 + r], vsh[t], u);
+            part[warp * 64 + r0 + lane] = u;
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < w2; r0 += 32) {
+            const int r = r0 + lane;
+            if (r < w2) {
+                double u = 0.0;
+                for (int w = 0; w < nw; ++w) u += part[w * 64 + r];
+                u *= tk;
+                for (int t = k + 1 + warp; t < n; t += nw) P[(size_t)t * w2 + r] = fma(-u, vsh[t], P[(size_t)t * w2 + r]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// P <- P Z by the logged rotations, one warp per cluster, lanes own the 2 mc rows.
+__global__ void k_replay_fwd(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                             double* __restrict__ arena, const int* __restrict__ iters,
+                             const int* __restrict__ status) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= ncl) return;
+    const int ci = order[wid];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    const int w2 = 2 * d.mc;
+    double* P = arena + d.cc_off;
+    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
+    const int* hdr = iters + d.it_off;
+    const int nsw = hdr[0];
+    for (int r0 = 0; r0 < w2; r0 += 32) {
+        const int r = r0 + lane;
+        if (r >= w2) continue;
+        for (int k = 0; k < nsw; ++k) {
+            const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
+            double xi1 = P[(size_t)(i0 + 1) * w2 + r];
+            for (int u = 0; u < cnt; ++u) {
+                const int i = i0 - u;
+                const double2 cs = rot[start + u];
+                const double xi = P[(size_t)i * w2 + r];
+                // column update of Z G: z_{i+1} <- s z_i + c z_{i+1}, z_i <- c z_i - s z_{i+1}
+                P[(size_t)(i + 1) * w2 + r] = fma(cs.y, xi, cs.x * xi1);
+                xi1 = fma(cs.x, xi, -cs.y * xi1);
+            }
+            P[(size_t)(i0 + 1 - cnt) * w2 + r] = xi1;
+        }
+    }
+}
+
+// eigenvalues and weights: eps_mu = d_mu, q_mu = sum_a P[mu][a] P[mu][mc + a]
+__global__ void k_weights(int ncl, const ClusterDesc* __restrict__ cls, const double* __restrict__ arena,
+                          const int* __restrict__ status, double* __restrict__ eps, double* __restrict__ q) {
+    const int ci = blockIdx.y;
+    if (ci >= ncl || status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    const int n = d.n, mc = d.mc;
+    const double* dv = arena + d.aux_off;
+    const double* P = arena + d.cc_off;
+    for (int mu = blockIdx.x * blockDim.x + threadIdx.x; mu < n; mu += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < mc; ++a) s = fma(P[(size_t)mu * 2 * mc + a], P[(size_t)mu * 2 * mc + mc + a], s);
+        eps[d.eig_off + mu] = dv[mu];
+        q[d.eig_off + mu] = s;
+    }
+}
+
+static size_t smem_gemm_bytes() { return (size_t)(NB * DK_LD + NB + GT_SMEM_DOUBLES) * sizeof(double); }
+
+dclno_status launch_solve_fp64(dclno_ctx* c) {
+    const int N = c->N;
+    int maxn = 0;
+    for (const auto& d : c->cl) maxn = std::max(maxn, d.n);
+    const int nw = DCLNO_SOLVE_THREADS / 32;
+    size_t sm_chol = smem_gemm_bytes();
+    size_t sm_tri = std::max((size_t)GT_SMEM_DOUBLES, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
+    size_t sm_q = (size_t)(DCLNO_MAX_M * DCLNO_MAX_M + maxn + nw * 64) * sizeof(double);
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_congruence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tri));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_apply_q_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_q));
+    if (sm_tri > 227 * 1024 || sm_q > 227 * 1024)
+        return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the FP64 solver (n = " + std::to_string(maxn) + ")");
+
+    {
+        ProfScope ps__(c, "k_cholesky");
+        k_cholesky<<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_congruence");
+        k_congruence<<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_tridiag");
+        k_tridiag<<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_ql");
+        k_ql<<<(N + 7) / 8, 8, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_apply_q_rows");
+        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_replay_fwd");
+        k_replay_fwd<<<(N * 32 + 127) / 128, 128, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters,
+                                                              c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_weights");
+        k_weights<<<dim3((maxn + 255) / 256, N), 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_status, c->d_eps,
+                                                                   c->d_q);
+    }
+    DCLNO_LAUNCHED(c);
+    std::vector<int> st(N);
+    DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < N; ++i) {
+        if (st[i] == ST_NOT_SPD)
+            return set_err(c, DCLNO_ERR_NOT_SPD, "overlap of cluster " + std::to_string(i) + " is not positive definite");
+        if (st[i] == ST_NOT_CONVERGED)
+            return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL did not converge for cluster " + std::to_string(i));
+        if (st[i] == ST_LOG_FULL)
+            return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL rotation log full for cluster " + std::to_string(i));
+        if (st[i] != ST_OK) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "solver failed for cluster " + std::to_string(i));
+    }
+    return DCLNO_OK;
+}

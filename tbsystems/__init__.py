@@ -25,6 +25,13 @@ Conventions
   ``H``.
 * Entries of S below ``drop_tol`` (1e-10) are dropped (set to zero, and blocks
   that become all-zero are removed); H is zero wherever S is.
+* Hamiltonian (extended-Hueckel form): two-centre elements (orbitals on
+  different atoms, or on different images of one atom) follow Wolfsberg-Helmholz,
+  H_ab = 1.75 S_ab (h_a + h_b)/2; one-centre elements use the same form with
+  K = 1, H_ab = S_ab (h_a + h_b)/2, which gives H_aa = h_a (the on-site energy).
+  Applying K = 1.75 to one-centre pairs of the strongly overlapping same-atom
+  Gaussians would make H inconsistent with S in its near-null space and put
+  spurious eigenvalues of order h / lambda_min(S) ~ 1e5 Ha into every cluster.
 """
 from __future__ import annotations
 
@@ -149,10 +156,9 @@ def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
                 sblk[sblk < drop_tol] = 0.0
                 ea = onsite[i][None, :, None]
                 eb = np.stack([onsite[jj] for jj in j])[:, None, :]
-                hblk = WH_K * sblk * 0.5 * (ea + eb)
                 self_mask = (j == i) & np.all(sh == 0, axis=1)
-                for k in np.nonzero(self_mask)[0]:
-                    np.fill_diagonal(hblk[k], onsite[i])
+                kfac = np.where(self_mask, 1.0, WH_K)[:, None, None]
+                hblk = kfac * sblk * 0.5 * (ea + eb)
                 keep = np.any(sblk != 0.0, axis=(1, 2))
                 order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], j))
                 order = order[keep[order]]
@@ -171,9 +177,8 @@ def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
                     sb[sb < drop_tol] = 0.0
                     if not np.any(sb != 0.0):
                         continue
-                    hb = WH_K * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
-                    if jj == i and not np.any(sh[k]):
-                        np.fill_diagonal(hb, onsite[i])
+                    kf = 1.0 if (jj == i and not np.any(sh[k])) else WH_K
+                    hb = kf * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
                     blocks.append((jj, tuple(int(x) for x in sh[k]), sb, hb))
                 blocks.sort(key=lambda t: (t[0],) + t[1])
                 rows_col.append(np.array([t[0] for t in blocks], dtype=np.int32))
@@ -349,30 +354,36 @@ def synthetic_density(system: System, seed: int = 11, width: float = 3.0) -> np.
 
     It stands in for the density matrix of the previous SCF step when a test
     runs one LNO step on a system too large for the oracle to converge.  The
-    on-site block is diag(p) with slowly decreasing populations p (a fixed
-    random permutation-free profile scaled by a seeded factor per atom); the
-    off-site blocks are a seeded symmetric amplitude times exp(-d^2/width^2)
-    times w_alpha w_beta.  Symmetry rho_{0i,Rj} = rho_{0j,-Ri}^T holds by
-    construction.  Only the pattern and the geometry are read from ``system``.
+    on-site block is diag(p) with populations p_a = 0.9 exp(-0.6 a) times a
+    seeded per-atom factor in [0.9, 1.1]; an off-site block is
+    0.05 exp(-d^2/width^2) sqrt(s_i s_j) w_a w_b with w_a = exp(-0.4 a).
+    Symmetry rho_{0i,Rj} = rho_{0j,-Ri}^T holds by construction.  Only the
+    pattern and the geometry are read from ``system``.
     """
     rng = np.random.default_rng(seed)
     n = system.natoms
     scale = rng.uniform(0.9, 1.1, size=n)
-    rho = np.zeros_like(system.S)
     brow = system.block_rows()
-    for b in range(system.nnzb):
-        i, j = int(brow[b]), int(system.col[b])
-        sh = system.shift[b].astype(np.float64)
-        d = system.pos[j] + sh @ system.cell - system.pos[i]
-        r2 = float(d @ d)
-        mi, mj = int(system.norb[i]), int(system.norb[j])
-        o = int(system.blk_off[b])
-        if i == j and not np.any(system.shift[b]):
-            p = 0.9 * np.exp(-0.6 * np.arange(mi))
-            rho[o:o + mi * mj] = np.diag(p * scale[i]).reshape(-1)
-        else:
+    col = system.col.astype(np.int64)
+    d = system.pos[col] + system.shift.astype(np.float64) @ system.cell - system.pos[brow]
+    r2 = np.einsum("kd,kd->k", d, d)
+    onsite = (brow == col) & ~np.any(system.shift != 0, axis=1)
+    amp = 0.05 * np.exp(-r2 / (width * width)) * np.sqrt(scale[brow] * scale[col])
+    rho = np.zeros_like(system.S)
+    mi_all = system.norb[brow].astype(np.int64)
+    mj_all = system.norb[col].astype(np.int64)
+    for mi in np.unique(mi_all):
+        for mj in np.unique(mj_all):
+            sel = np.nonzero((mi_all == mi) & (mj_all == mj))[0]
+            if len(sel) == 0:
+                continue
             wi = np.exp(-0.4 * np.arange(mi))
             wj = np.exp(-0.4 * np.arange(mj))
-            amp = 0.05 * math.exp(-r2 / (width * width)) * math.sqrt(scale[i] * scale[j])
-            rho[o:o + mi * mj] = (amp * np.outer(wi, wj)).reshape(-1)
+            blocks = amp[sel, None, None] * np.outer(wi, wj)[None, :, :]
+            ons = onsite[sel]
+            if np.any(ons):
+                p = 0.9 * np.exp(-0.6 * np.arange(mi))
+                blocks[ons] = np.diag(p)[None, :, :] * scale[brow[sel[ons]], None, None]
+            idx = system.blk_off[sel][:, None] + np.arange(mi * mj)[None, :]
+            rho[idx] = blocks.reshape(len(sel), -1)
     return rho

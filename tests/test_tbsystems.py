@@ -67,12 +67,25 @@ def test_drop_rule_and_cutoff(cfg1):
 
 
 def test_wolfsberg_helmholz(mixed_system):
+    """Two-centre elements: K = 1.75; one-centre elements: K = 1 (diagonal = on-site energy)."""
     s = mixed_system
     brow = s.block_rows()
     b = next(b for b in range(s.nnzb) if int(s.col[b]) != int(brow[b]))
     i, j = int(brow[b]), int(s.col[b])
     want = 1.75 * s.block(s.S, b) * 0.5 * (s.onsite[i][:, None] + s.onsite[j][None, :])
     np.testing.assert_allclose(s.block(s.H, b), want, rtol=1e-15, atol=0)
+    b = next(b for b in range(s.nnzb) if int(s.col[b]) == int(brow[b]) and not np.any(s.shift[b]))
+    i = int(brow[b])
+    want = s.block(s.S, b) * 0.5 * (s.onsite[i][:, None] + s.onsite[i][None, :])
+    np.testing.assert_allclose(s.block(s.H, b), want, rtol=1e-15, atol=0)
+
+
+def test_no_spurious_low_states(cfg1):
+    """With the one-centre K = 1 rule no cluster eigenvalue falls far below the on-site energies."""
+    import oracle
+    H, S, _ = oracle.dense_matrices(cfg1)
+    eps = oracle.gen_eig(H, S)[0]
+    assert eps.min() > -5.0
 
 
 def test_cfg1_overlap_spd(cfg1):
