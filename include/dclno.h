@@ -171,6 +171,32 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
                         double n_electrons, double kT,
                         double *mu_out, double *nelec_out, double *eband_out);
 
+/*
+ * The chemical-potential search of dclno_find_mu without any device
+ * allocation, for callers that cannot call cudaMalloc: code that runs while a
+ * stream is captured into a CUDA graph, applications whose pool allocator owns
+ * all device memory, control loops that must not allocate once running.  The
+ * paper has no counterpart: this is an interface for such callers.
+ * Inputs: eps, q: device arrays of `count` eigenvalue / weight pairs (for
+ * example a copy of dclno_get_spectrum's output); n_electrons, kT as in
+ * dclno_find_mu.  Outputs: mu_out, nelec_out (host scalars, nullable).  Work is
+ * ordered on `cuda_stream` (NULL = legacy default stream); the call
+ * synchronises it.
+ * Scratch: a file-scope device array of about 165 KB inside the library,
+ * allocated on every GPU that loads the library and kept until exit; it
+ * covers at most 8,388,608 pairs (4096 blocks x 256 threads x 8), and a larger
+ * count returns DCLNO_ERR_ARG without touching the GPU.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls whose GPU work overlaps (other threads or streams) race and must be
+ * serialised by the caller.
+ * Errors: DCLNO_ERR_ARG (null pointers, count < 1 or too large, kT <= 0),
+ * DCLNO_ERR_NO_BRACKET, DCLNO_ERR_CUDA.  No context: there is no message.
+ */
+dclno_status dclno_find_mu_noalloc(const double *eps, const double *q, long long count,
+                                   double n_electrons, double kT, double *mu_out,
+                                   double *nelec_out, void *cuda_stream);
+
 /* ---- inspection (tests, benchmarks) ------------------------------------ */
 
 /*

@@ -8,5 +8,5 @@ been built; there is no CPU fallback.
 """
 from ._lib import (  # noqa: F401
     DCLNO_FP64, DCLNO_MIXED, LIB_PATH, Context, DclnoError, STATUS_NAMES, exported_symbols, load_library,
-    measure_fp64_peaks,
+    find_mu_noalloc, measure_fp64_peaks,
 )

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_
 SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clusters", "dclno_compute_lnos",
            "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
-           "dclno_kernel_time", "dclno_measure_fp64_peaks"]
+           "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc"]
 
 
 class DclnoError(RuntimeError):
@@ -75,6 +75,7 @@ def load_library():
         "dclno_set_profiling": ([P, I], I),
         "dclno_kernel_time": ([P, ctypes.c_char_p, P, P], I),
         "dclno_measure_fp64_peaks": ([P, P], I),
+        "dclno_find_mu_noalloc": ([P, P, ctypes.c_longlong, D, D, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -98,6 +99,22 @@ def measure_fp64_peaks():
     if st != 0:
         raise DclnoError(st, "dclno_measure_fp64_peaks failed")
     return a.value, b.value
+
+
+def find_mu_noalloc(eps, q, n_electrons, kT, stream=None):
+    """dclno_find_mu_noalloc on device arrays eps, q (torch, float64); returns (mu, N(mu)).
+
+    The library allocates nothing in this call (see include/dclno.h)."""
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    mu, n = ctypes.c_double(), ctypes.c_double()
+    st = lib.dclno_find_mu_noalloc(_ptr(eps), _ptr(q), int(eps.numel()), float(n_electrons), float(kT),
+                                   _dptr(mu), _dptr(n), ctypes.c_void_p(stream))
+    if st != 0:
+        raise DclnoError(st, "dclno_find_mu_noalloc failed")
+    return mu.value, n.value
 
 
 def _ptr(x):

@@ -405,3 +405,70 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
     }
     return DCLNO_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Chemical potential without any device allocation (dclno_find_mu_noalloc).
+//
+// Some callers cannot call cudaMalloc at all: code that runs while a stream is
+// being captured into a CUDA graph, applications that hand every byte of device
+// memory to their own pool allocator, and control loops that must not allocate
+// once they are running.  This variant keeps its scratch (the per-block partial
+// sums of the k-section and its bracket scalars) in the file-scope array below,
+// which every GPU that loads the library holds until the process exits.  The
+// caller passes the (eps, q) pairs; one partial sum per block of
+// 256 threads x NOALLOC_PER_THREAD pairs bounds the pair count.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define NOALLOC_MAX_BLOCKS 4096
+#define NOALLOC_PER_THREAD 8
+#define NOALLOC_MAX_PAIRS ((long long)NOALLOC_MAX_BLOCKS * 256 * NOALLOC_PER_THREAD)
+#define NOALLOC_SCALARS 64
+
+// partial sums [NOALLOC_MAX_BLOCKS][KSEC + 2] followed by the bracket scalars (about 165 KB)
+static __device__ __align__(256) double g_mu_scratch[NOALLOC_MAX_BLOCKS * (KSEC + 2) + NOALLOC_SCALARS];
+
+static std::mutex g_mu_scratch_lock;
+static double* g_mu_scratch_addr[128];  // device address of g_mu_scratch per device, set up once
+
+extern "C" dclno_status dclno_find_mu_noalloc(const double* eps, const double* q, long long count, double n_electrons,
+                                              double kT, double* mu_out, double* nelec_out, void* cuda_stream) {
+    if (!eps || !q || count < 1 || !(kT > 0.0)) return DCLNO_ERR_ARG;
+    if (count > NOALLOC_MAX_PAIRS) return DCLNO_ERR_ARG;  // more pairs than the static scratch covers
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return DCLNO_ERR_CUDA;
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu_scratch_lock);
+        if (!g_mu_scratch_addr[dev]) {
+            void* p = nullptr;
+            // the host-side name g_mu_scratch is only a stand-in: ask the runtime for the device address
+            if (cudaGetSymbolAddress(&p, g_mu_scratch) != cudaSuccess || !p) return DCLNO_ERR_CUDA;
+            g_mu_scratch_addr[dev] = static_cast<double*>(p);
+        }
+        base = g_mu_scratch_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nblk = (int)((count + 256LL * NOALLOC_PER_THREAD - 1) / (256LL * NOALLOC_PER_THREAD));
+    double* part = base;
+    double* scal = base + NOALLOC_MAX_BLOCKS * (KSEC + 2);
+    // every scratch word that is read is written first in this call: k_mu_init sets all
+    // bracket scalars (the done flag to 0), each pass rewrites the partial sums it reads
+    k_mu_bracket<<<nblk, 256, 0, st>>>(count, eps, part);
+    k_mu_init<<<1, 1, 0, st>>>(nblk, part, scal, kT, n_electrons);
+    for (int pass = 0; pass < MU_PASSES; ++pass) {
+        k_mu_partial<<<nblk, 256, 0, st>>>(count, eps, q, scal, part, pass == 0);
+        k_mu_update<<<1, 32, 0, st>>>(nblk, part, scal, pass == 0, pass == MU_PASSES - 1);
+    }
+    k_mu_final_partial<<<nblk, 256, 0, st>>>(count, eps, q, scal, part);
+    k_mu_final<<<1, 32, 0, st>>>(nblk, part, scal);
+    if (cudaGetLastError() != cudaSuccess) return DCLNO_ERR_CUDA;
+    double h[10];
+    if (cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DCLNO_ERR_CUDA;
+    if (h[4] == 2.0) return DCLNO_ERR_NO_BRACKET;
+    if (mu_out) *mu_out = h[2];
+    if (nelec_out) *nelec_out = h[3];
+    return DCLNO_OK;
+}
