@@ -247,15 +247,19 @@ __global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double*
     }
 }
 
-// G <- Z G: the logged rotations in reverse order acting on rows (i, i+1)
-__global__ void k_replay_rev(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
-                             double* __restrict__ arena, const int* __restrict__ iters) {
+// G <- Z G: the logged rotations in reverse order acting on rows (i, i+1).
+// A warp packs floor(32 / mc) clusters, one lane per column of G.
+__global__ void k_replay_rev(int ncl, int per_warp, int mc_max, const ClusterDesc* __restrict__ cls,
+                             const int* __restrict__ order, double* __restrict__ arena, const int* __restrict__ iters) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (wid >= ncl) return;
-    const ClusterDesc d = cls[order[wid]];
+    const int grp = lane / mc_max, col = lane % mc_max;
+    if (grp >= per_warp) return;
+    const int item = wid * per_warp + grp;
+    if (item >= ncl) return;
+    const ClusterDesc d = cls[order[item]];
     const int mc = d.mc;
-    if (lane >= mc) return;
+    if (col >= mc) return;
     double* G = arena + d.aux_off + 3 * d.ld;
     const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
     const int* hdr = iters + d.it_off;
@@ -265,14 +269,22 @@ __global__ void k_replay_rev(int ncl, const ClusterDesc* __restrict__ cls, const
         if (cnt == 0) continue;
         // rotations u = cnt-1 .. 0 act on (i, i+1) with i = i0 - u, i increasing
         int i = i0 - (cnt - 1);
-        double wi = G[(size_t)i * mc + lane];
+        double wi = G[(size_t)i * mc + col];
+        double wi1 = G[(size_t)(i + 1) * mc + col];
+        double2 cs = rot[start + cnt - 1];
         for (int u = cnt - 1; u >= 0; --u, ++i) {
-            const double2 cs = rot[start + u];
-            const double wi1 = G[(size_t)(i + 1) * mc + lane];
-            G[(size_t)i * mc + lane] = fma(cs.x, wi, cs.y * wi1);
+            double wn = 0.0;
+            double2 csn = cs;
+            if (u > 0) {  // prefetch the next rotation's operands
+                wn = G[(size_t)(i + 2) * mc + col];
+                csn = rot[start + u - 1];
+            }
+            G[(size_t)i * mc + col] = fma(cs.x, wi, cs.y * wi1);
             wi = fma(-cs.y, wi, cs.x * wi1);
+            wi1 = wn;
+            cs = csn;
         }
-        G[(size_t)i * mc + lane] = wi;
+        G[(size_t)i * mc + col] = wi;
     }
 }
 
@@ -376,7 +388,12 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_replay_rev");
-        k_replay_rev<<<(N * 32 + 127) / 128, 128, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters);
+        int mcmax = 1;
+        for (const auto& d : c->cl) mcmax = std::max(mcmax, d.mc);
+        const int per_warp = std::max(1, 32 / mcmax);
+        const int warps = (N + per_warp - 1) / per_warp;
+        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, mcmax, c->d_cl, c->d_order,
+                                                                      c->d_arena, c->d_iters);
     }
     DCLNO_LAUNCHED(c);
     const size_t sm = (size_t)(maxn + 32 * (DCLNO_SOLVE_THREADS / 32)) * sizeof(double);

@@ -322,81 +322,182 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDe
 }
 
 // ---------------------------------------------------------------------------
-// Implicit QL (one thread per cluster) on (d, e); rotations are logged as (c, s)
-// per sweep: header = (first rotation, first index i, count) with i decreasing.
-// Header block of a cluster: [nsweeps, (start, i_first, count) x nsweeps].
+// Implicit QL on (d, e), one lane per cluster, lanes in lockstep.
+// Every pass of the loop advances each lane by one unit of work: up to 8
+// deflation checks (phase SEEK), the Wilkinson-type shift of a new sweep
+// (START) or one plane rotation (ROT), so a warp's FP64 instructions serve all
+// its clusters at once (an FP64 instruction costs the same whatever its number
+// of active lanes).  Rotations are logged as (c, s) per sweep:
+// header block of a cluster = [nsweeps, (first rotation, first index i, count) x nsweeps],
+// i decreasing within a sweep.
 // ---------------------------------------------------------------------------
-__global__ void k_ql(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
-                     double* __restrict__ arena, int* __restrict__ iters, int* __restrict__ status) {
+enum { QL_SEEK = 0, QL_START = 1, QL_ROT = 2, QL_FIN = 3, QL_DONE = 4 };
+
+__device__ __forceinline__ int exp_bits(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// |e| negligible beside d_m, d_{m+1}: |e| < 2^-52 max(|d_m|, |d_{m+1}|), by exponents only
+__device__ __forceinline__ bool negligible(double e, double d0, double d1) {
+    if (e == 0.0) return true;
+    const int ed = max(exp_bits(d0), exp_bits(d1));
+    return exp_bits(e) + 53 <= ed;
+}
+
+__global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restrict__ cls,
+                                           const int* __restrict__ order, double* __restrict__ arena,
+                                           int* __restrict__ iters, int* __restrict__ status) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncl) return;
-    const int ci = order[t];
-    if (status[ci] != ST_OK) return;
-    const ClusterDesc dsc = cls[ci];
-    const int n = dsc.n;
-    double* d = arena + dsc.aux_off;
-    double* e = d + dsc.ld;
-    double2* rot = reinterpret_cast<double2*>(arena + dsc.rot_off);
-    int* hdr = iters + dsc.it_off;
-    const double eps = 2.220446049250313e-16;
-    e[n - 1] = 0.0;
-    int nrot = 0, nsw = 0;
-    for (int l = 0; l < n; ++l) {
-        int it = 0;
-        while (true) {
-            int m = l;
-            for (; m < n - 1; ++m) {
-                const double dd = fabs(d[m]) + fabs(d[m + 1]);
-                if (fabs(e[m]) <= eps * dd) break;
-            }
-            if (m == l) break;
-            if (++it > 60) {
-                status[ci] = ST_NOT_CONVERGED;
-                hdr[0] = nsw;
-                return;
-            }
-            if (nsw >= (dsc.it_cap - 1) / 3 || nrot + (m - l) > dsc.rot_cap) {
-                status[ci] = ST_LOG_FULL;
-                hdr[0] = nsw;
-                return;
-            }
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, p = 0.0;
-            const int start = nrot;
-            bool early = false;
-            for (int i = m - 1; i >= l; --i) {
-                const double f = s * e[i], b = c * e[i];
+    int phase = QL_DONE, n = 0, ci = -1;
+    double* d = nullptr;
+    double* e = nullptr;
+    double2* rot = nullptr;
+    int* hdr = nullptr;
+    int rot_cap = 0, sw_cap = 0;
+    if (t < ncl) {
+        ci = order[t];
+        if (status[ci] == ST_OK) {
+            const ClusterDesc dsc = cls[ci];
+            n = dsc.n;
+            d = arena + dsc.aux_off;
+            e = d + dsc.ld;
+            rot = reinterpret_cast<double2*>(arena + dsc.rot_off);
+            hdr = iters + dsc.it_off;
+            rot_cap = dsc.rot_cap;
+            sw_cap = (dsc.it_cap - 1) / 3;
+            e[n - 1] = 0.0;
+            phase = (n > 1) ? QL_SEEK : QL_DONE;
+            if (n <= 1) hdr[0] = 0;
+        }
+    }
+    int l = 0, m = 0, mm = 0, i = 0, it = 0, nrot = 0, nsw = 0, start = 0;
+    int lowneg = 0;       // smallest index in (l, m] whose e became negligible during this sweep
+    double s = 1.0, c = 1.0, p = 0.0, g = 0.0;
+    double ce = 0.0, cd0 = 0.0, cd1 = 0.0;  // e[i], d[i], d[i+1] of the current rotation
+    double ne = 0.0, nd = 0.0;              // e[i-1], d[i-1] loaded one rotation ahead
+    double dnext = 0.0;                     // new d[i+2] written by the previous rotation
+    while (__any_sync(0xffffffffu, phase != QL_DONE)) {
+        // a burst of rotations: lanes outside a sweep are predicated off, the FP64
+        // instructions of one rotation serve every lane that is inside one
+#pragma unroll 1
+        for (int u = 0; u < 32; ++u) {
+            if (phase != QL_ROT) continue;
+            const double f = s * ce, b = c * ce;
+            const double ss = fma(f, f, g * g);
+            double r;
+            if (exp_bits(ss) < 64) {
+                // tiny or zero: the careful hypot path (rare)
                 r = hypot(f, g);
-                e[i + 1] = r;
                 if (r == 0.0) {
-                    d[i + 1] -= p;
+                    e[i + 1] = 0.0;
+                    d[i + 1] = cd1 - p;
                     e[m] = 0.0;
-                    early = true;
-                    break;
+                    lowneg = i + 1;  // e[i+1] = 0: the next block ends here
+                    phase = QL_FIN;  // the sweep ends early, d[l] and e[l] untouched
+                    continue;
                 }
                 s = f / r;
                 c = g / r;
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - b;
-                rot[nrot++] = make_double2(c, s);
+            } else {
+                const double ti = rsqrt(ss);
+                r = ss * ti;
+                s = f * ti;
+                c = g * ti;
             }
+            e[i + 1] = r;
+            g = cd1 - p;
+            const double rr = fma(cd0 - g, s, (b + b) * c);
+            p = s * rr;
+            const double dn = g + p;
+            d[i + 1] = dn;
+            g = fma(c, rr, -b);
+            rot[nrot++] = make_double2(c, s);
+            // deflation bookkeeping for the next sweep: e[i+1], d[i+1], d[i+2] are final now
+            if (i + 1 < m && negligible(r, dn, dnext)) lowneg = i + 1;
+            dnext = dn;
+            if (--i < l) {
+                const double dl = d[l] - p;
+                d[l] = dl;
+                e[l] = g;
+                e[m] = 0.0;
+                if (negligible(g, dl, dn)) lowneg = l;
+                phase = QL_FIN;
+            } else {
+                cd1 = cd0;
+                cd0 = nd;
+                ce = ne;
+                if (i - 1 >= l) {
+                    ne = e[i - 1];
+                    nd = d[i - 1];
+                }
+            }
+        }
+        if (phase == QL_FIN) {
             hdr[1 + 3 * nsw] = start;
             hdr[2 + 3 * nsw] = m - 1;
             hdr[3 + 3 * nsw] = nrot - start;
             ++nsw;
-            if (!early) {
-                d[l] -= p;
-                e[l] = g;
-                e[m] = 0.0;
+            if (lowneg > l) {
+                m = lowneg;  // the unreduced block shrank: no scan needed
+                phase = QL_START;
+            } else {
+                mm = l;
+                phase = QL_SEEK;
+            }
+        }
+        if (phase == QL_SEEK) {
+#pragma unroll 1
+            for (int u = 0; u < 64 && phase == QL_SEEK; ++u) {
+                if (mm == n - 1 || negligible(e[mm], d[mm], d[mm + 1])) {
+                    if (mm == l) {
+                        ++l;
+                        it = 0;
+                        mm = l;
+                        if (l >= n - 1) {
+                            phase = QL_DONE;
+                            hdr[0] = nsw;
+                        }
+                    } else {
+                        m = mm;
+                        phase = QL_START;
+                    }
+                } else {
+                    ++mm;
+                }
+            }
+        }
+        if (phase == QL_START) {
+            if (++it > 60) {
+                status[ci] = ST_NOT_CONVERGED;
+                hdr[0] = nsw;
+                phase = QL_DONE;
+            } else if (nsw >= sw_cap || nrot + (m - l) > rot_cap) {
+                status[ci] = ST_LOG_FULL;
+                hdr[0] = nsw;
+                phase = QL_DONE;
+            } else {
+                const double dl = d[l], dl1 = d[l + 1], el = e[l], dm = d[m];
+                g = (dl1 - dl) / (2.0 * el);
+                const double r = hypot(g, 1.0);
+                g = dm - dl + el / (g + copysign(r, g));
+                s = 1.0;
+                c = 1.0;
+                p = 0.0;
+                i = m - 1;
+                start = nrot;
+                lowneg = m;
+                ce = e[i];
+                cd0 = d[i];
+                cd1 = dm;
+                dnext = (m + 1 < n) ? d[m + 1] : 0.0;
+                if (i - 1 >= l) {
+                    ne = e[i - 1];
+                    nd = d[i - 1];
+                }
+                phase = QL_ROT;
             }
         }
     }
-    hdr[0] = nsw;
 }
 
 // ---------------------------------------------------------------------------
@@ -465,37 +566,51 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const Clus
     }
 }
 
-// P <- P Z by the logged rotations, one warp per cluster, lanes own the 2 mc rows.
-__global__ void k_replay_fwd(int ncl, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
-                             double* __restrict__ arena, const int* __restrict__ iters,
-                             const int* __restrict__ status) {
+// P <- P Z by the logged rotations.  Work items are (cluster, strip) pairs with
+// strip 0 = the mc rows of R1 and strip 1 = the mc rows of R2; a warp packs
+// floor(32 / mc) items, one lane per row, so one FP64 instruction updates the rows
+// of several clusters.
+__global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const ClusterDesc* __restrict__ cls,
+                             const int* __restrict__ order, double* __restrict__ arena,
+                             const int* __restrict__ iters, const int* __restrict__ status) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (wid >= ncl) return;
-    const int ci = order[wid];
+    const int grp = lane / mc_max, row = lane % mc_max;
+    if (grp >= per_warp) return;
+    const int item = wid * per_warp + grp;
+    if (item >= nitems) return;
+    const int ci = order[item >> 1];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
+    if (row >= d.mc) return;
     const int w2 = 2 * d.mc;
+    const int r = (item & 1) * d.mc + row;
     double* P = arena + d.cc_off;
     const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
     const int* hdr = iters + d.it_off;
     const int nsw = hdr[0];
-    for (int r0 = 0; r0 < w2; r0 += 32) {
-        const int r = r0 + lane;
-        if (r >= w2) continue;
-        for (int k = 0; k < nsw; ++k) {
-            const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
-            double xi1 = P[(size_t)(i0 + 1) * w2 + r];
-            for (int u = 0; u < cnt; ++u) {
-                const int i = i0 - u;
-                const double2 cs = rot[start + u];
-                const double xi = P[(size_t)i * w2 + r];
-                // column update of Z G: z_{i+1} <- s z_i + c z_{i+1}, z_i <- c z_i - s z_{i+1}
-                P[(size_t)(i + 1) * w2 + r] = fma(cs.y, xi, cs.x * xi1);
-                xi1 = fma(cs.x, xi, -cs.y * xi1);
+    for (int k = 0; k < nsw; ++k) {
+        const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
+        if (cnt == 0) continue;
+        double xi1 = P[(size_t)(i0 + 1) * w2 + r];
+        double xi = P[(size_t)i0 * w2 + r];
+        double2 cs = rot[start];
+        for (int u = 0; u < cnt; ++u) {
+            const int i = i0 - u;
+            // prefetch the next rotation's operands (independent of this rotation's result)
+            double xn = 0.0;
+            double2 csn = cs;
+            if (u + 1 < cnt) {
+                xn = P[(size_t)(i - 1) * w2 + r];
+                csn = rot[start + u + 1];
             }
-            P[(size_t)(i0 + 1 - cnt) * w2 + r] = xi1;
+            // column update of Z G: z_{i+1} <- s z_i + c z_{i+1}, z_i <- c z_i - s z_{i+1}
+            P[(size_t)(i + 1) * w2 + r] = fma(cs.y, xi, cs.x * xi1);
+            xi1 = fma(cs.x, xi, -cs.y * xi1);
+            xi = xn;
+            cs = csn;
         }
+        P[(size_t)(i0 + 1 - cnt) * w2 + r] = xi1;
     }
 }
 
@@ -550,7 +665,7 @@ dclno_status launch_solve_fp64(dclno_ctx* c) {
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_ql");
-        k_ql<<<(N + 7) / 8, 8, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters, c->d_status);
+        k_ql<<<(N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
@@ -560,8 +675,13 @@ dclno_status launch_solve_fp64(dclno_ctx* c) {
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_replay_fwd");
-        k_replay_fwd<<<(N * 32 + 127) / 128, 128, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters,
-                                                              c->d_status);
+        int mcmax = 1;
+        for (const auto& d : c->cl) mcmax = std::max(mcmax, d.mc);
+        const int per_warp = std::max(1, 32 / mcmax);
+        const int items = 2 * N;
+        const int warps = (items + per_warp - 1) / per_warp;
+        k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, c->d_order,
+                                                                      c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
