@@ -40,6 +40,10 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_order);
     dfree(c->d_mem);
     dfree(c->d_mem_cl);
+    dfree(c->d_pairblk);
+    dfree(c->d_brow);
+    dfree(c->d_tblk_off);
+    dfree(c->d_tblk);
     dfree(c->d_rowblk_member);
     dfree(c->d_status);
     dfree(c->d_arena);
@@ -270,7 +274,7 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     std::vector<int> rowblk_member(c->nnzb, -1);
     std::vector<int> mem_cl;
     c->has_lno_region = false;
-    long long mat = 0, eig = 0, its = 0;
+    long long mat = 0, eig = 0, its = 0, pairs = 0;
     for (int i = 0; i < N; ++i) {
         const double xi = c->pos[3 * i], yi = c->pos[3 * i + 1], zi = c->pos[3 * i + 2];
         std::vector<Cand> cand;
@@ -340,9 +344,26 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
         its += 3LL * d.it_cap;
         d.eig_off = eig;
         eig += n;
+        d.pair_off = pairs;
+        pairs += (long long)d.nmem * d.nmem;
     }
     c->total_dim = eig;
+    c->pair_total = pairs;
     c->arena_doubles = (size_t)mat;
+    // LNO-transformed copies of every stored block: V_j1^T X, X V_j2, V_j1^T X V_j2 for X = H, S
+    std::vector<long long> tblk_off(c->nnzb, 0), brow(c->nnzb);
+    long long tb = 0;
+    for (int i = 0; i < N; ++i)
+        for (long long b = c->row_ptr[i]; b < c->row_ptr[i + 1]; ++b) {
+            brow[b] = i;
+            tblk_off[b] = tb;
+            if (c->has_lno_region) {
+                const long long m1 = c->norb[i], m2 = c->norb[c->col[b]], k = k_lno;
+                tb += 2 * (k * m2 + m1 * k + k * k);
+            }
+        }
+    c->tblk_total = tb;
+    std::vector<int> brow32(brow.begin(), brow.end());
     c->order.resize(N);
     std::iota(c->order.begin(), c->order.end(), 0);
     std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) { return c->cl[a].n > c->cl[b].n; });
@@ -361,7 +382,8 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     // ---- device memory
     size_t free_b = 0, tot_b = 0;
     DCLNO_CUDA(c, cudaMemGetInfo(&free_b, &tot_b));
-    size_t need = c->arena_doubles * 8 + (size_t)its * 4 + (size_t)c->total_dim * 16 + (size_t)c->nnzb * 32;
+    size_t need = c->arena_doubles * 8 + (size_t)its * 4 + (size_t)c->total_dim * 16 + (size_t)c->nnzb * 48 +
+                  (size_t)c->pair_total * 4 + (size_t)c->tblk_total * 8;
     if (need + (size_t)(1u << 30) > free_b) {
         free_clusters(c);
         return set_err(c, DCLNO_ERR_OOM,
@@ -386,6 +408,8 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     COPY(c->d_order, c->order);
     COPY(c->d_mem, c->mem);
     COPY(c->d_mem_cl, mem_cl);
+    COPY(c->d_brow, brow32);
+    COPY(c->d_tblk_off, tblk_off);
     COPY(c->d_rowblk_member, rowblk_member);
 #undef COPY
     cudaError_t e;
@@ -401,10 +425,18 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
         (e = cudaMalloc(&c->d_lflags, sizeof(int) * N)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_eband, sizeof(double) * N)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_scalars, sizeof(double) * 64)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_mu_work, sizeof(double) * 4096 * 8)) != cudaSuccess) {
+        (e = cudaMalloc(&c->d_mu_work, sizeof(double) * 4096 * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_pairblk, sizeof(int) * std::max<long long>(c->pair_total, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_tblk, sizeof(double) * std::max<long long>(c->tblk_total, 1))) != cudaSuccess) {
         free_clusters(c);
         return cuda_err(c, e, "cudaMalloc (cluster workspace)");
     }
+    st = launch_pair_index(c);
+    if (st != DCLNO_OK) {
+        free_clusters(c);
+        return st;
+    }
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
     c->built = true;
     c->lnos_ready = !c->has_lno_region;
     return DCLNO_OK;

@@ -36,6 +36,7 @@ struct ClusterDesc {
     int it_cap;         // capacity of the sweep headers
     int mc;             // M of the central atom
     int pad;
+    long long pair_off; // offset of the cluster's member-pair block table (nmem x nmem ints)
 };
 
 struct MemberDesc {
@@ -110,6 +111,12 @@ struct dclno_ctx {
     int* d_order = nullptr;
     MemberDesc* d_mem = nullptr;
     int* d_mem_cl = nullptr;           // cluster of each member (atom order)
+    int* d_pairblk = nullptr;          // per cluster, member pair -> BSR block (or -1)
+    long long pair_total = 0;
+    int* d_brow = nullptr;             // row (atom) of every BSR block
+    long long* d_tblk_off = nullptr;   // per block: offset of its LNO-transformed blocks
+    double* d_tblk = nullptr;          // LNO-transformed blocks (V^T X, X V, V^T X V for X = H, S)
+    long long tblk_total = 0;
     int* d_rowblk_member = nullptr;    // per block of row i: member of cluster i or -1
     int* d_status = nullptr;           // per cluster
     double* d_arena = nullptr;
@@ -185,6 +192,7 @@ dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where);
 // kernels' host-side launchers (one per .cu file)
 dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
 dclno_status launch_assemble(dclno_ctx* c);
+dclno_status launch_pair_index(dclno_ctx* c);
 dclno_status launch_solve_fp64(dclno_ctx* c);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
 dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband);
