@@ -463,11 +463,11 @@ extern "C" dclno_status dclno_solve_clusters(dclno_ctx* c, dclno_precision prec)
     c->err.clear();
     if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: build clusters first");
     if (!c->lnos_ready) return set_err(c, DCLNO_ERR_NO_LNOS, "dclno_solve_clusters: compute LNOs first");
-    if (prec != DCLNO_FP64)
-        return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: only DCLNO_FP64 is available in this build");
+    if (prec != DCLNO_FP64 && prec != DCLNO_MIXED)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: unknown precision");
     dclno_status st = launch_assemble(c);
     if (st != DCLNO_OK) return st;
-    st = launch_solve_fp64(c);
+    st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c) : launch_solve_fp64(c);
     if (st != DCLNO_OK) return st;
     c->solved = true;
     return DCLNO_OK;

@@ -194,6 +194,7 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
 dclno_status launch_assemble(dclno_ctx* c);
 dclno_status launch_pair_index(dclno_ctx* c);
 dclno_status launch_solve_fp64(dclno_ctx* c);
+dclno_status launch_solve_mixed(dclno_ctx* c);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
 dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband);
 

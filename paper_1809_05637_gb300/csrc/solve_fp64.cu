@@ -14,9 +14,21 @@
 // need only the M_i x n strips, never the full eigenvector matrix (Eq. (Gi) is
 // evaluated through these strips).
 #include "dclno_internal.cuh"
+#include "emu_gemm.cuh"
 
 #define NB DCLNO_NB
 #define DK_LD 33
+
+// The cubic steps' tile update: FP64 mma.sync tiles (FP64 path) or FP64 emulated
+// on BF16 tensor cores (mixed path).
+template <bool LOWER, bool EMU>
+__device__ __forceinline__ void tile_update(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                                            int M, int N, int K, int diag, double* smem) {
+    if (EMU)
+        cta_gemm_nt_sub_emu<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, reinterpret_cast<unsigned char*>(smem));
+    else
+        cta_gemm_nt_sub<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, smem);
+}
 
 // x L_kk^T = h for rows [r0, r1) of M (columns kb .. kb+nb-1), L_kk in smem (lower),
 // reciprocals of its diagonal in invd.
@@ -56,7 +68,8 @@ __device__ static void load_diag_block(const double* L, int ld, int kb, int nb, 
 // ---------------------------------------------------------------------------
 // Cholesky of S^(i) in place (lower); sets ST_NOT_SPD on a non-positive pivot.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_cholesky(const ClusterDesc* __restrict__ cls,
+template <bool EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_cholesky(const ClusterDesc* __restrict__ cls,
                                                                   const int* __restrict__ order,
                                                                   double* __restrict__ arena,
                                                                   int* __restrict__ status) {
@@ -114,7 +127,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_cholesky(const ClusterD
         const int m2 = n - kb - nb;
         if (m2 > 0) {
             double* P = L + (size_t)(kb + nb) * ld + kb;
-            cta_gemm_nt_sub<true>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G);
+            tile_update<true, EMU>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G);
         }
     }
     if (threadIdx.x == 0) status[ci] = ST_OK;
@@ -124,7 +137,8 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_cholesky(const ClusterD
 // A = L^-1 H L^-T, lower triangle valid on exit (in place of H^(i)).
 // Y = H L^-T (all rows), transpose, then A = Y^T L^-T restricted to the lower part.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_congruence(const ClusterDesc* __restrict__ cls,
+template <bool EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_congruence(const ClusterDesc* __restrict__ cls,
                                                                     const int* __restrict__ order,
                                                                     double* __restrict__ arena,
                                                                     const int* __restrict__ status) {
@@ -144,7 +158,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_congruence(const Cluste
         panel_solve_rows(A, ld, kb, nb, 0, n, Dk, invd);
         __syncthreads();
         const int n2 = n - kb - nb;
-        if (n2 > 0) cta_gemm_nt_sub<false>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G);
+        if (n2 > 0) tile_update<false, EMU>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G);
     }
     // in-place transpose
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -164,7 +178,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_congruence(const Cluste
         const int m2 = n - kb - nb;
         if (m2 > 0) {
             double* C = A + (size_t)(kb + nb) * ld + kb + nb;
-            cta_gemm_nt_sub<true>(C, ld, A + (size_t)(kb + nb) * ld + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, m2, m2,
+            tile_update<true, EMU>(C, ld, A + (size_t)(kb + nb) * ld + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, m2, m2,
                                   nb, 0, G);
         }
     }
@@ -186,7 +200,8 @@ __device__ static double block_sum(double v, double* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDesc* __restrict__ cls,
+template <bool EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_tridiag(const ClusterDesc* __restrict__ cls,
                                                                  const int* __restrict__ order,
                                                                  double* __restrict__ arena,
                                                                  const int* __restrict__ status) {
@@ -209,8 +224,6 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDe
     double* sc = pc + NB;             // NB: V^T v
     double* G = sm;                   // GEMM tiles alias the vectors between panels
 
-    for (int e = threadIdx.x; e < nw * n; e += blockDim.x) yw[e] = 0.0;
-    __syncthreads();
     for (int c0 = 0; c0 < n; c0 += NB) {
         const int nb = min(NB, n - c0);
         for (int j = 0; j < nb; ++j) {
@@ -255,28 +268,53 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDe
                 tauv[c] = tau;
             }
             __syncthreads();
-            // (3) y = A22 v with A22 = A[c+1:, c+1:] (lower storage, not yet updated by this panel)
-            for (int r = c + 1 + warp; r < n; r += nw) {
-                const double* Ar = A + (size_t)r * ld;
-                const double vr = vs[r];
-                double acc = 0.0;
+            // (3) y = A22 v with A22 = A[c+1:, c+1:] (lower storage, not yet updated by this panel).
+            // Row r contributes A[r][t] v_t to y_r (warp sum, written once: each row has one warp)
+            // and A[r][t] v_r to y_t for t < r (per-warp partials in shared memory).  A warp takes
+            // four rows per pass, so each shared-memory update carries four rows' contributions.
+            {
                 double* yr = yw + (size_t)warp * n;
-                for (int t = c + 1 + lane; t <= r; t += 32) {
-                    const double a = Ar[t];
-                    acc = fma(a, vs[t], acc);
-                    if (t < r) yr[t] = fma(a, vr, yr[t]);
+                for (int t = c + 1 + lane; t < n; t += 32) yr[t] = 0.0;
+                __syncwarp();
+                for (int r0 = c + 1 + warp; r0 < n; r0 += 4 * nw) {
+                    int rr[4];
+                    double vr[4], acc[4];
+                    const double* Ar[4];
+                    int rmax = r0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        rr[q] = r0 + q * nw;
+                        const bool ok = rr[q] < n;
+                        vr[q] = ok ? vs[rr[q]] : 0.0;
+                        Ar[q] = A + (size_t)(ok ? rr[q] : r0) * ld;
+                        acc[q] = 0.0;
+                        if (ok) rmax = rr[q];
+                        else rr[q] = -1;
+                    }
+                    for (int t = c + 1 + lane; t <= rmax; t += 32) {
+                        const double vt = vs[t];
+                        double ysum = 0.0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (t <= rr[q]) {
+                                const double a = Ar[q][t];
+                                acc[q] = fma(a, vt, acc[q]);
+                                if (t < rr[q]) ysum = fma(a, vr[q], ysum);
+                            }
+                        }
+                        yr[t] += ysum;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const double a = warp_sum(acc[q]);
+                        if (lane == 0 && rr[q] >= 0) ys[rr[q]] = a;
+                    }
                 }
-                acc = warp_sum(acc);
-                if (lane == 0) yr[r] += acc;
-                __syncwarp();  // the next row's lanes update yr[r] too
             }
             __syncthreads();
             for (int t = c + 1 + threadIdx.x; t < n; t += blockDim.x) {
-                double s = 0.0;
-                for (int w = 0; w < nw; ++w) {
-                    s += yw[(size_t)w * n + t];
-                    yw[(size_t)w * n + t] = 0.0;
-                }
+                double s = ys[t];
+                for (int w = 0; w < nw; ++w) s += yw[(size_t)w * n + t];
                 ys[t] = s;
             }
             // panel corrections: pc = W^T v, sc = V^T v over rows c+1..n-1
@@ -313,10 +351,8 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_tridiag(const ClusterDe
             double* C = A + (size_t)(c0 + nb) * ld + c0 + nb;
             const double* Vp = A + (size_t)(c0 + nb) * ld + c0;
             const double* Wp = W + (size_t)(c0 + nb) * NB;
-            cta_gemm_nt_sub<true>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G);
-            cta_gemm_nt_sub<true>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G);
-            for (int e = threadIdx.x; e < nw * n; e += blockDim.x) yw[e] = 0.0;
-            __syncthreads();
+            tile_update<true, EMU>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G);
+            tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G);
         }
     }
 }
@@ -631,36 +667,37 @@ __global__ void k_weights(int ncl, const ClusterDesc* __restrict__ cls, const do
     }
 }
 
-static size_t smem_gemm_bytes() { return (size_t)(NB * DK_LD + NB + GT_SMEM_DOUBLES) * sizeof(double); }
 
-dclno_status launch_solve_fp64(dclno_ctx* c) {
+template <bool EMU>
+static dclno_status launch_solve(dclno_ctx* c) {
     const int N = c->N;
     int maxn = 0;
     for (const auto& d : c->cl) maxn = std::max(maxn, d.n);
     const int nw = DCLNO_SOLVE_THREADS / 32;
-    size_t sm_chol = smem_gemm_bytes();
-    size_t sm_tri = std::max((size_t)GT_SMEM_DOUBLES, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
+    const size_t gemm_doubles = EMU ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
+    size_t sm_chol = (size_t)(NB * DK_LD + NB + gemm_doubles) * sizeof(double);
+    size_t sm_tri = std::max(gemm_doubles, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
     size_t sm_q = (size_t)(DCLNO_MAX_M * DCLNO_MAX_M + maxn + nw * 64) * sizeof(double);
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_congruence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tri));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_cholesky<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_congruence<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_tridiag<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tri));
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_apply_q_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_q));
     if (sm_tri > 227 * 1024 || sm_q > 227 * 1024)
         return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the FP64 solver (n = " + std::to_string(maxn) + ")");
 
     {
         ProfScope ps__(c, "k_cholesky");
-        k_cholesky<<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_cholesky<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_congruence");
-        k_congruence<<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_congruence<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_tridiag");
-        k_tridiag<<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
@@ -704,3 +741,6 @@ dclno_status launch_solve_fp64(dclno_ctx* c) {
     }
     return DCLNO_OK;
 }
+
+dclno_status launch_solve_fp64(dclno_ctx* c) { return launch_solve<false>(c); }
+dclno_status launch_solve_mixed(dclno_ctx* c) { return launch_solve<true>(c); }

@@ -35,3 +35,15 @@ def spectral_moments(eps, q, mus, kT):
 
 def eps_tol(e):
     return 1e-10 + 1e-12 * np.abs(e)
+
+
+U = 2.0 ** -53
+
+
+def state_tol(r):
+    """First-order bound for each eigenvalue of the pencil (H^(i), S^(i)): a backward
+    error of n u in H and S moves eps_mu by at most n u (|H| + |eps_mu| |S|) c_mu^T c_mu
+    (c_mu^T S c_mu = 1).  1e-10 Ha is the floor; well-conditioned states stay there."""
+    n = len(r.eps)
+    cc = np.einsum("am,am->m", r.C, r.C)
+    return 1e-10 + 2.0 * n * U * (r.h_norm + np.abs(r.eps) * r.s_norm) * cc

@@ -12,18 +12,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import tbsystems as T  # noqa: E402
-from gpu_helpers import fermi, gpu_context, spectral_moments, to_dev  # noqa: E402
-
-U = 2.0 ** -53
-
-
-def state_tol(r):
-    """First-order bound for each eigenvalue of the pencil (H^(i), S^(i)): a backward
-    error of n u in H and S moves eps_mu by at most n u (|H| + |eps_mu| |S|) c_mu^T c_mu
-    (c_mu^T S c_mu = 1).  1e-10 Ha is the floor; well-conditioned clusters stay there."""
-    n = len(r.eps)
-    cc = np.einsum("am,am->m", r.C, r.C)
-    return 1e-10 + 2.0 * n * U * (r.h_norm + np.abs(r.eps) * r.s_norm) * cc
+from gpu_helpers import fermi, gpu_context, spectral_moments, state_tol, to_dev  # noqa: E402
 
 SAMPLE = [0, 777, 1727]
 MU_TEST = -0.25  # a fixed chemical potential for element-wise rho comparison
