@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""DC-LNO clusters per second on one GB300 (FP64 path).
+"""DC-LNO clusters per second on one GB300: FP64 path (value) and mixed path ("mixed").
 
 A step is one pass of the whole hot path on the 1,728-atom gapped rock-salt
 workload (12x12x12 simple-cubic sites, a = 3.0 bohr, two species, 9 s-Gaussians
@@ -183,7 +183,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import tbsystems as T
-    from paper_1809_05637_gb300 import Context, measure_fp64_peaks
+    from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context, measure_fp64_peaks
 
     dev = torch.device("cuda", local)
     s = T.make_system(2)
@@ -199,8 +199,8 @@ def run_ours(args):
     dims = ctx.cluster_info()[0]
     ncl = int(s.natoms)
 
-    def step():
-        return ctx.step(rho_in, rho_out, s.n_electrons, s.kT)
+    def step(prec=DCLNO_FP64):
+        return ctx.step(rho_in, rho_out, s.n_electrons, s.kT, precision=prec)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -230,6 +230,27 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * ncl * args.steps / (ms / 1e3)
+
+    # the mixed-precision form of the same step (BF16 tensor-core emulation of the FP64
+    # contractions), timed the same way; accuracy against the FP64 step above
+    step(DCLNO_MIXED)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        mu_mx, n_mx, e_mx = step(DCLNO_MIXED)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_mx = ev0.elapsed_time(ev1)
+    kmx_ms, kmx_n = ctx.kernel_time(DOMINANT)
+    ctx.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms_mx], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mx = float(t.item())
 
     # e2e: the C-ABI step with host buffers (H2D of rho_in and D2H of rho_out inside)
     e2e = None
@@ -266,6 +287,16 @@ def run_ours(args):
                                "weighted 1:1 by the kernel's flop mix (symv on FMA, rank-2k on MMA)",
                 "flops_per_launch": flops, "launch_ms": k_ms / max(k_n, 1)}
 
+    achieved_mx = flops / (kmx_ms / max(kmx_n, 1) / 1e3) / 1e12 if kmx_n else None
+    mixed = {"value": world * ncl * args.steps / (ms_mx / 1e3), "unit": "clusters/s", "ms_per_step": ms_mx / args.steps,
+             "speedup_vs_fp64": ms / ms_mx, "e_band_err_per_atom_vs_fp64": abs(e_mx - e_band) / s.natoms,
+             "mu_diff_vs_fp64": abs(mu_mx - mu), "dtype": "bf16 slices (8 x 8 bit) emulating f64 contractions; f64 elsewhere",
+             "roofline": {"bound": "alu", "kernel": DOMINANT, "achieved": achieved_mx, "peak": dfma, "unit": "TFLOP/s",
+                          "frac": (achieved_mx / dfma) if achieved_mx else None, "traffic": None,
+                          "peak_source": "measured in-process native FP64 FMA rate: FP64-equivalent throughput of the "
+                                         "mixed kernel against the native FP64 roofline",
+                          "launch_ms": kmx_ms / max(kmx_n, 1)}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         th = cpu_threads()
@@ -281,7 +312,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "mu": mu, "n_electrons": n_mu, "e_band": e_band}
+                "cpu_baseline": cpu, "mixed": mixed, "mu": mu, "n_electrons": n_mu, "e_band": e_band}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -59,7 +59,8 @@ typedef enum {
 
 typedef enum {
     DCLNO_FP64 = 0,   /* every step in FP64 */
-    DCLNO_MIXED = 1   /* reserved: FP32/TF32 bulk with FP64 refinement */
+    DCLNO_MIXED = 1   /* the cubic contractions on BF16 tensor cores, FP64 emulated by
+                         8-bit slices (FP64-level accuracy); everything else FP64 */
 } dclno_precision;
 
 /* LNO eigenvalue flags returned by dclno_get_lnos (bit set per atom). */
@@ -196,6 +197,23 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
 dclno_status dclno_find_mu_noalloc(const double *eps, const double *q, long long count,
                                    double n_electrons, double kT, double *mu_out,
                                    double *nelec_out, void *cuda_stream);
+
+/*
+ * Self-consistency loop with linear density mixing (Sec. II.C: LNOs are updated
+ * every SCF step; H and S are held fixed here): nsteps times
+ *   rho_out = DC-LNO step(rho);  rho <- rho + alpha (rho_out - rho)
+ * on the device array rho [nval] (in/out).  No host synchronisation inside the
+ * loop: statuses, mu and the band energy stay on the device and are checked
+ * after it.  With use_graph != 0 one step is captured into a CUDA graph and
+ * replayed nsteps times (the context must use a non-default stream).
+ * mu_hist, nelec_hist, eband_hist: host arrays [nsteps] (nullable) of mu,
+ * N(mu) and E_band per step.  After the call the spectrum of the last step is
+ * available through dclno_get_spectrum.
+ */
+dclno_status dclno_scf_run(dclno_ctx *ctx, double *rho, int nsteps, double alpha,
+                           dclno_precision precision, double n_electrons, double kT,
+                           int use_graph, double *mu_hist, double *nelec_hist,
+                           double *eband_hist);
 
 /* ---- inspection (tests, benchmarks) ------------------------------------ */
 

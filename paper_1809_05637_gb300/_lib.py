@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_
 SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clusters", "dclno_compute_lnos",
            "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
-           "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc"]
+           "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run"]
 
 
 class DclnoError(RuntimeError):
@@ -76,6 +76,7 @@ def load_library():
         "dclno_kernel_time": ([P, ctypes.c_char_p, P, P], I),
         "dclno_measure_fp64_peaks": ([P, P], I),
         "dclno_find_mu_noalloc": ([P, P, ctypes.c_longlong, D, D, P, P, P], I),
+        "dclno_scf_run": ([P, P, I, D, I, D, D, I, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -203,6 +204,18 @@ class Context:
                                         int(precision), float(n_electrons), float(kT), _dptr(mu), _dptr(n),
                                         _dptr(e)))
         return mu.value, n.value, e.value
+
+    def scf_run(self, rho, nsteps, alpha, n_electrons, kT, precision=DCLNO_FP64, use_graph=False):
+        """nsteps of (DC-LNO step, rho <- rho + alpha (rho_out - rho)) on the device array rho.
+
+        Returns per-step (mu, N(mu), E_band) as numpy arrays."""
+        mu = np.zeros(nsteps)
+        n = np.zeros(nsteps)
+        e = np.zeros(nsteps)
+        self._check(self.lib.dclno_scf_run(self.h, _ptr(rho), int(nsteps), float(alpha), int(precision),
+                                           float(n_electrons), float(kT), int(bool(use_graph)), _ptr(mu),
+                                           _ptr(n), _ptr(e)))
+        return mu, n, e
 
     # ---- inspection
     def cluster_info(self):

@@ -60,6 +60,9 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_eband);
     dfree(c->d_rho_in);
     dfree(c->d_rho_out);
+    dfree(c->d_err);
+    dfree(c->d_hist);
+    c->hist_cap = 0;
     c->built = c->lnos_ready = c->solved = false;
 }
 
@@ -556,5 +559,98 @@ extern "C" dclno_status dclno_get_lnos(dclno_ctx* c, double* V, double* lre, dou
     if (lre) DCLNO_CUDA(c, cudaMemcpy(lre, c->d_lam_re, sizeof(double) * msum, cudaMemcpyDeviceToHost));
     if (lim) DCLNO_CUDA(c, cudaMemcpy(lim, c->d_lam_im, sizeof(double) * msum, cudaMemcpyDeviceToHost));
     if (flags) DCLNO_CUDA(c, cudaMemcpy(flags, c->d_lflags, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    return DCLNO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SCF loop: nsteps of (DC-LNO step, linear mixing), optionally as one CUDA graph
+// ---------------------------------------------------------------------------
+static dclno_status scf_one_step(dclno_ctx* c, double* rho, double alpha, dclno_precision prec, double ne, double kT) {
+    dclno_status st = DCLNO_OK;
+    if (c->has_lno_region) st = launch_lambda_lno(c, rho);
+    if (st == DCLNO_OK) st = launch_assemble(c);
+    if (st == DCLNO_OK) st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c) : launch_solve_fp64(c);
+    double mu = 0.0, nmu = 0.0;
+    if (st == DCLNO_OK) st = launch_find_mu(c, ne, kT, &mu, &nmu);
+    if (st == DCLNO_OK) st = launch_density(c, 0.0, kT, c->d_rho_out, nullptr);
+    if (st == DCLNO_OK) st = launch_scf_tail(c, rho, c->d_rho_out, alpha);
+    return st;
+}
+
+extern "C" dclno_status dclno_scf_run(dclno_ctx* c, double* rho, int nsteps, double alpha, dclno_precision prec,
+                                      double ne, double kT, int use_graph, double* mu_hist, double* nelec_hist,
+                                      double* eband_hist) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: build clusters first");
+    if (!rho || nsteps < 1 || !(kT > 0.0) || !(alpha > 0.0 && alpha <= 1.0))
+        return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: need rho, nsteps >= 1, kT > 0, 0 < alpha <= 1");
+    if (prec != DCLNO_FP64 && prec != DCLNO_MIXED) return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: unknown precision");
+    if (use_graph && c->stream == nullptr)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: graph capture needs a context on a non-default stream");
+    const size_t bytes = (size_t)c->nval * sizeof(double);
+    if (!c->d_rho_out) DCLNO_CUDA(c, cudaMalloc(&c->d_rho_out, bytes));
+    if (!c->d_err) DCLNO_CUDA(c, cudaMalloc(&c->d_err, 2 * sizeof(int)));
+    if (c->hist_cap < nsteps) {
+        if (c->d_hist) cudaFree(c->d_hist);
+        c->d_hist = nullptr;
+        c->hist_cap = 0;
+        DCLNO_CUDA(c, cudaMalloc(&c->d_hist, 3 * sizeof(double) * nsteps));
+        c->hist_cap = nsteps;
+    }
+    DCLNO_CUDA(c, cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->stream));
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    c->deferred = true;
+    dclno_status st = DCLNO_OK;
+    if (use_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const long long l0 = c->launches;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) st = cuda_err(c, e, "cudaStreamBeginCapture");
+        if (st == DCLNO_OK) {
+            st = scf_one_step(c, rho, alpha, prec, ne, kT);
+            e = cudaStreamEndCapture(c->stream, &graph);
+            if (st == DCLNO_OK && e != cudaSuccess) st = cuda_err(c, e, "cudaStreamEndCapture");
+        }
+        if (st == DCLNO_OK) {
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) st = cuda_err(c, e, "cudaGraphInstantiate");
+        }
+        const long long per_step = c->launches - l0;
+        for (int k = 0; st == DCLNO_OK && k < nsteps; ++k) {
+            e = cudaGraphLaunch(exec, c->stream);
+            if (e != cudaSuccess) st = cuda_err(c, e, "cudaGraphLaunch");
+        }
+        if (st == DCLNO_OK) {
+            e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = cuda_err(c, e, "cudaStreamSynchronize");
+        }
+        c->launches += per_step * (nsteps - 1);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    } else {
+        for (int k = 0; st == DCLNO_OK && k < nsteps; ++k) st = scf_one_step(c, rho, alpha, prec, ne, kT);
+    }
+    c->deferred = false;
+    c->prof_on = prof;
+    if (st != DCLNO_OK) return st;
+    int err[2] = {0, 0};
+    std::vector<double> hist(3 * (size_t)nsteps);
+    DCLNO_CUDA(c, cudaMemcpyAsync(err, c->d_err, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+    DCLNO_CUDA(c, cudaMemcpyAsync(hist.data(), c->d_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost,
+                                  c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nsteps; ++k) {
+        if (mu_hist) mu_hist[k] = hist[3 * k];
+        if (nelec_hist) nelec_hist[k] = hist[3 * k + 1];
+        if (eband_hist) eband_hist[k] = hist[3 * k + 2];
+    }
+    c->solved = true;
+    c->lnos_ready = true;
+    if (err[0] == 16) return set_err(c, DCLNO_ERR_NO_BRACKET, "dclno_scf_run: N_e outside the bracket of N(mu)");
+    if (err[0] == ST_NOT_SPD) return set_err(c, DCLNO_ERR_NOT_SPD, "dclno_scf_run: a cluster overlap is not positive definite");
+    if (err[0] != 0) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "dclno_scf_run: an eigensolver failed (status " + std::to_string(err[0]) + ")");
     return DCLNO_OK;
 }

@@ -144,6 +144,13 @@ struct dclno_ctx {
     double* d_rho_in = nullptr;
     double* d_rho_out = nullptr;
 
+    // deferred mode (SCF loop, graph capture): launchers skip every host readback;
+    // statuses accumulate in d_err, mu stays on the device, per-step results go to d_hist
+    bool deferred = false;
+    int* d_err = nullptr;       // [0] sticky worst status of the loop, [1] step counter
+    double* d_hist = nullptr;   // per step: mu, N(mu), E_band
+    int hist_cap = 0;
+
     // optional per-kernel CUDA-event timing (dclno_set_profiling)
     struct Prof {
         std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
@@ -197,6 +204,8 @@ dclno_status launch_solve_fp64(dclno_ctx* c);
 dclno_status launch_solve_mixed(dclno_ctx* c);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
 dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband);
+dclno_status launch_status_or(dclno_ctx* c);
+dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -403,6 +403,7 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
                                                    c->d_lam_re, c->d_lam_im, c->d_lflags, c->d_status);
     }
     DCLNO_LAUNCHED(c);
+    if (c->deferred) return launch_status_or(c);
     std::vector<int> st(N);
     DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
     DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));

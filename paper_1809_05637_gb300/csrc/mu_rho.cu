@@ -203,6 +203,7 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
         k_mu_final<<<1, 32, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars);
     }
     DCLNO_LAUNCHED(c);
+    if (c->deferred) return DCLNO_OK;  // mu stays in d_scalars[2]; a missing bracket is recorded by k_scf_record
     double h[10];
     DCLNO_CUDA(c, cudaMemcpyAsync(h, c->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -221,9 +222,10 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
 // ---------------------------------------------------------------------------
 // G[mu][a] = f(eps_mu) C_c[a][mu] (stored [n][mc] in the cluster's W area); band energy
 __global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double* __restrict__ arena,
-                           const double* __restrict__ eps, const double* __restrict__ q, double mu, double kT,
-                           double* __restrict__ eband) {
+                           const double* __restrict__ eps, const double* __restrict__ q, double mu_host,
+                           const double* __restrict__ mu_dev, double kT, double* __restrict__ eband) {
     const int ci = blockIdx.x;
+    const double mu = mu_dev ? *mu_dev : mu_host;
     const ClusterDesc d = cls[ci];
     const int n = d.n, mc = d.mc;
     const double* P = arena + d.cc_off;
@@ -383,7 +385,8 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
     for (int i = 0; i < N; ++i) maxrow = std::max(maxrow, c->row_ptr[i + 1] - c->row_ptr[i]);
     {
         ProfScope ps__(c, "k_rho_prep");
-        k_rho_prep<<<N, 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu, kT, c->d_eband);
+        k_rho_prep<<<N, 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
+                                             c->deferred ? c->d_scalars + 2 : nullptr, kT, c->d_eband);
     }
     DCLNO_LAUNCHED(c);
     {
@@ -412,7 +415,7 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
                                                           c->d_V, c->d_arena, rho_out);
     }
     DCLNO_LAUNCHED(c);
-    if (eband_out) {
+    if (eband_out && !c->deferred) {
         std::vector<double> eb(N);
         DCLNO_CUDA(c, cudaMemcpyAsync(eb.data(), c->d_eband, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
         DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -420,6 +423,58 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
         for (int i = 0; i < N; ++i) s += eb[i];
         *eband_out = s;
     }
+    return DCLNO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SCF loop support (deferred mode): sticky status, per-step record, linear mixing
+// ---------------------------------------------------------------------------
+__global__ void k_status_or(int n, const int* __restrict__ status, int* __restrict__ err) {
+    int w = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) w = max(w, status[i]);
+    for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+    __shared__ int red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) w = max(w, red[k]);
+        if (w > err[0]) err[0] = w;
+    }
+}
+
+// record mu, N(mu), E_band of this step (fixed summation order) and advance the step counter
+__global__ void k_scf_record(int n, const double* __restrict__ scal, const double* __restrict__ eband,
+                             int* __restrict__ err, double* __restrict__ hist, int cap) {
+    if (threadIdx.x != 0) return;
+    double e = 0.0;
+    for (int i = 0; i < n; ++i) e += eband[i];
+    const int k = err[1];
+    if (k < cap) {
+        hist[3 * k] = scal[2];
+        hist[3 * k + 1] = scal[3];
+        hist[3 * k + 2] = e;
+    }
+    if (scal[4] == 2.0 && err[0] < 16) err[0] = 16;  // no bracket for mu
+    err[1] = k + 1;
+}
+
+// rho <- rho + alpha (rho_out - rho)
+__global__ void k_mix(long long nval, double* __restrict__ rho, const double* __restrict__ rho_out, double alpha) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nval; t += (long long)gridDim.x * blockDim.x)
+        rho[t] = fma(alpha, rho_out[t] - rho[t], rho[t]);
+}
+
+dclno_status launch_status_or(dclno_ctx* c) {
+    k_status_or<<<1, 1024, 0, c->stream>>>(c->N, c->d_status, c->d_err);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha) {
+    k_scf_record<<<1, 32, 0, c->stream>>>(c->N, c->d_scalars, c->d_eband, c->d_err, c->d_hist, c->hist_cap);
+    DCLNO_LAUNCHED(c);
+    k_mix<<<152 * 8, 256, 0, c->stream>>>(c->nval, rho, rho_out, alpha);
+    DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
 

@@ -727,6 +727,7 @@ static dclno_status launch_solve(dclno_ctx* c) {
                                                                    c->d_q);
     }
     DCLNO_LAUNCHED(c);
+    if (c->deferred) return launch_status_or(c);
     std::vector<int> st(N);
     DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
     DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
