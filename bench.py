@@ -44,7 +44,18 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", choices=["rocksalt1728", "small64"], default="rocksalt1728",
+                   help="small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels")
     return p.parse_args()
+
+
+def make_workload(name):
+    import tbsystems as T
+    if name == "small64":
+        return T.small_lattice(4, 4, 4, a=2.5, jitter=0.05, exps=(0.1, 0.2, 0.45, 1.0, 2.2, 5.0),
+                               onsite=(-0.6, -0.4, -0.2, 0.0, 0.2, 0.4), e_per_atom=3.0, r_core=5.0, r_lno=8.0,
+                               k_lno=3, periodic=True, name="small64")
+    return T.make_system(2)
 
 
 # ---------------------------------------------------------------------------
@@ -186,7 +197,7 @@ def run_ours(args):
     from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context, measure_fp64_peaks
 
     dev = torch.device("cuda", local)
-    s = T.make_system(2)
+    s = make_workload(args.workload)
     rho_host = T.synthetic_density(s, seed=11)
     H = torch.from_numpy(s.H).to(dev)
     S = torch.from_numpy(s.S).to(dev)
@@ -307,7 +318,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "fp64", "clusters": ncl,
+                "config": {"workload": WORKLOAD if args.workload == "rocksalt1728" else args.workload,
+                           "precision": "fp64", "clusters": ncl,
                            "cluster_dim_min": int(dims.min()), "cluster_dim_max": int(dims.max()),
                            "parallelism": f"replicas x{world}",
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
