@@ -161,6 +161,16 @@ dclno_status dclno_density_matrix(dclno_ctx *ctx, double mu, double kT,
                                   double *rho_out, double *eband_out);
 
 /*
+ * Density matrix and energy density matrix rows together (Sec. II.C step (v)):
+ * rho as in dclno_density_matrix, and e_{0i alpha, Rj beta} =
+ * sum_mu f(eps_mu) eps_mu c_{mu,0i alpha} c_{mu,Rj beta} (Eq. (edm) with Eq. (Gi))
+ * into the device array edm_out [nval] (nullable: then rho only).  The energy
+ * density matrix needs M_i <= 16.  2 Tr(e S) equals the band energy.
+ */
+dclno_status dclno_density_matrices(dclno_ctx *ctx, double mu, double kT,
+                                    double *rho_out, double *edm_out, double *eband_out);
+
+/*
  * One whole DC-LNO step: compute_lnos(rho_in), solve_clusters(precision),
  * find_mu, density_matrix(rho_out).  With host_buffers != 0, rho_in and rho_out
  * are host arrays [nval] copied to and from the context's device buffers inside

@@ -21,7 +21,7 @@ __all__ = [
     "cholesky", "jacobi", "gen_eig", "nonsym_eig", "inverse_iter",
     "Cluster", "cluster_members", "lambda_blocks", "lnos", "compute_lnos",
     "assemble", "solve_cluster", "fermi", "n_of_mu", "find_mu", "density_rows",
-    "dclno_solve", "finish_step", "plain_dc_density", "full_diag", "dense_matrices",
+    "dclno_solve", "finish_step", "energy_density", "plain_dc_density", "full_diag", "dense_matrices",
     "cluster_dim", "time_ratio", "NoBracket", "NotSPD",
 ]
 
@@ -414,20 +414,23 @@ def find_mu(eps_all, q_all, n_e: float, kT: float, iters: int = 200):
 
 
 def density_rows(system, cl: Cluster, eps, C, V: dict, mu: float, kT: float,
-                 rho_out: np.ndarray, bidx_row: dict | None = None):
-    """Rows rho_{0i alpha, Rj beta} of the central atom i (Eq. (dm) with Eq. (Gi)).
+                 rho_out: np.ndarray, energy: bool = False):
+    """Rows of the central atom i of rho (Eq. (dm)) or, with energy=True, of the
+    energy density matrix e (Eq. (edm)), both with the spectral G^(i) of Eq. (Gi).
 
-    With the spectral G^(i) the energy integral of Eq. (dm) becomes
-    rho = sum_mu f(eps_mu) c_{mu,0i alpha} c_{mu,Rj beta}.  Columns of an LNO
-    member are returned to its PAOs with V_j; blocks of the S pattern outside
-    the cluster are zero (only elements with S != 0 are kept).
-    Writes into rho_out (the BSR value array) and returns the band energy
-    2 sum_mu f eps q of this cluster.
+    The energy integrals reduce to sums over the cluster's poles:
+    rho = sum_mu f(eps_mu) c_{mu,0i alpha} c_{mu,Rj beta} and
+    e = sum_mu f(eps_mu) eps_mu c_{mu,0i alpha} c_{mu,Rj beta}.  Columns of an LNO
+    member are returned to its PAOs with V_j; blocks of the S pattern outside the
+    cluster are zero (only elements with S != 0 are kept).  Writes the rows into
+    the BSR value array rho_out.
     """
     i = cl.centre
     c = cl.centre_slice
-    f = fermi((eps - mu) / kT)
-    rcl = (C[c, :] * f[None, :]) @ C.T  # M_i x n
+    w = fermi((eps - mu) / kT)
+    if energy:
+        w = w * eps
+    rcl = (C[c, :] * w[None, :]) @ C.T  # M_i x n
     where = {(int(cl.atoms[m]),) + tuple(int(x) for x in cl.shifts[m]): m for m in range(len(cl.atoms))}
     mi = int(system.norb[i])
     for b in range(int(system.row_ptr[i]), int(system.row_ptr[i + 1])):
@@ -441,6 +444,14 @@ def density_rows(system, cl: Cluster, eps, C, V: dict, mu: float, kT: float,
             cols = rcl[:, int(cl.offsets[m]):int(cl.offsets[m + 1])]
             blk = cols if cl.core[m] else cols @ V[j].T
         rho_out[o:o + mi * mj] = blk.reshape(-1)
+
+
+def energy_density(system, results: dict, V: dict, mu: float, kT: float) -> np.ndarray:
+    """Energy density matrix e (Eq. (edm)) rows of every solved cluster, BSR values."""
+    e = np.zeros_like(system.S)
+    for r in results.values():
+        density_rows(system, r.cluster, r.eps, r.C, V, mu, kT, e, energy=True)
+    return e
 
 
 @dataclasses.dataclass

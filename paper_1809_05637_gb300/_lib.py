@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_
 SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clusters", "dclno_compute_lnos",
            "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
-           "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run"]
+           "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
+           "dclno_density_matrices"]
 
 
 class DclnoError(RuntimeError):
@@ -77,6 +78,7 @@ def load_library():
         "dclno_measure_fp64_peaks": ([P, P], I),
         "dclno_find_mu_noalloc": ([P, P, ctypes.c_longlong, D, D, P, P, P], I),
         "dclno_scf_run": ([P, P, I, D, I, D, D, I, P, P, P], I),
+        "dclno_density_matrices": ([P, D, D, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -196,6 +198,13 @@ class Context:
     def density_matrix(self, mu, kT, rho_out):
         e = ctypes.c_double()
         self._check(self.lib.dclno_density_matrix(self.h, float(mu), float(kT), _ptr(rho_out), _dptr(e)))
+        return e.value
+
+    def density_matrices(self, mu, kT, rho_out, edm_out):
+        """rho and the energy density matrix e (Eq. (edm)) rows; returns the band energy."""
+        e = ctypes.c_double()
+        self._check(self.lib.dclno_density_matrices(self.h, float(mu), float(kT), _ptr(rho_out), _ptr(edm_out),
+                                                    _dptr(e)))
         return e.value
 
     def step(self, rho_in, rho_out, n_electrons, kT, host_buffers=False, precision=DCLNO_FP64):

@@ -497,6 +497,19 @@ extern "C" dclno_status dclno_density_matrix(dclno_ctx* c, double mu, double kT,
     return launch_density(c, mu, kT, rho_out, eband_out);
 }
 
+extern "C" dclno_status dclno_density_matrices(dclno_ctx* c, double mu, double kT, double* rho_out, double* edm_out,
+                                               double* eband_out) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->solved) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrices: solve clusters first");
+    if (!(kT > 0.0) || !rho_out) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrices: bad kT or rho_out");
+    if (edm_out)
+        for (const auto& d : c->cl)
+            if (2 * d.mc > 32)
+                return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrices: the energy density matrix needs M_i <= 16");
+    return launch_density(c, mu, kT, rho_out, eband_out, edm_out);
+}
+
 extern "C" dclno_status dclno_step(dclno_ctx* c, const double* rho_in, double* rho_out, int host_buffers,
                                    dclno_precision prec, double ne, double kT, double* mu_out,
                                    double* nelec_out, double* eband_out) {

@@ -203,7 +203,7 @@ dclno_status launch_pair_index(dclno_ctx* c);
 dclno_status launch_solve_fp64(dclno_ctx* c);
 dclno_status launch_solve_mixed(dclno_ctx* c);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
-dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband);
+dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband, double* e_out = nullptr);
 dclno_status launch_status_or(dclno_ctx* c);
 dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha);
 

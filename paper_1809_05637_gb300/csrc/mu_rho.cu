@@ -220,14 +220,16 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
 // ---------------------------------------------------------------------------
 // Density-matrix rows
 // ---------------------------------------------------------------------------
-// G[mu][a] = f(eps_mu) C_c[a][mu] (stored [n][mc] in the cluster's W area); band energy
+// G[mu][a] = f(eps_mu) C_c[a][mu] and, with the energy density matrix, G[mu][mc + a] =
+// f(eps_mu) eps_mu C_c[a][mu] (stored [n][w], w = mc or 2 mc, in the cluster's W area);
+// band energy of the cluster
 __global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double* __restrict__ arena,
                            const double* __restrict__ eps, const double* __restrict__ q, double mu_host,
-                           const double* __restrict__ mu_dev, double kT, double* __restrict__ eband) {
+                           const double* __restrict__ mu_dev, double kT, int with_e, double* __restrict__ eband) {
     const int ci = blockIdx.x;
     const double mu = mu_dev ? *mu_dev : mu_host;
     const ClusterDesc d = cls[ci];
-    const int n = d.n, mc = d.mc;
+    const int n = d.n, mc = d.mc, w = with_e ? 2 * mc : mc;
     const double* P = arena + d.cc_off;
     double* G = arena + d.aux_off + 3 * d.ld;
     const double inv = 1.0 / kT;
@@ -236,7 +238,11 @@ __global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double*
         const double e = eps[d.eig_off + m];
         const double f = fermi((e - mu) * inv);
         eb = fma(f * e, q[d.eig_off + m], eb);
-        for (int a = 0; a < mc; ++a) G[(size_t)m * mc + a] = f * P[(size_t)m * 2 * mc + a];
+        for (int a = 0; a < mc; ++a) {
+            const double c = P[(size_t)m * 2 * mc + a];
+            G[(size_t)m * w + a] = f * c;
+            if (with_e) G[(size_t)m * w + mc + a] = f * e * c;
+        }
     }
     __shared__ double red[8];
     eb = warp_sum(eb);
@@ -244,23 +250,23 @@ __global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double*
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
         eband[ci] = 2.0 * s;
     }
 }
 
 // G <- Z G: the logged rotations in reverse order acting on rows (i, i+1).
 // A warp packs floor(32 / mc) clusters, one lane per column of G.
-__global__ void k_replay_rev(int ncl, int per_warp, int mc_max, const ClusterDesc* __restrict__ cls,
+__global__ void k_replay_rev(int ncl, int per_warp, int w_max, int with_e, const ClusterDesc* __restrict__ cls,
                              const int* __restrict__ order, double* __restrict__ arena, const int* __restrict__ iters) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int grp = lane / mc_max, col = lane % mc_max;
+    const int grp = lane / w_max, col = lane % w_max;
     if (grp >= per_warp) return;
     const int item = wid * per_warp + grp;
     if (item >= ncl) return;
     const ClusterDesc d = cls[order[item]];
-    const int mc = d.mc;
+    const int mc = with_e ? 2 * d.mc : d.mc;  // columns of G
     if (col >= mc) return;
     double* G = arena + d.aux_off + 3 * d.ld;
     const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
@@ -294,10 +300,10 @@ __global__ void k_replay_rev(int ncl, int per_warp, int mc_max, const ClusterDes
 // X = L^-T G by back substitution; X overwrites G.
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDesc* __restrict__ cls,
                                                                 const int* __restrict__ order,
-                                                                double* __restrict__ arena) {
+                                                                double* __restrict__ arena, int with_e) {
     extern __shared__ double sm[];
     const ClusterDesc d = cls[order[blockIdx.x]];
-    const int n = d.n, ld = d.ld, mc = d.mc;
+    const int n = d.n, ld = d.ld, mc = with_e ? 2 * d.mc : d.mc;  // mc here: columns of G
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
@@ -337,47 +343,56 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDes
     }
 }
 
-// scatter the rows of atom i into the BSR pattern; one warp per block of row i
+// scatter the rows of atom i into the BSR pattern (rho from columns [0, mc) of X,
+// e from [mc, 2 mc) when e_out is given); one warp per block of row i
 __global__ void k_rho_scatter(int N, const ClusterDesc* __restrict__ cls, const MemberDesc* __restrict__ mem,
                               const int* __restrict__ norb, const long long* __restrict__ row_ptr,
                               const long long* __restrict__ key, const long long* __restrict__ blk_off,
                               const int* __restrict__ rowblk_member, const long long* __restrict__ voff, int k,
                               const double* __restrict__ V, const double* __restrict__ arena,
-                              double* __restrict__ rho) {
+                              double* __restrict__ rho, double* __restrict__ e_out) {
     const int i = blockIdx.y;
     const ClusterDesc d = cls[i];
-    const int mc = d.mc;
-    const double* X = arena + d.aux_off + 3 * d.ld;  // [n][mc]
+    const int mc = d.mc, w = e_out ? 2 * mc : mc;
+    const double* X = arena + d.aux_off + 3 * d.ld;  // [n][w]
     const int lane = threadIdx.x & 31;
     const long long b0 = row_ptr[i], b1 = row_ptr[i + 1];
     for (long long b = b0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < b1;
          b += (long long)gridDim.x * (blockDim.x >> 5)) {
         const int j = (int)(key[b] >> 24), mj = norb[j];
         double* out = rho + blk_off[b];
+        double* oute = e_out ? e_out + blk_off[b] : nullptr;
         const int m = rowblk_member[b];
         if (m < 0) {
-            for (int e = lane; e < mc * mj; e += 32) out[e] = 0.0;
+            for (int e = lane; e < mc * mj; e += 32) {
+                out[e] = 0.0;
+                if (oute) oute[e] = 0.0;
+            }
             continue;
         }
         const MemberDesc md = mem[d.mbeg + m];
-        if (md.core) {
-            for (int e = lane; e < mc * mj; e += 32) {
-                const int a = e / mj, bb = e % mj;
-                out[e] = X[(size_t)(md.off + bb) * mc + a];
+        const double* Vj = md.core ? nullptr : V + voff[j];
+        for (int e = lane; e < mc * mj; e += 32) {
+            const int a = e / mj, bb = e % mj;
+            double s = 0.0, se = 0.0;
+            if (md.core) {
+                s = X[(size_t)(md.off + bb) * w + a];
+                if (oute) se = X[(size_t)(md.off + bb) * w + mc + a];
+            } else {
+                for (int g = 0; g < k; ++g) {
+                    const double v = Vj[bb * k + g];
+                    s = fma(X[(size_t)(md.off + g) * w + a], v, s);
+                    if (oute) se = fma(X[(size_t)(md.off + g) * w + mc + a], v, se);
+                }
             }
-        } else {
-            const double* Vj = V + voff[j];
-            for (int e = lane; e < mc * mj; e += 32) {
-                const int a = e / mj, bb = e % mj;
-                double s = 0.0;
-                for (int g = 0; g < k; ++g) s = fma(X[(size_t)(md.off + g) * mc + a], Vj[bb * k + g], s);
-                out[e] = s;
-            }
+            out[e] = s;
+            if (oute) oute[e] = se;
         }
     }
 }
 
-dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband_out) {
+dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband_out, double* e_out) {
+    const int with_e = e_out ? 1 : 0;
     const int N = c->N;
     int maxn = 0;
     long long maxrow = 0;
@@ -386,16 +401,17 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
     {
         ProfScope ps__(c, "k_rho_prep");
         k_rho_prep<<<N, 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
-                                             c->deferred ? c->d_scalars + 2 : nullptr, kT, c->d_eband);
+                                             c->deferred ? c->d_scalars + 2 : nullptr, kT, with_e, c->d_eband);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_replay_rev");
         int mcmax = 1;
         for (const auto& d : c->cl) mcmax = std::max(mcmax, d.mc);
-        const int per_warp = std::max(1, 32 / mcmax);
+        const int wmax = with_e ? 2 * mcmax : mcmax;
+        const int per_warp = std::max(1, 32 / wmax);
         const int warps = (N + per_warp - 1) / per_warp;
-        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, mcmax, c->d_cl, c->d_order,
+        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, wmax, with_e, c->d_cl, c->d_order,
                                                                       c->d_arena, c->d_iters);
     }
     DCLNO_LAUNCHED(c);
@@ -403,7 +419,7 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_rho_qx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
         ProfScope ps__(c, "k_rho_qx");
-        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order, c->d_arena);
+        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order, c->d_arena, with_e);
     }
     DCLNO_LAUNCHED(c);
     const int wpb = 8;
@@ -412,7 +428,7 @@ dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out,
         ProfScope ps__(c, "k_rho_scatter");
         k_rho_scatter<<<dim3(bx, N), wpb * 32, 0, c->stream>>>(N, c->d_cl, c->d_mem, c->d_norb, c->d_row_ptr, c->d_key,
                                                           c->d_blk_off, c->d_rowblk_member, c->d_voff, c->k_lno,
-                                                          c->d_V, c->d_arena, rho_out);
+                                                          c->d_V, c->d_arena, rho_out, e_out);
     }
     DCLNO_LAUNCHED(c);
     if (eband_out && !c->deferred) {

@@ -81,6 +81,12 @@ def test_lno_step_cfg1(cfg1, cfg1_dc0):
     e = ctx.density_matrix(mu, s.kT, out)
     np.testing.assert_allclose(out.cpu().numpy(), rho, rtol=0, atol=1e-9)
     assert abs(e - e_band) <= 1e-9 * abs(e_band)
+    # rho and the energy density matrix together (Eq. (edm))
+    edm = torch.zeros_like(out)
+    e2 = ctx.density_matrices(mu, s.kT, out, edm)
+    np.testing.assert_allclose(out.cpu().numpy(), rho, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(edm.cpu().numpy(), O.energy_density(s, res, V, mu, s.kT), rtol=0, atol=1e-9)
+    assert e2 == e
     ctx.close()
 
 

@@ -182,3 +182,25 @@ def test_mixed_basis_step(mixed_system):
     assert abs(n_mu - s.n_electrons) < 1e-9
     assert abs(2 * _pair_trace(s, rho, s.S) - n_mu) < 1e-9
     assert abs(2 * _pair_trace(s, rho, s.H) - e_band) < 1e-9 * abs(e_band)
+
+
+def test_energy_density_matrix(cfg1, cfg1_exact, lno_step):
+    """Eq. (edm): 2 Tr(e S) = E_band; for a cluster covering the whole open system
+    e = S^-1 H rho exactly (H C = S C E), i.e. S e = H rho."""
+    lno, V, res, mu, n_mu, rho, e_band = lno_step
+    e = O.energy_density(cfg1, res, V, mu, cfg1.kT)
+    assert abs(2 * _pair_trace(cfg1, e, cfg1.S) - e_band) < 1e-9 * abs(e_band)
+    full = O.dclno_solve(cfg1, {}, 13.5, 13.5, 0)
+    mu_f, n_f, rho_f, e_f = O.finish_step(cfg1, full, {}, cfg1.n_electrons, cfg1.kT)
+    ed = O.energy_density(cfg1, full, {}, mu_f, cfg1.kT)
+    H, S, off = O.dense_matrices(cfg1)
+
+    def dense(x):
+        D = np.zeros_like(S)
+        brow = cfg1.block_rows()
+        for b in range(cfg1.nnzb):
+            i, j = int(brow[b]), int(cfg1.col[b])
+            D[off[i]:off[i + 1], off[j]:off[j + 1]] = cfg1.block(x, b)
+        return D
+
+    np.testing.assert_allclose(S @ dense(ed), H @ dense(rho_f), rtol=0, atol=1e-9)
