@@ -359,11 +359,14 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_tridiag(const Cluste
 
 // ---------------------------------------------------------------------------
 // Implicit QL on (d, e), one lane per cluster, lanes in lockstep.
-// Every pass of the loop advances each lane by one unit of work: up to 8
-// deflation checks (phase SEEK), the Wilkinson-type shift of a new sweep
-// (START) or one plane rotation (ROT), so a warp's FP64 instructions serve all
-// its clusters at once (an FP64 instruction costs the same whatever its number
-// of active lanes).  Rotations are logged as (c, s) per sweep:
+// Every pass of the loop advances each lane by a burst of up to 32 plane
+// rotations (phase ROT), the end of a sweep (FIN), up to 64 deflation checks
+// (SEEK) and the Wilkinson-type shift of a new sweep (START), so a warp's FP64
+// instructions serve all its clusters at once (an FP64 instruction costs the
+// same whatever its number of active lanes).  A sweep records the two smallest
+// negligible off-diagonals it leaves behind, so the next unreduced block is
+// known without a scan of e; SEEK runs only at the start and after a whole
+// block has converged.  Rotations are logged as (c, s) per sweep:
 // header block of a cluster = [nsweeps, (first rotation, first index i, count) x nsweeps],
 // i decreasing within a sweep.
 // ---------------------------------------------------------------------------
@@ -407,7 +410,9 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
         }
     }
     int l = 0, m = 0, mm = 0, i = 0, it = 0, nrot = 0, nsw = 0, start = 0;
-    int lowneg = 0;       // smallest index in (l, m] whose e became negligible during this sweep
+    // the two smallest indices in [l, m] whose e is negligible after this sweep (m counts
+    // as negligible): the next unreduced block is known without scanning e again
+    int lowneg = 0, low2 = 0;
     double s = 1.0, c = 1.0, p = 0.0, g = 0.0;
     double ce = 0.0, cd0 = 0.0, cd1 = 0.0;  // e[i], d[i], d[i+1] of the current rotation
     double ne = 0.0, nd = 0.0;              // e[i-1], d[i-1] loaded one rotation ahead
@@ -428,6 +433,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
                     e[i + 1] = 0.0;
                     d[i + 1] = cd1 - p;
                     e[m] = 0.0;
+                    low2 = lowneg;
                     lowneg = i + 1;  // e[i+1] = 0: the next block ends here
                     phase = QL_FIN;  // the sweep ends early, d[l] and e[l] untouched
                     continue;
@@ -449,14 +455,20 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
             g = fma(c, rr, -b);
             rot[nrot++] = make_double2(c, s);
             // deflation bookkeeping for the next sweep: e[i+1], d[i+1], d[i+2] are final now
-            if (i + 1 < m && negligible(r, dn, dnext)) lowneg = i + 1;
+            if (i + 1 < m && negligible(r, dn, dnext)) {
+                low2 = lowneg;
+                lowneg = i + 1;
+            }
             dnext = dn;
             if (--i < l) {
                 const double dl = d[l] - p;
                 d[l] = dl;
                 e[l] = g;
                 e[m] = 0.0;
-                if (negligible(g, dl, dn)) lowneg = l;
+                if (negligible(g, dl, dn)) {
+                    low2 = lowneg;
+                    lowneg = l;
+                }
                 phase = QL_FIN;
             } else {
                 cd1 = cd0;
@@ -477,8 +489,19 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
                 m = lowneg;  // the unreduced block shrank: no scan needed
                 phase = QL_START;
             } else {
-                mm = l;
-                phase = QL_SEEK;
+                // d[l] converged; the block below it ends at low2 unless e[l+1] is negligible too
+                ++l;
+                it = 0;
+                if (l >= n - 1) {
+                    phase = QL_DONE;
+                    hdr[0] = nsw;
+                } else if (low2 > l) {
+                    m = low2;
+                    phase = QL_START;
+                } else {
+                    mm = l;
+                    phase = QL_SEEK;
+                }
             }
         }
         if (phase == QL_SEEK) {
@@ -522,6 +545,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
                 i = m - 1;
                 start = nrot;
                 lowneg = m;
+                low2 = m;
                 ce = e[i];
                 cd0 = d[i];
                 cd1 = dm;
