@@ -127,6 +127,31 @@ dclno_status dclno_build_clusters(dclno_ctx *ctx, const dclno_system *sys,
 dclno_status dclno_compute_lnos(dclno_ctx *ctx, const double *rho);
 
 /*
+ * Memory admission.  Every cluster needs a private workspace while it is solved
+ * and until its density rows are written (about 8 (2.5 n^2 + 40 n) bytes for a
+ * cluster of dimension n: H^(i)/A, S^(i)/L, the QL rotation log, strips).
+ * dclno_build_clusters splits the clusters (in atom order) into contiguous
+ * batches whose workspace fits a budget: `bytes` when set here, otherwise the
+ * free device memory left after the context's other arrays, 1 GiB and room for
+ * two rho copies.  With one batch nothing changes.  With several, the solve
+ * runs batch by batch keeping only eps and q of earlier batches, and the
+ * density call solves every batch but the last one again before writing its
+ * rows (the same kernels on the same input give the same values), so a step
+ * costs up to one extra solve.  Takes effect at the next dclno_build_clusters;
+ * 0 restores the automatic budget.  A budget below one cluster's workspace
+ * makes dclno_build_clusters fail with DCLNO_ERR_OOM.  The paper has no
+ * counterpart (it distributes clusters over MPI ranks, Sec. III).
+ */
+dclno_status dclno_set_workspace_limit(dclno_ctx *ctx, size_t bytes);
+
+/*
+ * After dclno_build_clusters: the number of memory-admitted batches and the
+ * bytes of the workspace arena (the largest batch), both host scalars,
+ * nullable.
+ */
+dclno_status dclno_batch_info(dclno_ctx *ctx, int *nbatches_out, size_t *workspace_bytes_out);
+
+/*
  * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
  * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
  * implicit QL on the tridiagonal matrix, and the central-atom rows of the

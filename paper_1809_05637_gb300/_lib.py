@@ -19,7 +19,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
-           "dclno_density_matrices"]
+           "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info"]
 
 
 class DclnoError(RuntimeError):
@@ -79,6 +79,8 @@ def load_library():
         "dclno_find_mu_noalloc": ([P, P, ctypes.c_longlong, D, D, P, P, P], I),
         "dclno_scf_run": ([P, P, I, D, I, D, D, I, P, P, P], I),
         "dclno_density_matrices": ([P, D, D, P, P, P], I),
+        "dclno_set_workspace_limit": ([P, ctypes.c_size_t], I),
+        "dclno_batch_info": ([P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -163,6 +165,17 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_workspace_limit(self, nbytes):
+        """Workspace budget in bytes for the next build_clusters (0 = free device memory)."""
+        self._check(self.lib.dclno_set_workspace_limit(self.h, ctypes.c_size_t(int(nbytes))))
+
+    def batch_info(self):
+        """(number of memory-admitted batches, workspace arena bytes) after build_clusters."""
+        nb, ws = ctypes.c_int(), ctypes.c_size_t()
+        self._check(self.lib.dclno_batch_info(self.h, ctypes.cast(ctypes.byref(nb), ctypes.c_void_p),
+                                              ctypes.cast(ctypes.byref(ws), ctypes.c_void_p)))
+        return nb.value, ws.value
 
     # ---- the five calls of a DC-LNO step
     def build_clusters(self, pos, cell, pbc, norb, row_ptr, col, shift, blk_off, H, S, r_core, r_lno, k_lno):

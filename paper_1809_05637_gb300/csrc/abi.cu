@@ -277,7 +277,7 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     std::vector<int> rowblk_member(c->nnzb, -1);
     std::vector<int> mem_cl;
     c->has_lno_region = false;
-    long long mat = 0, eig = 0, its = 0, pairs = 0;
+    long long eig = 0, pairs = 0;
     for (int i = 0; i < N; ++i) {
         const double xi = c->pos[3 * i], yi = c->pos[3 * i + 1], zi = c->pos[3 * i + 2];
         std::vector<Cand> cand;
@@ -329,30 +329,15 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
             auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key[b], -1));
             if (it != keys.end() && it->first == key[b]) rowblk_member[b] = it->second;
         }
-        // workspace layout (doubles): A, L (n x ld each), d/e/tau (ld each), W (32 ld), P ([n][2 mc]),
-        // rotation log (2 rot_cap)
-        const long long n = d.n;
-        d.mat_off = mat;
-        mat += 2 * n * d.ld;
-        d.aux_off = mat;
-        mat += 3LL * d.ld + 32LL * d.ld;  // d, e, tau, W: each sub-region starts on a multiple of 4 doubles
-        d.cc_off = mat;
-        mat += 2LL * d.mc * d.ld;
-        d.rot_cap = (int)std::min<long long>(3 * n * n / 2 + 64 * n + 64, 2000000000LL);
-        d.rot_off = mat;
-        mat += 2LL * d.rot_cap;
-        mat = (mat + 31) & ~31LL;  // 256-byte alignment of every cluster's workspace
-        d.it_cap = 8 * (int)n + 64;
-        d.it_off = its;
-        its += 3LL * d.it_cap;
+        d.rot_cap = (int)std::min<long long>(3 * (long long)d.n * d.n / 2 + 64LL * d.n + 64, 2000000000LL);
+        d.it_cap = 8 * d.n + 64;
         d.eig_off = eig;
-        eig += n;
+        eig += d.n;
         d.pair_off = pairs;
         pairs += (long long)d.nmem * d.nmem;
     }
     c->total_dim = eig;
     c->pair_total = pairs;
-    c->arena_doubles = (size_t)mat;
     // LNO-transformed copies of every stored block: V_j1^T X, X V_j2, V_j1^T X V_j2 for X = H, S
     std::vector<long long> tblk_off(c->nnzb, 0), brow(c->nnzb);
     long long tb = 0;
@@ -367,9 +352,94 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
         }
     c->tblk_total = tb;
     std::vector<int> brow32(brow.begin(), brow.end());
+
+    // ---- memory admission: per-cluster workspace (doubles): A, L (n x ld each), d/e/tau (ld each),
+    // W (32 ld), P ([n][2 mc]), rotation log (2 rot_cap), 256-byte aligned; sweep headers 3 it_cap ints
+    auto ws_doubles = [](const ClusterDesc& d) {
+        const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap;
+        return (m + 31) & ~31LL;
+    };
+    auto ws_bytes = [&](const ClusterDesc& d) { return 8 * ws_doubles(d) + 12LL * d.it_cap; };
+    size_t free_b = 0, tot_b = 0;
+    DCLNO_CUDA(c, cudaMemGetInfo(&free_b, &tot_b));
+    long long msum_all = 0;
+    for (int i = 0; i < N; ++i) msum_all += c->norb[i];
+    const size_t other = (size_t)c->total_dim * 16 + (size_t)c->nnzb * 48 + (size_t)c->pair_total * 4 +
+                         (size_t)c->tblk_total * 8 + (size_t)msum_all * (8 * k_lno + 16 + 8 * DCLNO_MAX_M) +
+                         (size_t)N * 64 + c->mem.size() * 24;
+    const size_t reserve = (size_t)(1u << 30) + 2 * (size_t)c->nval * sizeof(double);  // host-buffer / SCF rho copies
+    long long budget;
+    if (c->ws_limit) budget = (long long)c->ws_limit;
+    else budget = free_b > other + reserve ? (long long)(free_b - other - reserve) : 0;
+    long long total_ws = 0, max_ws = 0;
+    for (int i = 0; i < N; ++i) {
+        total_ws += ws_bytes(c->cl[i]);
+        max_ws = std::max(max_ws, ws_bytes(c->cl[i]));
+    }
+    if (max_ws > budget)
+        return set_err(c, DCLNO_ERR_OOM, "the workspace of one cluster (" + std::to_string(max_ws >> 20) +
+                                             " MiB) exceeds the workspace budget (" + std::to_string(budget >> 20) +
+                                             " MiB)");
+    const long long nb_min = (total_ws + budget - 1) / budget;
+    const long long target = (total_ws + nb_min - 1) / nb_min;
+    c->batches.clear();
+    {
+        Batch cur;
+        long long acc = 0;
+        for (int i = 0; i < N; ++i) {
+            const long long w = ws_bytes(c->cl[i]);
+            if (acc > 0 && acc + w > budget) {
+                cur.id_hi = i;
+                c->batches.push_back(cur);
+                cur = Batch();
+                cur.id_lo = i;
+                acc = 0;
+            }
+            acc += w;
+            if (acc >= target && i + 1 < N) {
+                cur.id_hi = i + 1;
+                c->batches.push_back(cur);
+                cur = Batch();
+                cur.id_lo = i + 1;
+                acc = 0;
+            }
+        }
+        cur.id_hi = N;
+        if (cur.id_hi > cur.id_lo) c->batches.push_back(cur);
+    }
+    // offsets relative to the batch; order = each batch's clusters by decreasing n
     c->order.resize(N);
-    std::iota(c->order.begin(), c->order.end(), 0);
-    std::stable_sort(c->order.begin(), c->order.end(), [&](int a, int b) { return c->cl[a].n > c->cl[b].n; });
+    long long arena_max = 0, its_max = 0;
+    for (Batch& b : c->batches) {
+        long long mat = 0, its = 0;
+        b.maxn = 0;
+        b.mcmax = 1;
+        for (int i = b.id_lo; i < b.id_hi; ++i) {
+            ClusterDesc& d = c->cl[i];
+            d.mat_off = mat;
+            d.aux_off = mat + 2LL * d.n * d.ld;  // d, e, tau, W: each sub-region starts on a multiple of 4 doubles
+            d.cc_off = d.aux_off + 35LL * d.ld;
+            d.rot_off = d.cc_off + 2LL * d.mc * d.ld;
+            mat += ws_doubles(d);
+            d.it_off = its;
+            its += 3LL * d.it_cap;
+            b.maxn = std::max(b.maxn, d.n);
+            b.mcmax = std::max(b.mcmax, d.mc);
+        }
+        b.arena_doubles = mat;
+        b.iters = its;
+        arena_max = std::max(arena_max, mat);
+        its_max = std::max(its_max, its);
+        b.obeg = b.id_lo;
+        b.oend = b.id_hi;
+        std::iota(c->order.begin() + b.obeg, c->order.begin() + b.oend, b.id_lo);
+        std::stable_sort(c->order.begin() + b.obeg, c->order.begin() + b.oend,
+                         [&](int x, int y) { return c->cl[x].n > c->cl[y].n; });
+        b.mbeg = c->cl[b.id_lo].mbeg;
+        b.mend = b.id_hi < N ? c->cl[b.id_hi].mbeg : (long long)c->mem.size();
+    }
+    c->arena_doubles = (size_t)arena_max;
+    c->resident = -1;
 
     // ---- LNO storage offsets
     std::vector<long long> voff(N + 1), loff(N + 1), moff(N + 1);
@@ -383,10 +453,7 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     c->l_total = loff[N];
 
     // ---- device memory
-    size_t free_b = 0, tot_b = 0;
-    DCLNO_CUDA(c, cudaMemGetInfo(&free_b, &tot_b));
-    size_t need = c->arena_doubles * 8 + (size_t)its * 4 + (size_t)c->total_dim * 16 + (size_t)c->nnzb * 48 +
-                  (size_t)c->pair_total * 4 + (size_t)c->tblk_total * 8;
+    const size_t need = c->arena_doubles * 8 + (size_t)its_max * 4 + other;
     if (need + (size_t)(1u << 30) > free_b) {
         free_clusters(c);
         return set_err(c, DCLNO_ERR_OOM,
@@ -418,7 +485,7 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_status, sizeof(int) * N)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_arena, c->arena_doubles * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_iters, sizeof(int) * std::max<long long>(its, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_iters, sizeof(int) * std::max<long long>(its_max, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_eps, sizeof(double) * c->total_dim)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_q, sizeof(double) * c->total_dim)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_V, sizeof(double) * std::max<long long>(c->v_total, 1))) != cudaSuccess ||
@@ -461,6 +528,49 @@ extern "C" dclno_status dclno_compute_lnos(dclno_ctx* c, const double* rho) {
     return DCLNO_OK;
 }
 
+// assemble and solve one batch; its workspace becomes the resident one
+static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
+    const Batch& b = c->batches[bi];
+    c->resident = -1;
+    dclno_status st = launch_assemble(c, b);
+    if (st == DCLNO_OK) st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c, b) : launch_solve_fp64(c, b);
+    if (st == DCLNO_OK) c->resident = bi;
+    return st;
+}
+
+// every batch: assemble + solve (eps and q of all clusters)
+static dclno_status solve_all(dclno_ctx* c, dclno_precision prec) {
+    dclno_status st = launch_lno_blocks(c);
+    for (int bi = 0; st == DCLNO_OK && bi < (int)c->batches.size(); ++bi) st = solve_batch(c, bi, prec);
+    if (st == DCLNO_OK) c->solved_prec = prec;
+    return st;
+}
+
+// density rows of every batch, the resident one first; the others are solved again
+// (the same kernels on the same inputs give the same eps, q and workspace)
+static dclno_status density_all(dclno_ctx* c, double mu, double kT, double* rho_out, double* e_out) {
+    const int nb = (int)c->batches.size();
+    const int r0 = c->resident >= 0 ? c->resident : 0;
+    dclno_status st = DCLNO_OK;
+    for (int k = 0; st == DCLNO_OK && k < nb; ++k) {
+        const int bi = (r0 + k) % nb;
+        if (bi != c->resident) st = solve_batch(c, bi, c->solved_prec);
+        if (st == DCLNO_OK) st = launch_density(c, c->batches[bi], mu, kT, rho_out, e_out);
+    }
+    return st;
+}
+
+static dclno_status read_eband(dclno_ctx* c, double* eband_out) {
+    if (!eband_out) return DCLNO_OK;
+    std::vector<double> eb(c->N);
+    DCLNO_CUDA(c, cudaMemcpyAsync(eb.data(), c->d_eband, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    double s = 0.0;
+    for (int i = 0; i < c->N; ++i) s += eb[i];
+    *eband_out = s;
+    return DCLNO_OK;
+}
+
 extern "C" dclno_status dclno_solve_clusters(dclno_ctx* c, dclno_precision prec) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
@@ -468,9 +578,8 @@ extern "C" dclno_status dclno_solve_clusters(dclno_ctx* c, dclno_precision prec)
     if (!c->lnos_ready) return set_err(c, DCLNO_ERR_NO_LNOS, "dclno_solve_clusters: compute LNOs first");
     if (prec != DCLNO_FP64 && prec != DCLNO_MIXED)
         return set_err(c, DCLNO_ERR_ARG, "dclno_solve_clusters: unknown precision");
-    dclno_status st = launch_assemble(c);
-    if (st != DCLNO_OK) return st;
-    st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c) : launch_solve_fp64(c);
+    c->solved = false;
+    dclno_status st = solve_all(c, prec);
     if (st != DCLNO_OK) return st;
     c->solved = true;
     return DCLNO_OK;
@@ -494,7 +603,9 @@ extern "C" dclno_status dclno_density_matrix(dclno_ctx* c, double mu, double kT,
     c->err.clear();
     if (!c->solved) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix: solve clusters first");
     if (!(kT > 0.0) || !rho_out) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix: bad kT or rho_out");
-    return launch_density(c, mu, kT, rho_out, eband_out);
+    dclno_status st = density_all(c, mu, kT, rho_out, nullptr);
+    if (st != DCLNO_OK) return st;
+    return read_eband(c, eband_out);
 }
 
 extern "C" dclno_status dclno_density_matrices(dclno_ctx* c, double mu, double kT, double* rho_out, double* edm_out,
@@ -507,7 +618,24 @@ extern "C" dclno_status dclno_density_matrices(dclno_ctx* c, double mu, double k
         for (const auto& d : c->cl)
             if (2 * d.mc > 32)
                 return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrices: the energy density matrix needs M_i <= 16");
-    return launch_density(c, mu, kT, rho_out, eband_out, edm_out);
+    dclno_status st = density_all(c, mu, kT, rho_out, edm_out);
+    if (st != DCLNO_OK) return st;
+    return read_eband(c, eband_out);
+}
+
+extern "C" dclno_status dclno_set_workspace_limit(dclno_ctx* c, size_t bytes) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    c->ws_limit = bytes;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_batch_info(dclno_ctx* c, int* nbatches, size_t* workspace_bytes) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_batch_info: build clusters first");
+    if (nbatches) *nbatches = (int)c->batches.size();
+    if (workspace_bytes) *workspace_bytes = c->arena_doubles * sizeof(double);
+    return DCLNO_OK;
 }
 
 extern "C" dclno_status dclno_step(dclno_ctx* c, const double* rho_in, double* rho_out, int host_buffers,
@@ -581,11 +709,10 @@ extern "C" dclno_status dclno_get_lnos(dclno_ctx* c, double* V, double* lre, dou
 static dclno_status scf_one_step(dclno_ctx* c, double* rho, double alpha, dclno_precision prec, double ne, double kT) {
     dclno_status st = DCLNO_OK;
     if (c->has_lno_region) st = launch_lambda_lno(c, rho);
-    if (st == DCLNO_OK) st = launch_assemble(c);
-    if (st == DCLNO_OK) st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c) : launch_solve_fp64(c);
+    if (st == DCLNO_OK) st = solve_all(c, prec);
     double mu = 0.0, nmu = 0.0;
     if (st == DCLNO_OK) st = launch_find_mu(c, ne, kT, &mu, &nmu);
-    if (st == DCLNO_OK) st = launch_density(c, 0.0, kT, c->d_rho_out, nullptr);
+    if (st == DCLNO_OK) st = density_all(c, 0.0, kT, c->d_rho_out, nullptr);
     if (st == DCLNO_OK) st = launch_scf_tail(c, rho, c->d_rho_out, alpha);
     return st;
 }

@@ -105,8 +105,9 @@ __global__ void k_lno_blocks(long long nnzb, int k, const int* __restrict__ brow
     }
 }
 
-// gather: one CTA per (cluster, m1), warps over m2, lanes over the block's elements
-__global__ void __launch_bounds__(128) k_assemble(const ClusterDesc* __restrict__ cls,
+// gather: one CTA per (cluster, m1) of the batch's members from mbeg, warps over m2,
+// lanes over the block's elements
+__global__ void __launch_bounds__(128) k_assemble(long long mbeg, const ClusterDesc* __restrict__ cls,
                                                   const MemberDesc* __restrict__ mem,
                                                   const int* __restrict__ mem_cl, const int* __restrict__ norb,
                                                   const int* __restrict__ pairblk,
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(128) k_assemble(const ClusterDesc* __restrict_
                                                   const long long* __restrict__ tblk_off, int k,
                                                   const double* __restrict__ H, const double* __restrict__ S,
                                                   const double* __restrict__ tblk, double* __restrict__ arena) {
-    const long long g1 = blockIdx.x;
+    const long long g1 = mbeg + blockIdx.x;
     const ClusterDesc d = cls[mem_cl[g1]];
     const MemberDesc a = mem[g1];
     const int m1 = (int)(g1 - d.mbeg);
@@ -168,22 +169,26 @@ dclno_status launch_pair_index(dclno_ctx* c) {
     return DCLNO_OK;
 }
 
-dclno_status launch_assemble(dclno_ctx* c) {
-    const long long nm = (long long)c->mem.size();
+dclno_status launch_lno_blocks(dclno_ctx* c) {
+    if (!c->has_lno_region) return DCLNO_OK;
+    ProfScope ps__(c, "k_lno_blocks");
+    const long long warps = c->nnzb;
+    const int grid = (int)std::min<long long>((warps * 32 + 255) / 256, 152LL * 64);
+    k_lno_blocks<<<grid, 256, 0, c->stream>>>(c->nnzb, c->k_lno, c->d_brow, c->d_key, c->d_norb, c->d_blk_off,
+                                              c->d_voff, c->d_tblk_off, c->H, c->S, c->d_V, c->d_tblk);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+dclno_status launch_assemble(dclno_ctx* c, const Batch& b) {
+    const long long nm = b.mend - b.mbeg;
     if (nm > 2147483647LL) return set_err(c, DCLNO_ERR_ARG, "too many cluster members");
-    if (c->has_lno_region) {
-        ProfScope ps__(c, "k_lno_blocks");
-        const long long warps = c->nnzb;
-        const int grid = (int)std::min<long long>((warps * 32 + 255) / 256, 152LL * 64);
-        k_lno_blocks<<<grid, 256, 0, c->stream>>>(c->nnzb, c->k_lno, c->d_brow, c->d_key, c->d_norb, c->d_blk_off,
-                                                  c->d_voff, c->d_tblk_off, c->H, c->S, c->d_V, c->d_tblk);
-        DCLNO_LAUNCHED(c);
-    }
+    if (nm == 0) return DCLNO_OK;
     {
         ProfScope ps__(c, "k_assemble");
-        k_assemble<<<(unsigned)nm, 128, 0, c->stream>>>(c->d_cl, c->d_mem, c->d_mem_cl, c->d_norb, c->d_pairblk,
-                                                        c->d_blk_off, c->d_tblk_off, c->k_lno, c->H, c->S, c->d_tblk,
-                                                        c->d_arena);
+        k_assemble<<<(unsigned)nm, 128, 0, c->stream>>>(b.mbeg, c->d_cl, c->d_mem, c->d_mem_cl, c->d_norb,
+                                                        c->d_pairblk, c->d_blk_off, c->d_tblk_off, c->k_lno, c->H,
+                                                        c->S, c->d_tblk, c->d_arena);
     }
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;

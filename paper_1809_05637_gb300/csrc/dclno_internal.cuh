@@ -69,6 +69,18 @@ enum : int {
     ST_BAD_LNO = 4,
 };
 
+// A memory-admitted batch: a contiguous range of cluster ids whose workspace is
+// resident at once.  Arena offsets (mat_off, aux_off, cc_off, rot_off) and sweep
+// header offsets (it_off) of its clusters are relative to the batch; eig_off and
+// pair_off are global.
+struct Batch {
+    int id_lo = 0, id_hi = 0;       // clusters [id_lo, id_hi)
+    int obeg = 0, oend = 0;         // the same clusters in `order` (by decreasing n)
+    long long mbeg = 0, mend = 0;   // their members
+    int maxn = 0, mcmax = 1;
+    long long arena_doubles = 0, iters = 0;
+};
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------
@@ -104,7 +116,11 @@ struct dclno_ctx {
     int k_lno = 0;
     bool has_lno_region = false;
     std::vector<ClusterDesc> cl;      // one per atom, atom order
-    std::vector<int> order;           // clusters by decreasing n (scheduling)
+    std::vector<int> order;           // per batch, its clusters by decreasing n (scheduling)
+    std::vector<Batch> batches;       // memory-admitted batches (one when everything fits)
+    int resident = -1;                // batch whose solved workspace is in the arena
+    dclno_precision solved_prec = DCLNO_FP64;
+    size_t ws_limit = 0;              // workspace limit in bytes (0 = free device memory)
     std::vector<MemberDesc> mem;
     long long total_dim = 0;
     ClusterDesc* d_cl = nullptr;
@@ -198,12 +214,14 @@ dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where);
 
 // kernels' host-side launchers (one per .cu file)
 dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
-dclno_status launch_assemble(dclno_ctx* c);
+dclno_status launch_lno_blocks(dclno_ctx* c);
+dclno_status launch_assemble(dclno_ctx* c, const Batch& b);
 dclno_status launch_pair_index(dclno_ctx* c);
-dclno_status launch_solve_fp64(dclno_ctx* c);
-dclno_status launch_solve_mixed(dclno_ctx* c);
+dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b);
+dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
-dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband, double* e_out = nullptr);
+dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out,
+                            double* e_out = nullptr);
 dclno_status launch_status_or(dclno_ctx* c);
 dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha);
 

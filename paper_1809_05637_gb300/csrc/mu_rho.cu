@@ -223,10 +223,10 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
 // G[mu][a] = f(eps_mu) C_c[a][mu] and, with the energy density matrix, G[mu][mc + a] =
 // f(eps_mu) eps_mu C_c[a][mu] (stored [n][w], w = mc or 2 mc, in the cluster's W area);
 // band energy of the cluster
-__global__ void k_rho_prep(int ncl, const ClusterDesc* __restrict__ cls, double* __restrict__ arena,
+__global__ void k_rho_prep(int id_lo, const ClusterDesc* __restrict__ cls, double* __restrict__ arena,
                            const double* __restrict__ eps, const double* __restrict__ q, double mu_host,
                            const double* __restrict__ mu_dev, double kT, int with_e, double* __restrict__ eband) {
-    const int ci = blockIdx.x;
+    const int ci = id_lo + blockIdx.x;
     const double mu = mu_dev ? *mu_dev : mu_host;
     const ClusterDesc d = cls[ci];
     const int n = d.n, mc = d.mc, w = with_e ? 2 * mc : mc;
@@ -345,13 +345,13 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDes
 
 // scatter the rows of atom i into the BSR pattern (rho from columns [0, mc) of X,
 // e from [mc, 2 mc) when e_out is given); one warp per block of row i
-__global__ void k_rho_scatter(int N, const ClusterDesc* __restrict__ cls, const MemberDesc* __restrict__ mem,
+__global__ void k_rho_scatter(int id_lo, const ClusterDesc* __restrict__ cls, const MemberDesc* __restrict__ mem,
                               const int* __restrict__ norb, const long long* __restrict__ row_ptr,
                               const long long* __restrict__ key, const long long* __restrict__ blk_off,
                               const int* __restrict__ rowblk_member, const long long* __restrict__ voff, int k,
                               const double* __restrict__ V, const double* __restrict__ arena,
                               double* __restrict__ rho, double* __restrict__ e_out) {
-    const int i = blockIdx.y;
+    const int i = id_lo + blockIdx.y;
     const ClusterDesc d = cls[i];
     const int mc = d.mc, w = e_out ? 2 * mc : mc;
     const double* X = arena + d.aux_off + 3 * d.ld;  // [n][w]
@@ -391,54 +391,44 @@ __global__ void k_rho_scatter(int N, const ClusterDesc* __restrict__ cls, const 
     }
 }
 
-dclno_status launch_density(dclno_ctx* c, double mu, double kT, double* rho_out, double* eband_out, double* e_out) {
+dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out, double* e_out) {
     const int with_e = e_out ? 1 : 0;
-    const int N = c->N;
-    int maxn = 0;
+    const int N = b.oend - b.obeg;  // clusters of the batch
+    if (N == 0) return DCLNO_OK;
+    const int maxn = b.maxn;
     long long maxrow = 0;
-    for (const auto& d : c->cl) maxn = std::max(maxn, d.n);
-    for (int i = 0; i < N; ++i) maxrow = std::max(maxrow, c->row_ptr[i + 1] - c->row_ptr[i]);
+    for (int i = b.id_lo; i < b.id_hi; ++i) maxrow = std::max(maxrow, c->row_ptr[i + 1] - c->row_ptr[i]);
     {
         ProfScope ps__(c, "k_rho_prep");
-        k_rho_prep<<<N, 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
+        k_rho_prep<<<N, 256, 0, c->stream>>>(b.id_lo, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
                                              c->deferred ? c->d_scalars + 2 : nullptr, kT, with_e, c->d_eband);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_replay_rev");
-        int mcmax = 1;
-        for (const auto& d : c->cl) mcmax = std::max(mcmax, d.mc);
-        const int wmax = with_e ? 2 * mcmax : mcmax;
+        const int wmax = with_e ? 2 * b.mcmax : b.mcmax;
         const int per_warp = std::max(1, 32 / wmax);
         const int warps = (N + per_warp - 1) / per_warp;
-        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, wmax, with_e, c->d_cl, c->d_order,
-                                                                      c->d_arena, c->d_iters);
+        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, wmax, with_e, c->d_cl,
+                                                                      c->d_order + b.obeg, c->d_arena, c->d_iters);
     }
     DCLNO_LAUNCHED(c);
     const size_t sm = (size_t)(maxn + 32 * (DCLNO_SOLVE_THREADS / 32)) * sizeof(double);
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_rho_qx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
         ProfScope ps__(c, "k_rho_qx");
-        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order, c->d_arena, with_e);
+        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, with_e);
     }
     DCLNO_LAUNCHED(c);
     const int wpb = 8;
-    const int bx = (int)std::min<long long>((maxrow + wpb - 1) / wpb, 64);
+    const int bx = (int)std::max<long long>(1, std::min<long long>((maxrow + wpb - 1) / wpb, 64));
     {
         ProfScope ps__(c, "k_rho_scatter");
-        k_rho_scatter<<<dim3(bx, N), wpb * 32, 0, c->stream>>>(N, c->d_cl, c->d_mem, c->d_norb, c->d_row_ptr, c->d_key,
-                                                          c->d_blk_off, c->d_rowblk_member, c->d_voff, c->k_lno,
-                                                          c->d_V, c->d_arena, rho_out, e_out);
+        k_rho_scatter<<<dim3(bx, N), wpb * 32, 0, c->stream>>>(b.id_lo, c->d_cl, c->d_mem, c->d_norb, c->d_row_ptr,
+                                                          c->d_key, c->d_blk_off, c->d_rowblk_member, c->d_voff,
+                                                          c->k_lno, c->d_V, c->d_arena, rho_out, e_out);
     }
     DCLNO_LAUNCHED(c);
-    if (eband_out && !c->deferred) {
-        std::vector<double> eb(N);
-        DCLNO_CUDA(c, cudaMemcpyAsync(eb.data(), c->d_eband, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
-        DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
-        double s = 0.0;
-        for (int i = 0; i < N; ++i) s += eb[i];
-        *eband_out = s;
-    }
     return DCLNO_OK;
 }
 

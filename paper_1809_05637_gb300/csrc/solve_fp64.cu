@@ -675,10 +675,11 @@ __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const Cluster
 }
 
 // eigenvalues and weights: eps_mu = d_mu, q_mu = sum_a P[mu][a] P[mu][mc + a]
-__global__ void k_weights(int ncl, const ClusterDesc* __restrict__ cls, const double* __restrict__ arena,
-                          const int* __restrict__ status, double* __restrict__ eps, double* __restrict__ q) {
-    const int ci = blockIdx.y;
-    if (ci >= ncl || status[ci] != ST_OK) return;
+__global__ void k_weights(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                          const double* __restrict__ arena, const int* __restrict__ status,
+                          double* __restrict__ eps, double* __restrict__ q) {
+    const int ci = order[blockIdx.y];
+    if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     const int n = d.n, mc = d.mc;
     const double* dv = arena + d.aux_off;
@@ -693,10 +694,11 @@ __global__ void k_weights(int ncl, const ClusterDesc* __restrict__ cls, const do
 
 
 template <bool EMU>
-static dclno_status launch_solve(dclno_ctx* c) {
-    const int N = c->N;
-    int maxn = 0;
-    for (const auto& d : c->cl) maxn = std::max(maxn, d.n);
+static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
+    const int N = b.oend - b.obeg;  // clusters of the batch
+    if (N == 0) return DCLNO_OK;
+    const int maxn = b.maxn;
+    const int* order = c->d_order + b.obeg;
     const int nw = DCLNO_SOLVE_THREADS / 32;
     const size_t gemm_doubles = EMU ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
     size_t sm_chol = (size_t)(NB * DK_LD + NB + gemm_doubles) * sizeof(double);
@@ -711,61 +713,63 @@ static dclno_status launch_solve(dclno_ctx* c) {
 
     {
         ProfScope ps__(c, "k_cholesky");
-        k_cholesky<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_cholesky<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_congruence");
-        k_congruence<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_congruence<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_tridiag");
-        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_ql");
-        k_ql<<<(N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, c->d_order, c->d_arena, c->d_iters, c->d_status);
+        k_ql<<<(N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, order, c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_apply_q_rows");
-        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, c->d_order, c->d_arena, c->d_status);
+        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_replay_fwd");
-        int mcmax = 1;
-        for (const auto& d : c->cl) mcmax = std::max(mcmax, d.mc);
+        const int mcmax = b.mcmax;
         const int per_warp = std::max(1, 32 / mcmax);
         const int items = 2 * N;
         const int warps = (items + per_warp - 1) / per_warp;
-        k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, c->d_order,
+        k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, order,
                                                                       c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_weights");
-        k_weights<<<dim3((maxn + 255) / 256, N), 256, 0, c->stream>>>(N, c->d_cl, c->d_arena, c->d_status, c->d_eps,
-                                                                   c->d_q);
+        k_weights<<<dim3((maxn + 255) / 256, N), 256, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status,
+                                                                   c->d_eps, c->d_q);
     }
     DCLNO_LAUNCHED(c);
     if (c->deferred) return launch_status_or(c);
-    std::vector<int> st(N);
-    DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream));
+    const int nid = b.id_hi - b.id_lo;
+    std::vector<int> st(nid);
+    DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status + b.id_lo, sizeof(int) * nid, cudaMemcpyDeviceToHost,
+                                  c->stream));
     DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < N; ++i) {
-        if (st[i] == ST_NOT_SPD)
+    for (int k = 0; k < nid; ++k) {
+        const int i = b.id_lo + k;
+        if (st[k] == ST_NOT_SPD)
             return set_err(c, DCLNO_ERR_NOT_SPD, "overlap of cluster " + std::to_string(i) + " is not positive definite");
-        if (st[i] == ST_NOT_CONVERGED)
+        if (st[k] == ST_NOT_CONVERGED)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL did not converge for cluster " + std::to_string(i));
-        if (st[i] == ST_LOG_FULL)
+        if (st[k] == ST_LOG_FULL)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL rotation log full for cluster " + std::to_string(i));
-        if (st[i] != ST_OK) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "solver failed for cluster " + std::to_string(i));
+        if (st[k] != ST_OK) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "solver failed for cluster " + std::to_string(i));
     }
     return DCLNO_OK;
 }
 
-dclno_status launch_solve_fp64(dclno_ctx* c) { return launch_solve<false>(c); }
-dclno_status launch_solve_mixed(dclno_ctx* c) { return launch_solve<true>(c); }
+dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b) { return launch_solve<false>(c, b); }
+dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b) { return launch_solve<true>(c, b); }
