@@ -329,8 +329,10 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
             auto it = std::lower_bound(keys.begin(), keys.end(), std::make_pair(key[b], -1));
             if (it != keys.end() && it->first == key[b]) rowblk_member[b] = it->second;
         }
-        d.rot_cap = (int)std::min<long long>(3 * (long long)d.n * d.n / 2 + 64LL * d.n + 64, 2000000000LL);
-        d.it_cap = 8 * d.n + 64;
+        d.split = d.n >= DCLNO_TEAR_MIN ? d.n / 2 : 0;
+        const long long sm = d.split ? std::max(d.split, d.n - d.split) : d.n;  // longest segment
+        d.rot_cap = (int)std::min<long long>(3 * sm * sm / 2 + 64 * sm + 64, 2000000000LL);
+        d.it_cap = (int)(24 * sm + 64);
         d.eig_off = eig;
         eig += d.n;
         d.pair_off = pairs;
@@ -354,12 +356,15 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     std::vector<int> brow32(brow.begin(), brow.end());
 
     // ---- memory admission: per-cluster workspace (doubles): A, L (n x ld each), d/e/tau (ld each),
-    // W (32 ld), P ([n][2 mc]), rotation log (2 rot_cap), 256-byte aligned; sweep headers 3 it_cap ints
-    auto ws_doubles = [](const ClusterDesc& d) {
-        const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap;
+    // W (32 ld), P ([n][2 mc]), rotation logs (2 rot_cap per segment), for a torn problem the merge
+    // matrix and its transpose (n x ld each); 256-byte aligned.  Sweep headers: it_cap ints per segment.
+    auto nseg = [](const ClusterDesc& d) { return d.split ? 2LL : 1LL; };
+    auto ws_doubles = [&](const ClusterDesc& d) {
+        const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap * nseg(d) +
+                            (d.split ? 2LL * d.n * d.ld : 0LL);
         return (m + 31) & ~31LL;
     };
-    auto ws_bytes = [&](const ClusterDesc& d) { return 8 * ws_doubles(d) + 12LL * d.it_cap; };
+    auto ws_bytes = [&](const ClusterDesc& d) { return 8 * ws_doubles(d) + 4LL * d.it_cap * nseg(d); };
     size_t free_b = 0, tot_b = 0;
     DCLNO_CUDA(c, cudaMemGetInfo(&free_b, &tot_b));
     long long msum_all = 0;
@@ -420,9 +425,10 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
             d.aux_off = mat + 2LL * d.n * d.ld;  // d, e, tau, W: each sub-region starts on a multiple of 4 doubles
             d.cc_off = d.aux_off + 35LL * d.ld;
             d.rot_off = d.cc_off + 2LL * d.mc * d.ld;
+            d.m_off = d.rot_off + 2LL * d.rot_cap * nseg(d);
             mat += ws_doubles(d);
             d.it_off = its;
-            its += 3LL * d.it_cap;
+            its += (long long)d.it_cap * nseg(d);
             b.maxn = std::max(b.maxn, d.n);
             b.mcmax = std::max(b.mcmax, d.mc);
         }

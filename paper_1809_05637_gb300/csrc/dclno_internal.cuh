@@ -28,16 +28,24 @@ struct ClusterDesc {
     long long mbeg;     // first member in the member arrays
     long long mat_off;  // arena offset (doubles) of the H^(i)/A matrix; S^(i)/L follows at + n*ld
     long long eig_off;  // offset into eps/q (sum of earlier n)
-    long long cc_off;   // arena offset of the central rows C_c (M_i x n), then P2 (M_i x n)
-    long long rot_off;  // arena offset of the QL rotation log (2 doubles per rotation)
-    long long it_off;   // offset (ints) of the QL sweep headers (3 ints per sweep)
+    long long cc_off;   // arena offset of the central strips P ([n][2 M_i])
+    long long rot_off;  // arena offset of the QL rotation logs (2 doubles per rotation, rot_cap per segment)
+    long long it_off;   // offset (ints) of the QL sweep headers (it_cap ints per segment)
     long long aux_off;  // arena offset of per-cluster vectors d, e, tau (ld each) and W (32 ld)
-    int rot_cap;        // capacity of the rotation log
-    int it_cap;         // capacity of the sweep headers
+    int rot_cap;        // capacity of one segment's rotation log
+    int it_cap;         // ints of one segment's sweep headers
     int mc;             // M of the central atom
-    int pad;
+    int split;          // tear point k of the tridiagonal matrix (segments [0,k), [k,n)); 0 = no tear
     long long pair_off; // offset of the cluster's member-pair block table (nmem x nmem ints)
+    long long m_off;    // arena offset of the merge matrix M (n x ld) and its transpose (n x ld); split only
 };
+
+// segment s (0, 1) of a cluster's tridiagonal problem: first index and length
+__host__ __device__ inline int seg_start(const ClusterDesc& d, int s) { return s ? d.split : 0; }
+__host__ __device__ inline int seg_len(const ClusterDesc& d, int s) {
+    return d.split ? (s ? d.n - d.split : d.split) : (s ? 0 : d.n);
+}
+#define DCLNO_TEAR_MIN 64  // tear tridiagonal matrices of at least this dimension
 
 struct MemberDesc {
     int atom;   // j
@@ -219,6 +227,10 @@ dclno_status launch_assemble(dclno_ctx* c, const Batch& b);
 dclno_status launch_pair_index(dclno_ctx* c);
 dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b);
 dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b);
+dclno_status launch_merge(dclno_ctx* c, const Batch& b);
+// Y <- X Y for the torn clusters of a batch: dir 0 = central strips P <- M^T P (after the
+// forward replay), dir 1 = density columns G <- M G (before the reverse replay)
+dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
 dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out,
                             double* e_out = nullptr);

@@ -1,0 +1,394 @@
+// Merge of a torn tridiagonal eigenproblem (Cuppen's divide and conquer, one level).
+//
+// k_tridiag tears T at k = n/2: T = diag(T1, T2) + rho v v^T, rho = |beta|,
+// v = e_{k-1} + sign(beta) e_k (beta = T[k][k-1]).  k_ql solves T1 = Z1 D1 Z1^T and
+// T2 = Z2 D2 Z2^T as two segments.  With z = diag(Z1, Z2)^T v,
+//     T = diag(Z1, Z2) (D + rho z z^T) diag(Z1, Z2)^T,
+// and the rank-one problem D + rho z z^T = U Lambda U^T is solved here:
+//   * deflation (Bunch, Nielsen and Sorensen 1978; Dongarra and Sorensen 1987):
+//     a component with rho |z_i| below the tolerance leaves d_i and e_i unchanged;
+//     two nearly equal d's are combined by a plane rotation that zeroes one z;
+//   * the K remaining roots of the secular equation 1 + rho sum_i z_i^2/(d_i - lam) = 0,
+//     one in each (d_j, d_{j+1}) and one above d_K, by a safeguarded iteration on a
+//     model with the two nearest poles, with lam stored as pole + offset so that every
+//     difference d_i - lam is formed without cancellation;
+//   * z recomputed from the computed roots (Gu and Eisenstat 1995),
+//     z_i^2 = prod_j (lam_j - d_i) / (rho prod_{j != i} (d_j - d_i)), which makes the
+//     eigenvectors u_j = (z_i / (d_i - lam_j))_i / norm numerically orthogonal.
+// The eigenvectors of T are diag(Z1, Z2) U: U (the merge matrix M, n x n, and its
+// transpose) is stored for the back-transforms (k_mgemm); the eigenvalues replace d.
+#include "dclno_internal.cuh"
+
+#define MG_THREADS 256
+
+// z = v diag(Z1, Z2): each segment's rotation log replayed on one row vector
+// (one lane per (cluster, segment)); z is written to W[0, n).
+__global__ void k_replay_z(int nitems, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                           double* __restrict__ arena, const int* __restrict__ iters,
+                           const int* __restrict__ status) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= nitems) return;
+    const int ci = order[item >> 1];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!d.split) return;
+    const int sg = item & 1, s0 = seg_start(d, sg), ns = seg_len(d, sg);
+    double* W = arena + d.aux_off + 3 * d.ld;
+    const double beta = W[d.n];
+    double* x = W + s0;
+    for (int t = 0; t < ns; ++t) x[t] = 0.0;
+    if (sg == 0) x[ns - 1] = 1.0;
+    else x[0] = (beta < 0.0) ? -1.0 : 1.0;
+    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off) + (size_t)sg * d.rot_cap;
+    const int* hdr = iters + d.it_off + (size_t)sg * d.it_cap;
+    const int nsw = hdr[0];
+    for (int k = 0; k < nsw; ++k) {
+        const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
+        if (cnt == 0) continue;
+        double xi1 = x[i0 + 1], xi = x[i0];
+        double2 cs = rot[start];
+        for (int u = 0; u < cnt; ++u) {
+            const int i = i0 - u;
+            double xn = 0.0;
+            double2 csn = cs;
+            if (u + 1 < cnt) {
+                xn = x[i - 1];
+                csn = rot[start + u + 1];
+            }
+            x[i + 1] = fma(cs.y, xi, cs.x * xi1);
+            xi1 = fma(cs.x, xi, -cs.y * xi1);
+            xi = xn;
+            cs = csn;
+        }
+        x[i0 + 1 - cnt] = xi1;
+    }
+}
+
+// psi = sum_{i<=j} w_i/(d_i - lam), phi = sum_{i>j} w_i/(d_i - lam), their derivatives
+// in lam and sum |terms|, at lam = d_o + tau (differences d_i - d_o formed first)
+struct SecVal {
+    double psi, dpsi, phi, dphi, abs;
+};
+
+__device__ static SecVal sec_eval(int K, const double* dk, const double* w, int o, double tau, int j) {
+    SecVal v = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const double dorg = dk[o];
+    for (int i = 0; i <= j; ++i) {
+        const double del = (dk[i] - dorg) - tau;
+        const double t = w[i] / del;
+        v.psi += t;
+        v.dpsi = fma(t, 1.0 / del, v.dpsi);
+        v.abs += fabs(t);
+    }
+    for (int i = j + 1; i < K; ++i) {
+        const double del = (dk[i] - dorg) - tau;
+        const double t = w[i] / del;
+        v.phi += t;
+        v.dphi = fma(t, 1.0 / del, v.dphi);
+        v.abs += fabs(t);
+    }
+    return v;
+}
+
+// root h of A h^2 - B h + C = 0 inside (lo, hi); NaN if none (the caller bisects)
+__device__ static double quad_root_in(double A, double B, double C, double lo, double hi) {
+    if (A == 0.0) return (B != 0.0) ? C / B : nan("");
+    const double disc = fma(B, B, -4.0 * A * C);
+    if (!(disc >= 0.0)) return nan("");
+    const double sq = sqrt(disc);
+    double h1, h2;
+    if (B >= 0.0) {
+        h1 = (B + sq) / (2.0 * A);
+        h2 = (B + sq != 0.0) ? 2.0 * C / (B + sq) : nan("");
+    } else {
+        h1 = 2.0 * C / (B - sq);
+        h2 = (B - sq) / (2.0 * A);
+    }
+    if (h2 > lo && h2 < hi) return h2;
+    if (h1 > lo && h1 < hi) return h1;
+    return nan("");
+}
+
+// Root j of 1 + sum_i w_i/(d_i - lam) = 0 (d ascending, w > 0, wsum = sum w):
+// lam = d_o + tau.  Returns the number of iterations (> 100: not converged).
+__device__ static int sec_root(int K, const double* dk, const double* w, double wsum, int j, double& tau_out,
+                               int& org_out) {
+    const double u = 1.1102230246251565e-16;  // 2^-53
+    int o;
+    double lo, hi, tau;
+    SecVal v;
+    if (j < K - 1) {
+        const double gap = dk[j + 1] - dk[j];
+        const double mid = 0.5 * gap;
+        v = sec_eval(K, dk, w, j, mid, j);
+        if (1.0 + v.psi + v.phi >= 0.0) {  // root in (d_j, mid]: origin d_j
+            o = j;
+            lo = 0.0;
+            hi = mid;
+            tau = mid;
+        } else {                            // root in (mid, d_{j+1}): origin d_{j+1}
+            o = j + 1;
+            lo = mid - gap;
+            hi = 0.0;
+            tau = mid - gap;
+        }
+    } else {
+        o = j;
+        lo = 0.0;
+        hi = wsum;  // f(d_K + sum w) >= 0
+        tau = 0.5 * wsum;
+        v = sec_eval(K, dk, w, o, tau, j);
+    }
+    int it = 0;
+    for (; it < 100; ++it) {
+        const double f = 1.0 + v.psi + v.phi;
+        if (f < 0.0) lo = tau;
+        else hi = tau;
+        if (fabs(f) <= 8.0 * u * (1.0 + v.abs) || hi - lo <= 4.0 * u * fmax(fabs(lo), fabs(hi))) break;
+        // model: psi ~ a1 + b1/(p - x), phi ~ a2 + b2/(q - x), values and slopes matched at tau
+        const double dp = (dk[j] - dk[o]) - tau;
+        const double b1 = v.dpsi * dp * dp, a1 = v.psi - b1 / dp;
+        double h;
+        if (j < K - 1) {
+            const double dq = (dk[j + 1] - dk[o]) - tau;
+            const double b2 = v.dphi * dq * dq, a2 = v.phi - b2 / dq;
+            const double A = 1.0 + a1 + a2;
+            h = quad_root_in(A, A * (dp + dq) + b1 + b2, dp * dq * f, dp, dq);
+        } else {
+            h = (1.0 + a1 > 0.0) ? dp + b1 / (1.0 + a1) : nan("");
+        }
+        double tn = tau + h;
+        // inside the bracket; the last root may sit on its upper end (K = 1: lam = d + w exactly)
+        if (!(tn > lo && (tn < hi || (j == K - 1 && tn == hi)))) tn = 0.5 * (lo + hi);
+        if (tn == tau) break;
+        tau = tn;
+        v = sec_eval(K, dk, w, o, tau, j);
+    }
+    tau_out = tau;
+    org_out = o;
+    return it + 1;
+}
+
+__global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restrict__ cls,
+                                                      const int* __restrict__ order, double* __restrict__ arena,
+                                                      int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc dc = cls[ci];
+    if (!dc.split) return;
+    const int n = dc.n, ld = dc.ld, tid = threadIdx.x;
+    double* dv = arena + dc.aux_off;
+    const double* zin = dv + 3 * ld;  // W[0, n)
+    const double beta = zin[n];
+    double* M = arena + dc.m_off;       // row = coordinate, column = eigenpair
+    double* MT = M + (size_t)n * ld;    // row = eigenpair
+    double* dk = sm;          // sorted d; after deflation: the K non-deflated d
+    double* zk = dk + n;      // sorted normalised z; after deflation: the K non-deflated z
+    double* w = zk + n;       // rho' z_k^2
+    double* tau = w + n;      // root offsets
+    double* zh = tau + n;     // recomputed z
+    double* dev = zh + n;     // deflated eigenvalues
+    double* gcs = dev + n;    // rotation c, s pairs (2 n)
+    double* nrm = gcs + 2 * n;  // column norms
+    int* perm = reinterpret_cast<int*>(nrm + n);  // sorted position -> coordinate
+    int* kidx = perm + n;     // non-deflated entry -> coordinate
+    int* org = kidx + n;      // origin pole of root j
+    int* colc = org + n;      // deflated column -> coordinate
+    int* gpq = colc + n;      // rotation coordinate pairs (2 n)
+    __shared__ double red[MG_THREADS / 32][2];
+    __shared__ int sK, sND, sNG, sFail;
+    __shared__ double sRho, sWsum;
+
+    // norm of z and the largest |d|
+    double zz = 0.0, dmax = 0.0;
+    for (int t = tid; t < n; t += MG_THREADS) {
+        zz = fma(zin[t], zin[t], zz);
+        dmax = fmax(dmax, fabs(dv[t]));
+    }
+    zz = warp_sum(zz);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((tid & 31) == 0) {
+        red[tid >> 5][0] = zz;
+        red[tid >> 5][1] = dmax;
+    }
+    __syncthreads();
+    zz = 0.0;
+    dmax = 0.0;
+    for (int k = 0; k < MG_THREADS / 32; ++k) {
+        zz += red[k][0];
+        dmax = fmax(dmax, red[k][1]);
+    }
+    const double zscale = zz > 0.0 ? 1.0 / sqrt(zz) : 0.0;
+    // sort (d, coordinate) ascending by rank counting; ties by coordinate
+    for (int t = tid; t < n; t += MG_THREADS) {
+        const double dt = dv[t];
+        int r = 0;
+        for (int s = 0; s < n; ++s) {
+            const double ds = dv[s];
+            r += (ds < dt || (ds == dt && s < t)) ? 1 : 0;
+        }
+        perm[r] = t;
+        dk[r] = dt;
+        zk[r] = zin[t] * zscale;
+    }
+    __syncthreads();
+    // deflation (one thread, in sorted order)
+    if (tid == 0) {
+        const double rho = fabs(beta) * zz;
+        const double tol = 8.0 * 1.1102230246251565e-16 * fmax(dmax, rho);
+        int K = 0, nd = 0, ng = 0;
+        bool have = false;
+        double pd = 0.0, pz = 0.0;
+        int pc = -1;
+        for (int j = 0; j < n; ++j) {
+            const double dj = dk[j], zj = zk[j];
+            const int cj = perm[j];
+            if (rho * fabs(zj) <= tol) {  // z_j negligible: (d_j, e_j) is an eigenpair
+                dev[nd] = dj;
+                colc[nd] = cj;
+                ++nd;
+                continue;
+            }
+            if (!have) {
+                have = true;
+                pd = dj;
+                pz = zj;
+                pc = cj;
+                continue;
+            }
+            const double t = hypot(pz, zj);
+            const double c = zj / t, s = -pz / t;
+            if (fabs(c * s * (dj - pd)) <= tol) {
+                // rotate (pc, cj) so that the z of pc vanishes; pc deflates
+                gpq[2 * ng] = pc;
+                gpq[2 * ng + 1] = cj;
+                gcs[2 * ng] = c;
+                gcs[2 * ng + 1] = s;
+                ++ng;
+                dev[nd] = fma(c * c, pd, s * s * dj);
+                colc[nd] = pc;
+                ++nd;
+                pd = fma(s * s, pd, c * c * dj);
+                pz = t;
+                pc = cj;
+            } else {
+                dk[K] = pd;  // K <= j - 1: entries not yet read are not overwritten
+                zk[K] = pz;
+                kidx[K] = pc;
+                ++K;
+                pd = dj;
+                pz = zj;
+                pc = cj;
+            }
+        }
+        if (have) {
+            dk[K] = pd;
+            zk[K] = pz;
+            kidx[K] = pc;
+            ++K;
+        }
+        sK = K;
+        sND = nd;
+        sNG = ng;
+        sRho = rho;
+        sFail = 0;
+    }
+    __syncthreads();
+    const int K = sK, nd = sND, ng = sNG;
+    const double rho = sRho;
+    for (int i = tid; i < K; i += MG_THREADS) w[i] = rho * zk[i] * zk[i];
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < K; ++i) s += w[i];
+        sWsum = s;
+    }
+    __syncthreads();
+    // secular roots
+    for (int j = tid; j < K; j += MG_THREADS) {
+        double t;
+        int o;
+        if (sec_root(K, dk, w, sWsum, j, t, o) > 100) sFail = 1;
+        tau[j] = t;
+        org[j] = o;
+    }
+    __syncthreads();
+    // z from the computed roots (Gu-Eisenstat), ratios paired to stay near 1
+    for (int i = tid; i < K; i += MG_THREADS) {
+        const double di = dk[i];
+        double prod = ((dk[org[K - 1]] - di) + tau[K - 1]) / rho;
+        for (int j = 0; j < K - 1; ++j) {
+            const double num = (dk[org[j]] - di) + tau[j];
+            const double den = (j < i) ? (dk[j] - di) : (dk[j + 1] - di);
+            prod *= num / den;
+        }
+        zh[i] = copysign(sqrt(fmax(prod, 0.0)), zk[i]);
+    }
+    // M = 0
+    for (size_t e = tid; e < (size_t)n * ld; e += MG_THREADS) M[e] = 0.0;
+    __syncthreads();
+    // root columns: u_j = (z_i / (d_i - lam_j))_i at the non-deflated coordinates
+    for (int j = tid; j < K; j += MG_THREADS) {
+        const double dj = dk[org[j]], tj = tau[j];
+        double s = 0.0;
+        for (int i = 0; i < K; ++i) {
+            const double uij = zh[i] / ((dk[i] - dj) - tj);
+            M[(size_t)kidx[i] * ld + j] = uij;
+            s = fma(uij, uij, s);
+        }
+        nrm[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        dv[j] = dj + tj;
+    }
+    for (int r = tid; r < nd; r += MG_THREADS) {
+        M[(size_t)colc[r] * ld + K + r] = 1.0;
+        dv[K + r] = dev[r];
+    }
+    __syncthreads();
+    for (size_t e = tid; e < (size_t)K * n; e += MG_THREADS) {
+        const int i = (int)(e / K), j = (int)(e % K);
+        M[(size_t)i * ld + j] *= nrm[j];
+    }
+    __syncthreads();
+    // undo the deflation rotations (last first): rows (p, q) <- R^T rows (p, q)
+    for (int g = ng - 1; g >= 0; --g) {
+        const int p = gpq[2 * g], q = gpq[2 * g + 1];
+        const double c = gcs[2 * g], s = gcs[2 * g + 1];
+        for (int col = tid; col < n; col += MG_THREADS) {
+            const double a = M[(size_t)p * ld + col], b = M[(size_t)q * ld + col];
+            M[(size_t)p * ld + col] = fma(c, a, -s * b);
+            M[(size_t)q * ld + col] = fma(s, a, c * b);
+        }
+        __syncthreads();
+    }
+    for (size_t e = tid; e < (size_t)n * n; e += MG_THREADS) {
+        const int col = (int)(e / n), r = (int)(e % n);
+        MT[(size_t)col * ld + r] = M[(size_t)r * ld + col];
+    }
+    if (tid == 0 && sFail) status[ci] = ST_NOT_CONVERGED;
+}
+
+dclno_status launch_merge(dclno_ctx* c, const Batch& b) {
+    const int N = b.oend - b.obeg;
+    if (N == 0) return DCLNO_OK;
+    const int* order = c->d_order + b.obeg;
+    bool any = false;
+    for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
+    if (!any) return DCLNO_OK;
+    {
+        ProfScope ps__(c, "k_replay_z");
+        k_replay_z<<<(2 * N + 127) / 128, 128, 0, c->stream>>>(2 * N, c->d_cl, order, c->d_arena, c->d_iters,
+                                                              c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    const size_t sm = (size_t)b.maxn * (10 * sizeof(double) + 6 * sizeof(int));
+    if (sm > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the merge step");
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+        ProfScope ps__(c, "k_merge");
+        k_merge<<<N, MG_THREADS, sm, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}

@@ -255,22 +255,24 @@ __global__ void k_rho_prep(int id_lo, const ClusterDesc* __restrict__ cls, doubl
     }
 }
 
-// G <- Z G: the logged rotations in reverse order acting on rows (i, i+1).
-// A warp packs floor(32 / mc) clusters, one lane per column of G.
-__global__ void k_replay_rev(int ncl, int per_warp, int w_max, int with_e, const ClusterDesc* __restrict__ cls,
+// G <- diag(Z1, Z2) G: each segment's logged rotations in reverse order acting on rows
+// (i, i+1).  Work items are (cluster, segment); a warp packs floor(32 / w) items, one
+// lane per column of G.
+__global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, const ClusterDesc* __restrict__ cls,
                              const int* __restrict__ order, double* __restrict__ arena, const int* __restrict__ iters) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int grp = lane / w_max, col = lane % w_max;
     if (grp >= per_warp) return;
     const int item = wid * per_warp + grp;
-    if (item >= ncl) return;
-    const ClusterDesc d = cls[order[item]];
+    if (item >= nitems) return;
+    const ClusterDesc d = cls[order[item >> 1]];
+    const int sg = item & 1;
     const int mc = with_e ? 2 * d.mc : d.mc;  // columns of G
-    if (col >= mc) return;
-    double* G = arena + d.aux_off + 3 * d.ld;
-    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
-    const int* hdr = iters + d.it_off;
+    if (col >= mc || seg_len(d, sg) == 0) return;
+    double* G = arena + d.aux_off + 3 * d.ld + (size_t)seg_start(d, sg) * mc;
+    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off) + (size_t)sg * d.rot_cap;
+    const int* hdr = iters + d.it_off + (size_t)sg * d.it_cap;
     const int nsw = hdr[0];
     for (int k = nsw - 1; k >= 0; --k) {
         const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
@@ -405,11 +407,15 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
     }
     DCLNO_LAUNCHED(c);
     {
+        const dclno_status st = launch_mgemm(c, b, 1, with_e, c->solved_prec == DCLNO_MIXED);
+        if (st != DCLNO_OK) return st;
+    }
+    {
         ProfScope ps__(c, "k_replay_rev");
         const int wmax = with_e ? 2 * b.mcmax : b.mcmax;
         const int per_warp = std::max(1, 32 / wmax);
-        const int warps = (N + per_warp - 1) / per_warp;
-        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(N, per_warp, wmax, with_e, c->d_cl,
+        const int warps = (2 * N + per_warp - 1) / per_warp;
+        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(2 * N, per_warp, wmax, with_e, c->d_cl,
                                                                       c->d_order + b.obeg, c->d_arena, c->d_iters);
     }
     DCLNO_LAUNCHED(c);

@@ -355,6 +355,18 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_tridiag(const Cluste
             tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G);
         }
     }
+    // Cuppen's tear: T = diag(T1, T2) + |beta| v v^T with beta = e[k-1], v = e_{k-1} + sign(beta) e_k;
+    // T1 and T2 (d[k-1], d[k] lowered by |beta|) are solved as separate QL segments and merged
+    // afterwards (k_merge).  beta is kept in W[n].
+    __syncthreads();
+    if (d.split && threadIdx.x == 0) {
+        const int k = d.split;
+        const double beta = ev[k - 1];
+        W[n] = beta;
+        ev[k - 1] = 0.0;
+        dv[k - 1] -= fabs(beta);
+        dv[k] -= fabs(beta);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -386,27 +398,30 @@ __device__ __forceinline__ bool negligible(double e, double d0, double d1) {
 __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restrict__ cls,
                                            const int* __restrict__ order, double* __restrict__ arena,
                                            int* __restrict__ iters, int* __restrict__ status) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // lane = (cluster, segment)
     int phase = QL_DONE, n = 0, ci = -1;
     double* d = nullptr;
     double* e = nullptr;
     double2* rot = nullptr;
     int* hdr = nullptr;
     int rot_cap = 0, sw_cap = 0;
-    if (t < ncl) {
-        ci = order[t];
+    if (t < 2 * ncl) {
+        ci = order[t >> 1];
+        const int sg = t & 1;
         if (status[ci] == ST_OK) {
             const ClusterDesc dsc = cls[ci];
-            n = dsc.n;
-            d = arena + dsc.aux_off;
-            e = d + dsc.ld;
-            rot = reinterpret_cast<double2*>(arena + dsc.rot_off);
-            hdr = iters + dsc.it_off;
-            rot_cap = dsc.rot_cap;
-            sw_cap = (dsc.it_cap - 1) / 3;
-            e[n - 1] = 0.0;
-            phase = (n > 1) ? QL_SEEK : QL_DONE;
-            if (n <= 1) hdr[0] = 0;
+            n = seg_len(dsc, sg);
+            if (n > 0) {
+                d = arena + dsc.aux_off + seg_start(dsc, sg);
+                e = d + dsc.ld;
+                rot = reinterpret_cast<double2*>(arena + dsc.rot_off) + (size_t)sg * dsc.rot_cap;
+                hdr = iters + dsc.it_off + (size_t)sg * dsc.it_cap;
+                rot_cap = dsc.rot_cap;
+                sw_cap = (dsc.it_cap - 1) / 3;
+                e[n - 1] = 0.0;
+                phase = (n > 1) ? QL_SEEK : QL_DONE;
+                if (n <= 1) hdr[0] = 0;
+            }
         }
     }
     int l = 0, m = 0, mm = 0, i = 0, it = 0, nrot = 0, nsw = 0, start = 0;
@@ -626,10 +641,10 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const Clus
     }
 }
 
-// P <- P Z by the logged rotations.  Work items are (cluster, strip) pairs with
-// strip 0 = the mc rows of R1 and strip 1 = the mc rows of R2; a warp packs
-// floor(32 / mc) items, one lane per row, so one FP64 instruction updates the rows
-// of several clusters.
+// P <- P diag(Z1, Z2) by the logged rotations of each segment.  Work items are
+// (cluster, segment, strip) with strip 0 = the mc rows of R1 and strip 1 = the mc
+// rows of R2; a warp packs floor(32 / mc) items, one lane per row, so one FP64
+// instruction updates the rows of several clusters.
 __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const ClusterDesc* __restrict__ cls,
                              const int* __restrict__ order, double* __restrict__ arena,
                              const int* __restrict__ iters, const int* __restrict__ status) {
@@ -639,15 +654,16 @@ __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const Cluster
     if (grp >= per_warp) return;
     const int item = wid * per_warp + grp;
     if (item >= nitems) return;
-    const int ci = order[item >> 1];
+    const int ci = order[item >> 2];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
-    if (row >= d.mc) return;
+    const int sg = (item >> 1) & 1;
+    if (row >= d.mc || seg_len(d, sg) == 0) return;
     const int w2 = 2 * d.mc;
     const int r = (item & 1) * d.mc + row;
-    double* P = arena + d.cc_off;
-    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off);
-    const int* hdr = iters + d.it_off;
+    double* P = arena + d.cc_off + (size_t)seg_start(d, sg) * w2;
+    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off) + (size_t)sg * d.rot_cap;
+    const int* hdr = iters + d.it_off + (size_t)sg * d.it_cap;
     const int nsw = hdr[0];
     for (int k = 0; k < nsw; ++k) {
         const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
@@ -672,6 +688,64 @@ __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const Cluster
         }
         P[(size_t)(i0 + 1 - cnt) * w2 + r] = xi1;
     }
+}
+
+// Merge-matrix products of a torn cluster (one CTA per cluster):
+//   dir 0: P <- M^T P   (P = [n][2 mc] central strips; X = M^T stored row-major)
+//   dir 1: G <- M G     (G = [n][w] density columns in W; X = M)
+// as C -= X B^T with B = -Y^T staged in scratch (W for dir 0, the M^T area for dir 1)
+// and C = Y cleared.
+template <bool EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterDesc* __restrict__ cls,
+                                                               const int* __restrict__ order,
+                                                               double* __restrict__ arena,
+                                                               const int* __restrict__ status, int dir, int with_e) {
+    extern __shared__ double sm[];
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!d.split) return;
+    const int n = d.n, ld = d.ld;
+    const int w = (dir == 0 || with_e) ? 2 * d.mc : d.mc;
+    double* M = arena + d.m_off;
+    double* MT = M + (size_t)n * ld;
+    double* Y = (dir == 0) ? arena + d.cc_off : arena + d.aux_off + 3 * ld;
+    double* Bt = (dir == 0) ? arena + d.aux_off + 3 * ld : MT;
+    const double* X = (dir == 0) ? MT : M;
+    for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) {
+        const int t = (int)(e / w), a = (int)(e % w);
+        Bt[(size_t)a * ld + t] = -Y[e];
+    }
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Y[e] = 0.0;
+    __syncthreads();
+    if (EMU) {
+        for (int k0 = 0; k0 < n; k0 += EG_K)
+            tile_update<false, true>(Y, w, X + k0, ld, Bt + k0, ld, n, w, min(EG_K, n - k0), 0, sm);
+    } else {
+        tile_update<false, false>(Y, w, X, ld, Bt, ld, n, w, n, 0, sm);
+    }
+}
+
+dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu) {
+    const int N = b.oend - b.obeg;
+    if (N == 0) return DCLNO_OK;
+    bool any = false;
+    for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
+    if (!any) return DCLNO_OK;
+    const size_t smb = emu ? (size_t)EG_SMEM_BYTES : (size_t)GT_SMEM_DOUBLES * sizeof(double);
+    ProfScope ps__(c, dir == 0 ? "k_mgemm_fwd" : "k_mgemm_rev");
+    if (emu) {
+        DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        k_mgemm<true><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena,
+                                                                  c->d_status, dir, with_e);
+    } else {
+        DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+        k_mgemm<false><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena,
+                                                                   c->d_status, dir, with_e);
+    }
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
 }
 
 // eigenvalues and weights: eps_mu = d_mu, q_mu = sum_a P[mu][a] P[mu][mc + a]
@@ -728,9 +802,13 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_ql");
-        k_ql<<<(N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, order, c->d_arena, c->d_iters, c->d_status);
+        k_ql<<<(2 * N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, order, c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
+    {
+        const dclno_status st = launch_merge(c, b);
+        if (st != DCLNO_OK) return st;
+    }
     {
         ProfScope ps__(c, "k_apply_q_rows");
         k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
@@ -740,12 +818,16 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
         ProfScope ps__(c, "k_replay_fwd");
         const int mcmax = b.mcmax;
         const int per_warp = std::max(1, 32 / mcmax);
-        const int items = 2 * N;
+        const int items = 4 * N;
         const int warps = (items + per_warp - 1) / per_warp;
         k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, order,
                                                                       c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
+    {
+        const dclno_status st = launch_mgemm(c, b, 0, 0, EMU);
+        if (st != DCLNO_OK) return st;
+    }
     {
         ProfScope ps__(c, "k_weights");
         k_weights<<<dim3((maxn + 255) / 256, N), 256, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status,
