@@ -248,6 +248,85 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// One logged QL sweep applied to a strided vector x_t = X[t * stride]:
+// rotations u = 0 .. cnt-1 act on (i, i+1) with i = i0 - u, as column updates
+//   x_{i+1} <- s x_i + c x_{i+1},  x_i <- c x_i - s x_{i+1}
+// (sweep_fwd, the order they were generated: x <- x Z), or in reverse order with the
+// transposed rotations (sweep_rev: x <- Z x).  Operands are loaded D rotations
+// ahead: a replay is a serial chain per vector, so the load latency would
+// otherwise set the time per rotation.  rot points at the sweep's first rotation.
+template <int D>
+__host__ __device__ __forceinline__ void sweep_fwd(double* __restrict__ X, size_t stride, const double2* __restrict__ rot,
+                                          int i0, int cnt) {
+    double xb[D];
+    double2 cb[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        xb[q] = 0.0;
+        cb[q] = make_double2(1.0, 0.0);
+        if (q < cnt) {
+            xb[q] = X[(size_t)(i0 - q) * stride];
+            cb[q] = rot[q];
+        }
+    }
+    double xi1 = X[(size_t)(i0 + 1) * stride];
+    for (int u0 = 0; u0 < cnt; u0 += D) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const int u = u0 + q;
+            if (u < cnt) {
+                const int i = i0 - u;
+                const double xi = xb[q];
+                const double2 cs = cb[q];
+                if (u + D < cnt) {  // row i - D is written only after rotation u + D has read it
+                    xb[q] = X[(size_t)(i - D) * stride];
+                    cb[q] = rot[u + D];
+                }
+                X[(size_t)(i + 1) * stride] = fma(cs.y, xi, cs.x * xi1);
+                xi1 = fma(cs.x, xi, -cs.y * xi1);
+            }
+        }
+    }
+    X[(size_t)(i0 + 1 - cnt) * stride] = xi1;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void sweep_rev(double* __restrict__ X, size_t stride, const double2* __restrict__ rot,
+                                          int i0, int cnt) {
+    const int ib = i0 - (cnt - 1);  // rows (ib + m, ib + m + 1) at step m = 0 .. cnt-1 (rotation cnt-1-m)
+    double xb[D];
+    double2 cb[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        xb[q] = 0.0;
+        cb[q] = make_double2(1.0, 0.0);
+        if (q < cnt) {
+            xb[q] = X[(size_t)(ib + q + 1) * stride];
+            cb[q] = rot[cnt - 1 - q];
+        }
+    }
+    double wi = X[(size_t)ib * stride];
+    for (int m0 = 0; m0 < cnt; m0 += D) {
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const int m = m0 + q;
+            if (m < cnt) {
+                const int i = ib + m;
+                const double wi1 = xb[q];
+                const double2 cs = cb[q];
+                if (m + D < cnt) {  // row i + 1 + D is written at step m + D + 1
+                    xb[q] = X[(size_t)(i + 1 + D) * stride];
+                    cb[q] = rot[cnt - 1 - m - D];
+                }
+                X[(size_t)i * stride] = fma(cs.x, wi, cs.y * wi1);
+                wi = fma(-cs.y, wi, cs.x * wi1);
+            }
+        }
+    }
+    X[(size_t)(ib + cnt) * stride] = wi;
+}
+#define DCLNO_REPLAY_DEPTH 1  // the replays run many warps per SM and are bound by the FP64 pipe
+
 // One FP64 tensor-core MMA: D(8x8) += A(8x4, row) * B(4x8, col).
 // Fragments (per lane l): a = A[l/4][l%4], b = B[l%4][l/4],
 // c = {C[l/4][2(l%4)], C[l/4][2(l%4)+1]}.

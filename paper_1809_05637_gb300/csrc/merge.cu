@@ -2,7 +2,8 @@
 //
 // k_tridiag tears T at k = n/2: T = diag(T1, T2) + rho v v^T, rho = |beta|,
 // v = e_{k-1} + sign(beta) e_k (beta = T[k][k-1]).  k_ql solves T1 = Z1 D1 Z1^T and
-// T2 = Z2 D2 Z2^T as two segments.  With z = diag(Z1, Z2)^T v,
+// T2 = Z2 D2 Z2^T as two segments and applies each rotation also to the row v, so
+// that z = diag(Z1, Z2)^T v is ready in W[0, n) when it finishes.  With that z,
 //     T = diag(Z1, Z2) (D + rho z z^T) diag(Z1, Z2)^T,
 // and the rank-one problem D + rho z z^T = U Lambda U^T is solved here:
 //   * deflation (Bunch, Nielsen and Sorensen 1978; Dongarra and Sorensen 1987):
@@ -21,49 +22,6 @@
 
 #define MG_THREADS 256
 
-// z = v diag(Z1, Z2): each segment's rotation log replayed on one row vector
-// (one lane per (cluster, segment)); z is written to W[0, n).
-__global__ void k_replay_z(int nitems, const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
-                           double* __restrict__ arena, const int* __restrict__ iters,
-                           const int* __restrict__ status) {
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= nitems) return;
-    const int ci = order[item >> 1];
-    if (status[ci] != ST_OK) return;
-    const ClusterDesc d = cls[ci];
-    if (!d.split) return;
-    const int sg = item & 1, s0 = seg_start(d, sg), ns = seg_len(d, sg);
-    double* W = arena + d.aux_off + 3 * d.ld;
-    const double beta = W[d.n];
-    double* x = W + s0;
-    for (int t = 0; t < ns; ++t) x[t] = 0.0;
-    if (sg == 0) x[ns - 1] = 1.0;
-    else x[0] = (beta < 0.0) ? -1.0 : 1.0;
-    const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off) + (size_t)sg * d.rot_cap;
-    const int* hdr = iters + d.it_off + (size_t)sg * d.it_cap;
-    const int nsw = hdr[0];
-    for (int k = 0; k < nsw; ++k) {
-        const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
-        if (cnt == 0) continue;
-        double xi1 = x[i0 + 1], xi = x[i0];
-        double2 cs = rot[start];
-        for (int u = 0; u < cnt; ++u) {
-            const int i = i0 - u;
-            double xn = 0.0;
-            double2 csn = cs;
-            if (u + 1 < cnt) {
-                xn = x[i - 1];
-                csn = rot[start + u + 1];
-            }
-            x[i + 1] = fma(cs.y, xi, cs.x * xi1);
-            xi1 = fma(cs.x, xi, -cs.y * xi1);
-            xi = xn;
-            cs = csn;
-        }
-        x[i0 + 1 - cnt] = xi1;
-    }
-}
-
 // psi = sum_{i<=j} w_i/(d_i - lam), phi = sum_{i>j} w_i/(d_i - lam), their derivatives
 // in lam and sum |terms|, at lam = d_o + tau (differences d_i - d_o formed first)
 struct SecVal {
@@ -74,17 +32,17 @@ __device__ static SecVal sec_eval(int K, const double* dk, const double* w, int 
     SecVal v = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dorg = dk[o];
     for (int i = 0; i <= j; ++i) {
-        const double del = (dk[i] - dorg) - tau;
-        const double t = w[i] / del;
+        const double r = 1.0 / ((dk[i] - dorg) - tau);
+        const double t = w[i] * r;
         v.psi += t;
-        v.dpsi = fma(t, 1.0 / del, v.dpsi);
+        v.dpsi = fma(t, r, v.dpsi);
         v.abs += fabs(t);
     }
     for (int i = j + 1; i < K; ++i) {
-        const double del = (dk[i] - dorg) - tau;
-        const double t = w[i] / del;
+        const double r = 1.0 / ((dk[i] - dorg) - tau);
+        const double t = w[i] * r;
         v.phi += t;
-        v.dphi = fma(t, 1.0 / del, v.dphi);
+        v.dphi = fma(t, r, v.dphi);
         v.abs += fabs(t);
     }
     return v;
@@ -376,12 +334,6 @@ dclno_status launch_merge(dclno_ctx* c, const Batch& b) {
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
-    {
-        ProfScope ps__(c, "k_replay_z");
-        k_replay_z<<<(2 * N + 127) / 128, 128, 0, c->stream>>>(2 * N, c->d_cl, order, c->d_arena, c->d_iters,
-                                                              c->d_status);
-    }
-    DCLNO_LAUNCHED(c);
     const size_t sm = (size_t)b.maxn * (10 * sizeof(double) + 6 * sizeof(int));
     if (sm > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the merge step");
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

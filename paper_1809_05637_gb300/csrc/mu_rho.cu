@@ -276,25 +276,7 @@ __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, co
     const int nsw = hdr[0];
     for (int k = nsw - 1; k >= 0; --k) {
         const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
-        if (cnt == 0) continue;
-        // rotations u = cnt-1 .. 0 act on (i, i+1) with i = i0 - u, i increasing
-        int i = i0 - (cnt - 1);
-        double wi = G[(size_t)i * mc + col];
-        double wi1 = G[(size_t)(i + 1) * mc + col];
-        double2 cs = rot[start + cnt - 1];
-        for (int u = cnt - 1; u >= 0; --u, ++i) {
-            double wn = 0.0;
-            double2 csn = cs;
-            if (u > 0) {  // prefetch the next rotation's operands
-                wn = G[(size_t)(i + 2) * mc + col];
-                csn = rot[start + u - 1];
-            }
-            G[(size_t)i * mc + col] = fma(cs.x, wi, cs.y * wi1);
-            wi = fma(-cs.y, wi, cs.x * wi1);
-            wi1 = wn;
-            cs = csn;
-        }
-        G[(size_t)i * mc + col] = wi;
+        if (cnt > 0) sweep_rev<DCLNO_REPLAY_DEPTH>(G + col, mc, rot + start, i0, cnt);
     }
 }
 

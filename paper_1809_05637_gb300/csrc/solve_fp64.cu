@@ -378,7 +378,9 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_tridiag(const Cluste
 // same whatever its number of active lanes).  A sweep records the two smallest
 // negligible off-diagonals it leaves behind, so the next unreduced block is
 // known without a scan of e; SEEK runs only at the start and after a whole
-// block has converged.  Rotations are logged as (c, s) per sweep:
+// block has converged.  Lanes are (cluster, segment) pairs of a torn problem (or
+// the whole problem), with d, e and, for a torn problem, the row z = v Z of the merge
+// (k_merge) kept in shared memory.  Rotations are logged as (c, s) per sweep:
 // header block of a cluster = [nsweeps, (first rotation, first index i, count) x nsweeps],
 // i decreasing within a sweep.
 // ---------------------------------------------------------------------------
@@ -395,25 +397,41 @@ __device__ __forceinline__ bool negligible(double e, double d0, double d1) {
     return exp_bits(e) + 53 <= ed;
 }
 
-__global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restrict__ cls,
+__global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const ClusterDesc* __restrict__ cls,
                                            const int* __restrict__ order, double* __restrict__ arena,
                                            int* __restrict__ iters, int* __restrict__ status) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // lane = (cluster, segment)
+    extern __shared__ double sm[];
+    // lane = (cluster, segment); the lane's d, e and z row live in shared memory (segp each)
+    const int t = blockIdx.x * lanes + threadIdx.x;
     int phase = QL_DONE, n = 0, ci = -1;
-    double* d = nullptr;
-    double* e = nullptr;
+    double* d = sm + (size_t)threadIdx.x * 3 * segp;
+    double* e = d + segp;
+    double* x = e + segp;  // z row of a torn problem: v diag(Z1, Z2) restricted to this segment
+    double* dg = nullptr;  // the segment's d in global memory (eigenvalues out)
+    double* zg = nullptr;  // the segment's part of z in W (torn problems only)
     double2* rot = nullptr;
     int* hdr = nullptr;
     int rot_cap = 0, sw_cap = 0;
-    if (t < 2 * ncl) {
+    if (threadIdx.x < lanes && t < 2 * ncl) {
         ci = order[t >> 1];
         const int sg = t & 1;
         if (status[ci] == ST_OK) {
             const ClusterDesc dsc = cls[ci];
             n = seg_len(dsc, sg);
             if (n > 0) {
-                d = arena + dsc.aux_off + seg_start(dsc, sg);
-                e = d + dsc.ld;
+                dg = arena + dsc.aux_off + seg_start(dsc, sg);
+                for (int k = 0; k < n; ++k) {
+                    d[k] = dg[k];
+                    e[k] = dg[dsc.ld + k];
+                    x[k] = 0.0;
+                }
+                if (dsc.split) {
+                    // v = e_{k-1} + sign(beta) e_k, beta kept by k_tridiag in W[n]
+                    double* W = arena + dsc.aux_off + 3 * dsc.ld;
+                    zg = W + seg_start(dsc, sg);
+                    if (sg == 0) x[n - 1] = 1.0;
+                    else x[0] = (W[dsc.n] < 0.0) ? -1.0 : 1.0;
+                }
                 rot = reinterpret_cast<double2*>(arena + dsc.rot_off) + (size_t)sg * dsc.rot_cap;
                 hdr = iters + dsc.it_off + (size_t)sg * dsc.it_cap;
                 rot_cap = dsc.rot_cap;
@@ -425,6 +443,8 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
         }
     }
     int l = 0, m = 0, mm = 0, i = 0, it = 0, nrot = 0, nsw = 0, start = 0;
+    double zx1 = 0.0;  // z row: value of the row the sweep carries (crow), updated with each rotation
+    int crow = 0;
     // the two smallest indices in [l, m] whose e is negligible after this sweep (m counts
     // as negligible): the next unreduced block is known without scanning e again
     int lowneg = 0, low2 = 0;
@@ -469,6 +489,12 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
             d[i + 1] = dn;
             g = fma(c, rr, -b);
             rot[nrot++] = make_double2(c, s);
+            {  // the same rotation on the z row (off the recurrence's critical path)
+                const double xi = x[i];
+                x[i + 1] = fma(s, xi, c * zx1);
+                zx1 = fma(c, xi, -s * zx1);
+                crow = i;
+            }
             // deflation bookkeeping for the next sweep: e[i+1], d[i+1], d[i+2] are final now
             if (i + 1 < m && negligible(r, dn, dnext)) {
                 low2 = lowneg;
@@ -496,6 +522,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
             }
         }
         if (phase == QL_FIN) {
+            x[crow] = zx1;
             hdr[1 + 3 * nsw] = start;
             hdr[2 + 3 * nsw] = m - 1;
             hdr[3 + 3 * nsw] = nrot - start;
@@ -561,6 +588,8 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
                 start = nrot;
                 lowneg = m;
                 low2 = m;
+                zx1 = x[m];
+                crow = m;
                 ce = e[i];
                 cd0 = d[i];
                 cd1 = dm;
@@ -573,6 +602,9 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, const ClusterDesc* __restric
             }
         }
     }
+    for (int k = 0; k < n; ++k) dg[k] = d[k];
+    if (zg)
+        for (int k = 0; k < n; ++k) zg[k] = x[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -667,34 +699,56 @@ __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const Cluster
     const int nsw = hdr[0];
     for (int k = 0; k < nsw; ++k) {
         const int start = hdr[1 + 3 * k], i0 = hdr[2 + 3 * k], cnt = hdr[3 + 3 * k];
-        if (cnt == 0) continue;
-        double xi1 = P[(size_t)(i0 + 1) * w2 + r];
-        double xi = P[(size_t)i0 * w2 + r];
-        double2 cs = rot[start];
-        for (int u = 0; u < cnt; ++u) {
-            const int i = i0 - u;
-            // prefetch the next rotation's operands (independent of this rotation's result)
-            double xn = 0.0;
-            double2 csn = cs;
-            if (u + 1 < cnt) {
-                xn = P[(size_t)(i - 1) * w2 + r];
-                csn = rot[start + u + 1];
+        if (cnt > 0) sweep_fwd<DCLNO_REPLAY_DEPTH>(P + r, w2, rot + start, i0, cnt);
+    }
+}
+
+// C = X Y for a tall-skinny Y (n x w, w <= 32, row-major with stride w, staged in Ys):
+// FP64 tensor-core MMA (m8n8k4); warp k of 8 owns the 8-row blocks k, k+8, ... of C
+// and all its columns in 8-wide tiles, so the MMA work is padded only to a multiple
+// of 8 columns.  X is n x n row-major (ld), read once.
+__device__ static void tall_gemm_fp64(double* __restrict__ C, const double* __restrict__ X, int ld,
+                                      const double* __restrict__ Ys, int n, int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int fr = lane >> 2, fk = lane & 3;
+    const int nt = (w + 7) >> 3;
+    for (int rb = warp; rb * 8 < n; rb += nw) {
+        const int r = rb * 8 + fr;
+        const bool rok = r < n;
+        double acc[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < n; k += 4) {
+            const int kk = k + fk;
+            const double a = (rok && kk < n) ? X[(size_t)r * ld + kk] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j < nt) {  // uniform across the warp
+                    const int col = 8 * j + fr;
+                    const double b = (kk < n && col < w) ? Ys[(size_t)kk * w + col] : 0.0;
+                    dmma_8x8x4(acc[j][0], acc[j][1], a, b);
+                }
             }
-            // column update of Z G: z_{i+1} <- s z_i + c z_{i+1}, z_i <- c z_i - s z_{i+1}
-            P[(size_t)(i + 1) * w2 + r] = fma(cs.y, xi, cs.x * xi1);
-            xi1 = fma(cs.x, xi, -cs.y * xi1);
-            xi = xn;
-            cs = csn;
         }
-        P[(size_t)(i0 + 1 - cnt) * w2 + r] = xi1;
+        if (rok) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = 8 * j + 2 * fk + h;
+                    if (j < nt && col < w) C[(size_t)r * w + col] = acc[j][h];
+                }
+        }
     }
 }
 
 // Merge-matrix products of a torn cluster (one CTA per cluster):
 //   dir 0: P <- M^T P   (P = [n][2 mc] central strips; X = M^T stored row-major)
 //   dir 1: G <- M G     (G = [n][w] density columns in W; X = M)
-// as C -= X B^T with B = -Y^T staged in scratch (W for dir 0, the M^T area for dir 1)
-// and C = Y cleared.
+// Y is first copied to scratch (W for dir 0, the M^T area for dir 1).  FP64 path:
+// tall_gemm_fp64.  Mixed path: C -= X B^T on the emulated tile GEMM with B = -Y^T
+// staged in the scratch and C = Y cleared.
 template <bool EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterDesc* __restrict__ cls,
                                                                const int* __restrict__ order,
@@ -712,6 +766,12 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
     double* Y = (dir == 0) ? arena + d.cc_off : arena + d.aux_off + 3 * ld;
     double* Bt = (dir == 0) ? arena + d.aux_off + 3 * ld : MT;
     const double* X = (dir == 0) ? MT : M;
+    if (!EMU) {
+        for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Bt[e] = Y[e];
+        __syncthreads();
+        tall_gemm_fp64(Y, X, ld, Bt, n, w);
+        return;
+    }
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) {
         const int t = (int)(e / w), a = (int)(e % w);
         Bt[(size_t)a * ld + t] = -Y[e];
@@ -719,12 +779,8 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
     __syncthreads();
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Y[e] = 0.0;
     __syncthreads();
-    if (EMU) {
-        for (int k0 = 0; k0 < n; k0 += EG_K)
-            tile_update<false, true>(Y, w, X + k0, ld, Bt + k0, ld, n, w, min(EG_K, n - k0), 0, sm);
-    } else {
-        tile_update<false, false>(Y, w, X, ld, Bt, ld, n, w, n, 0, sm);
-    }
+    for (int k0 = 0; k0 < n; k0 += EG_K)
+        tile_update<false, true>(Y, w, X + k0, ld, Bt + k0, ld, n, w, min(EG_K, n - k0), 0, sm);
 }
 
 dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu) {
@@ -733,7 +789,7 @@ dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, boo
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
-    const size_t smb = emu ? (size_t)EG_SMEM_BYTES : (size_t)GT_SMEM_DOUBLES * sizeof(double);
+    const size_t smb = emu ? (size_t)EG_SMEM_BYTES : 0;
     ProfScope ps__(c, dir == 0 ? "k_mgemm_fwd" : "k_mgemm_rev");
     if (emu) {
         DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
@@ -802,7 +858,15 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_ql");
-        k_ql<<<(2 * N + 31) / 32, 32, 0, c->stream>>>(N, c->d_cl, order, c->d_arena, c->d_iters, c->d_status);
+        int segmax = 1;
+        for (int i = b.id_lo; i < b.id_hi; ++i) segmax = std::max(segmax, std::max(seg_len(c->cl[i], 0), seg_len(c->cl[i], 1)));
+        const int segp = segmax | 1;  // odd: lanes' arrays start in different banks
+        const int lanes = (int)std::max<long long>(1, std::min<long long>(32, (200LL * 1024) / (24LL * segp)));
+        const size_t smq = (size_t)lanes * 3 * segp * sizeof(double);
+        if (smq > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "tridiagonal segment too long for the QL kernel");
+        DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+        k_ql<<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
+                                                                 c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     {
