@@ -209,8 +209,9 @@ def _sc_lattice(nx, ny, nz, a):
     return g.reshape(-1, 3).astype(np.float64) * a, g.reshape(-1, 3)
 
 
-def make_system(cfg: int, seed: int | None = None, **over) -> System:
+def make_system(cfg: int, seed: int | None = None, n_atoms: int | None = None, **over) -> System:
     """One of the five workloads; keyword overrides replace r_core, r_lno, k_lno.
+    n_atoms (workload 5 only) packs fewer atoms at the same density (a smaller cube).
 
     1  64-atom simple-cubic 4x4x4, a=2.5, open, 4 s-Gaussians, 2 e/atom.
     2  1,728-atom rock-salt arrangement on SC 12^3, a=3.0, periodic, jitter 0.05,
@@ -261,7 +262,7 @@ def make_system(cfg: int, seed: int | None = None, **over) -> System:
                    n_electrons=1.0 * n, kT=0.005, r_core=6.0, r_lno=11.0, k_lno=3)
     elif cfg == 5:
         rng = np.random.default_rng(1005 if seed is None else seed)
-        n = 32000
+        n = 32000 if n_atoms is None else int(n_atoms)
         L = (n / 0.012) ** (1.0 / 3.0)
         pos = _rsa(n, L, 3.8, rng)
         species = np.zeros(n, np.int32)
@@ -269,7 +270,7 @@ def make_system(cfg: int, seed: int | None = None, **over) -> System:
         e = np.geomspace(0.08, 6.0, 13)
         base = np.linspace(-0.6, 0.5, 13)
         onsite = [base + (-0.15 if s == 0 else 0.15) for s in species]
-        sys = dict(name="cfg5_rsa32000", pos=pos, cell=np.eye(3) * L,
+        sys = dict(name=f"cfg5_rsa{n}", pos=pos, cell=np.eye(3) * L,
                    pbc=np.ones(3, bool), species=species,
                    exps=[e.copy() for _ in range(n)], onsite=onsite,
                    n_electrons=5.0 * n, kT=0.01, r_core=6.0, r_lno=10.0, k_lno=4)
@@ -294,41 +295,51 @@ def assemble_system(name, pos, cell, pbc, species, exps, onsite, n_electrons, kT
                   r_core=float(r_core), r_lno=float(r_lno), k_lno=int(k_lno))
 
 
-def _rsa(n, L, dmin, rng):
-    """Random sequential addition in a periodic cube with a minimum distance."""
-    nc = max(1, int(L // dmin))
-    cw = L / nc
-    grid: dict = {}
+def _rsa(n, L, dmin, rng, batch=65536):
+    """Random sequential addition in a periodic cube with a minimum distance.
+
+    Candidates are drawn uniformly in batches; a candidate is kept when no point
+    already placed (or kept earlier in the same batch) lies within dmin under the
+    minimum-image convention.  A cell grid of width <= dmin / sqrt(3) holds at most
+    one point per cell, so every conflict lies within two cells of the candidate.
+    """
+    g = max(1, int(L / (dmin / np.sqrt(3.0))))
+    cw = L / g
+    reach = int(np.ceil(dmin / cw))
+    occ = -np.ones((g, g, g), dtype=np.int64)
     pts = np.empty((n, 3))
+    off = np.array([(a, b, c) for a in range(-reach, reach + 1) for b in range(-reach, reach + 1)
+                    for c in range(-reach, reach + 1)], dtype=np.int64)
     k = 0
     tries = 0
     while k < n:
-        tries += 1
-        if tries > 200 * n:
+        if tries > 20000 * n:
             raise RuntimeError("random sequential addition jammed")
-        p = rng.uniform(0.0, L, size=3)
-        c = (p // cw).astype(int) % nc
-        ok = True
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    key = ((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc)
-                    for q in grid.get(key, ()):
-                        d = pts[q] - p
-                        d -= L * np.round(d / L)
-                        if d @ d < dmin * dmin:
-                            ok = False
-                            break
-                    if not ok:
-                        break
-                if not ok:
-                    break
-            if not ok:
-                break
-        if ok:
-            pts[k] = p
-            grid.setdefault(tuple(c), []).append(k)
+        cand = rng.uniform(0.0, L, size=(batch, 3))
+        tries += batch
+        cell = np.minimum((cand // cw).astype(np.int64), g - 1)
+        nb = (cell[:, None, :] + off[None, :, :]) % g
+        who = occ[nb[..., 0], nb[..., 1], nb[..., 2]]
+        d = pts[np.maximum(who, 0)] - cand[:, None, :]
+        d -= L * np.round(d / L)
+        bad = (who >= 0) & (np.einsum("bkd,bkd->bk", d, d) < dmin * dmin)
+        for b in np.nonzero(~bad.any(axis=1))[0]:
+            c = cell[b]
+            if occ[c[0], c[1], c[2]] >= 0:
+                continue
+            near = (c[None, :] + off) % g
+            w = occ[near[:, 0], near[:, 1], near[:, 2]]
+            w = w[w >= 0]
+            if len(w):  # points placed earlier in this batch
+                dd = pts[w] - cand[b]
+                dd -= L * np.round(dd / L)
+                if np.min(np.einsum("kd,kd->k", dd, dd)) < dmin * dmin:
+                    continue
+            pts[k] = cand[b]
+            occ[c[0], c[1], c[2]] = k
             k += 1
+            if k == n:
+                break
     return pts
 
 

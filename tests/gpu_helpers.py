@@ -47,3 +47,13 @@ def state_tol(r):
     n = len(r.eps)
     cc = np.einsum("am,am->m", r.C, r.C)
     return 1e-10 + 2.0 * n * U * (r.h_norm + np.abs(r.eps) * r.s_norm) * cc
+
+
+def rho_row_tol(r, big):
+    """Density-matrix elements of one cluster: rho = C F C^T with C S^(i)-orthonormal
+    has a first-order relative error of at most n u kappa for a backward error of
+    n u in S^(i), kappa = |S^(i)| max_mu c_mu^T c_mu (the condition number of the
+    cluster overlap); big is the largest element of the rows compared."""
+    n = len(r.eps)
+    kappa = r.s_norm * float(np.max(np.einsum("am,am->m", r.C, r.C)))
+    return 1e-9 + n * U * kappa * big
