@@ -34,11 +34,10 @@ WORKLOAD = ("DC-LNO step, 1728-atom gapped rock-salt (12^3 SC sites, a=3.0 bohr,
             "9 s-Gaussians/atom, r_core=6, r_lno=10 bohr, 3 LNOs/atom, kT=0.01 Ha), FP64")
 DOMINANT = "k_tridiag"
 CPU_SAMPLE_CLUSTERS = 8
-# DRAM read + write of one FP64 k_tridiag launch on the small64 workload (ncu, see
-# profiles/k_tridiag_fp64_small.md) and that workload's sum of n^3; the bench's
-# traffic figure scales it by the cubic work of its own clusters.
-TRIDIAG_TRAFFIC_SMALL64 = 821.0e6
-TRIDIAG_SUM_N3_SMALL64 = 9337346712.0
+# DRAM read + write of one FP64 k_tridiag launch, captured by ncu on each workload
+# itself (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture; see
+# profiles/k_tridiag_fp64_rocksalt1728.md and profiles/k_tridiag_fp64_small.md)
+TRIDIAG_TRAFFIC = {"rocksalt1728": 842008137216.0 + 60257138176.0, "small64": 384489728.0 + 284888320.0}
 
 
 def parse():
@@ -297,10 +296,11 @@ def run_ours(args):
     dfma, dmma = measure_fp64_peaks()
     peak = 1.0 / (0.5 / dfma + 0.5 / dmma)
     achieved = flops / (k_ms / max(k_n, 1) / 1e3) / 1e12 if k_n else None
-    traffic = TRIDIAG_TRAFFIC_SMALL64 * float(np.sum(dims.astype(np.float64) ** 3)) / TRIDIAG_SUM_N3_SMALL64
+    traffic = TRIDIAG_TRAFFIC.get(args.workload)
     roofline = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "traffic_source": "ncu DRAM bytes of k_tridiag on small64, scaled by sum n^3",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 k_tridiag launch "
+                                  "on this workload",
                 "peak_source": f"measured in-process: FP64 FMA {dfma:.3f} and FP64 MMA {dmma:.3f} TFLOP/s, "
                                "weighted 1:1 by the kernel's flop mix (symv on FMA, rank-2k on MMA)",
                 "flops_per_launch": flops, "launch_ms": k_ms / max(k_n, 1)}
