@@ -183,6 +183,27 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (replicas: one whole workload per rank)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x, world, device=None):
+    """The largest of the ranks' values (a job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, clusters, steps, seconds):
+    """Clusters per second of the whole job: every rank solves all clusters of its
+    own copy of the workload, the job takes the slowest rank's time."""
+    return world * clusters * steps / seconds
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -240,11 +261,8 @@ def run_ours(args):
     k_ms, k_n = ctx.kernel_time(DOMINANT)
     ctx.set_profiling(False)
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncl * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = replica_throughput(world, ncl, args.steps, ms / 1e3)
 
     # the mixed-precision form of the same step (BF16 tensor-core emulation of the FP64
     # contractions), timed the same way; accuracy against the FP64 step above
@@ -259,13 +277,12 @@ def run_ours(args):
         mu_mx, n_mx, e_mx = step(DCLNO_MIXED)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ms_mx = ev0.elapsed_time(ev1)
     kmx_ms, kmx_n = ctx.kernel_time(DOMINANT)
     ctx.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms_mx], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mx = float(t.item())
+    ms_mx = max_over_ranks(ms_mx, world, dev)
 
     # e2e: the C-ABI step with host buffers (H2D of rho_in and D2H of rho_out inside)
     e2e = None
@@ -281,12 +298,10 @@ def run_ours(args):
             ctx.step(h_in, h_out, s.n_electrons, s.kT, host_buffers=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, world, dev)
         nbytes = int(rho_host.nbytes)
-        e2e = {"value": world * ncl * args.steps / dt, "unit": "clusters/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": replica_throughput(world, ncl, args.steps, dt), "unit": "clusters/s",
+               "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
     # roofline of the dominant kernel: algorithmic flops of Householder tridiagonalisation,
@@ -306,7 +321,7 @@ def run_ours(args):
                 "flops_per_launch": flops, "launch_ms": k_ms / max(k_n, 1)}
 
     achieved_mx = flops / (kmx_ms / max(kmx_n, 1) / 1e3) / 1e12 if kmx_n else None
-    mixed = {"value": world * ncl * args.steps / (ms_mx / 1e3), "unit": "clusters/s", "ms_per_step": ms_mx / args.steps,
+    mixed = {"value": replica_throughput(world, ncl, args.steps, ms_mx / 1e3), "unit": "clusters/s", "ms_per_step": ms_mx / args.steps,
              "speedup_vs_fp64": ms / ms_mx, "e_band_err_per_atom_vs_fp64": abs(e_mx - e_band) / s.natoms,
              "mu_diff_vs_fp64": abs(mu_mx - mu), "dtype": "bf16 slices (8 x 8 bit) emulating f64 contractions; f64 elsewhere",
              "roofline": {"bound": "alu", "kernel": DOMINANT, "achieved": achieved_mx, "peak": dfma, "unit": "TFLOP/s",
