@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
     p.add_argument("--workload", choices=["rocksalt1728", "small64"], default="rocksalt1728",
                    help="small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels")
     return p.parse_args()
@@ -204,6 +205,53 @@ def replica_throughput(world, clusters, steps, seconds):
 
 
 # ---------------------------------------------------------------------------
+# the SCF loop (mixing) on the metallic bcc slab
+# ---------------------------------------------------------------------------
+SCF_WORKLOAD = ("SCF loop, 7840-atom bcc slab (20x20x10 cells, a=5.4 bohr, 2% vacancies, vacuum in z, "
+                "9 s-Gaussians/atom, r_core=6, r_lno=11 bohr, 3 LNOs/atom, kT=0.005 Ha): 5 steps of LNO "
+                "regeneration, solve, mu search, rho rows and linear mixing 0.3, one CUDA graph per step")
+SCF_STEPS = 5
+
+
+def measure_scf(world):
+    """Five SCF steps (dclno_scf_run, captured graph) in each precision, CUDA events
+    on the context's stream; inputs resident on the device."""
+    import torch
+
+    import tbsystems as T
+    from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context
+
+    s = T.make_system(4)
+    rho0 = torch.from_numpy(T.synthetic_density(s, seed=4)).cuda()
+    H = torch.from_numpy(s.H).cuda()
+    S = torch.from_numpy(s.S).cuda()
+    stream = torch.cuda.Stream()
+    out = {"workload": SCF_WORKLOAD, "steps": SCF_STEPS, "clusters": s.natoms}
+    with torch.cuda.stream(stream):
+        ctx = Context(stream=stream.cuda_stream)
+        ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
+                           s.r_core, s.r_lno, s.k_lno)
+        dims = ctx.cluster_info()[0]
+        out["cluster_dim_min"], out["cluster_dim_max"] = int(dims.min()), int(dims.max())
+        for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
+            rho = rho0.clone()
+            ctx.scf_run(rho, 1, 0.3, s.n_electrons, s.kT, prec, use_graph=True)  # warm-up
+            rho = rho0.clone()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mu, n, eb = ctx.scf_run(rho, SCF_STEPS, 0.3, s.n_electrons, s.kT, prec, use_graph=True)
+            e1.record(stream)
+            stream.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            out[name] = {"value": replica_throughput(world, s.natoms, SCF_STEPS, ms / 1e3), "unit": "clusters/s",
+                         "ms_per_step": ms / SCF_STEPS, "mu_last": float(mu[-1]), "e_band_last": float(eb[-1])}
+        ctx.close()
+    out["e_band_diff_per_atom_mixed_vs_fp64"] = abs(out["mixed"]["e_band_last"] - out["fp64"]["e_band_last"]) / s.natoms
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -330,6 +378,11 @@ def run_ours(args):
                                          "mixed kernel against the native FP64 roofline",
                           "launch_ms": kmx_ms / max(kmx_n, 1)}}
 
+    scf = None
+    if not args.no_scf:
+        ctx.close()
+        scf = measure_scf(world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         th = cpu_threads()
@@ -346,7 +399,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "mixed": mixed, "mu": mu, "n_electrons": n_mu, "e_band": e_band}
+                "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "mu": mu, "n_electrons": n_mu, "e_band": e_band}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -47,8 +47,11 @@ __global__ void __launch_bounds__(128) k_pair_index(const ClusterDesc* __restric
 }
 
 // Per stored block b (rows of atom j1, columns of atom j2) and X = H, S:
-//   LP = V_j1^T X (k x M2), PL = X V_j2 (M1 x k), LL = V_j1^T X V_j2 (k x k),
+//   LP = V_j1^T X (k x M2), PL = X V_j2 (M1 x k), LL = V_j1^T X V_j2 = V_j1^T PL (k x k),
 // stored at tblk + tblk_off[b] as [LP_H | LP_S | PL_H | PL_S | LL_H | LL_S].
+// One warp per block: LP and PL elements over the lanes, then LL from the PL just
+// written (a warp's FP64 instruction costs the same whatever its active lanes, so
+// the work is spread evenly instead of recomputing X V_j2 inside every LL element).
 __global__ void k_lno_blocks(long long nnzb, int k, const int* __restrict__ brow, const long long* __restrict__ key,
                              const int* __restrict__ norb, const long long* __restrict__ blk_off,
                              const long long* __restrict__ voff, const long long* __restrict__ tblk_off,
@@ -65,7 +68,9 @@ __global__ void k_lno_blocks(long long nnzb, int k, const int* __restrict__ brow
         const double* Xs = S + blk_off[b];
         double* out = tblk + tblk_off[b];
         const int nlp = k * M2, npl = M1 * k, nll = k * k;
-        for (int e = lane; e < nlp + npl + nll; e += 32) {
+        double* PLh = out + 2 * nlp;
+        double* PLs = PLh + npl;
+        for (int e = lane; e < nlp + npl; e += 32) {
             double h = 0.0, s = 0.0;
             if (e < nlp) {
                 const int p = e / M2, q = e % M2;
@@ -76,32 +81,30 @@ __global__ void k_lno_blocks(long long nnzb, int k, const int* __restrict__ brow
                 }
                 out[e] = h;
                 out[nlp + e] = s;
-            } else if (e < nlp + npl) {
+            } else {
                 const int f = e - nlp, p = f / k, q = f % k;
                 for (int t = 0; t < M2; ++t) {
                     const double v = V2[t * k + q];
                     h = fma(Xh[p * M2 + t], v, h);
                     s = fma(Xs[p * M2 + t], v, s);
                 }
-                out[2 * nlp + f] = h;
-                out[2 * nlp + npl + f] = s;
-            } else {
-                const int f = e - nlp - npl, p = f / k, q = f % k;
-                for (int t = 0; t < M1; ++t) {
-                    double ht = 0.0, st = 0.0;
-                    for (int u = 0; u < M2; ++u) {
-                        const double v = V2[u * k + q];
-                        ht = fma(Xh[t * M2 + u], v, ht);
-                        st = fma(Xs[t * M2 + u], v, st);
-                    }
-                    const double w = V1[t * k + p];
-                    h = fma(w, ht, h);
-                    s = fma(w, st, s);
-                }
-                out[2 * nlp + 2 * npl + f] = h;
-                out[2 * nlp + 2 * npl + nll + f] = s;
+                PLh[f] = h;
+                PLs[f] = s;
             }
         }
+        __syncwarp();
+        for (int f = lane; f < nll; f += 32) {
+            const int p = f / k, q = f % k;
+            double h = 0.0, s = 0.0;
+            for (int t = 0; t < M1; ++t) {
+                const double w = V1[t * k + p];
+                h = fma(w, PLh[t * k + q], h);
+                s = fma(w, PLs[t * k + q], s);
+            }
+            out[2 * nlp + 2 * npl + f] = h;
+            out[2 * nlp + 2 * npl + nll + f] = s;
+        }
+        __syncwarp();
     }
 }
 
