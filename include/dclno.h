@@ -152,6 +152,22 @@ dclno_status dclno_set_workspace_limit(dclno_ctx *ctx, size_t bytes);
 dclno_status dclno_batch_info(dclno_ctx *ctx, int *nbatches_out, size_t *workspace_bytes_out);
 
 /*
+ * Launch-shape autotuner (on by default).  The first solve of each batch made
+ * outside stream capture (dclno_solve_clusters, dclno_step) times the QL kernel,
+ * whose lanes are tridiagonal segments run in lockstep within a warp, at 4, 8, 12,
+ * 16, 24 and 32 lanes per warp on the batch's own matrices (restoring its input
+ * between tries; the results do not depend on the choice) and keeps the fastest
+ * for later solves; this allocates a scratch copy of the batch's tridiagonal
+ * matrices once (2 n doubles per cluster).  With it off, or before any eager solve
+ * (a first dclno_scf_run), the most lanes that fit in shared memory are used.
+ * dclno_get_tuning returns the chosen lanes per warp of batch `batch` (0 = not
+ * tuned yet) and, in candidate_ms[6] (host, nullable), the timed milliseconds of
+ * each candidate (-1 = not tried).  The paper has no counterpart.
+ */
+dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
+dclno_status dclno_get_tuning(dclno_ctx *ctx, int batch, int *ql_lanes_out, float *candidate_ms);
+
+/*
  * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
  * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
  * implicit QL on the tridiagonal matrix, and the central-atom rows of the

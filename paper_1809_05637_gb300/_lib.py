@@ -19,7 +19,8 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_solve_clusters", "dclno_find_mu", "dclno_density_matrix", "dclno_step", "dclno_cluster_info",
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
-           "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info"]
+           "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
+           "dclno_set_autotune", "dclno_get_tuning"]
 
 
 class DclnoError(RuntimeError):
@@ -81,6 +82,8 @@ def load_library():
         "dclno_density_matrices": ([P, D, D, P, P, P], I),
         "dclno_set_workspace_limit": ([P, ctypes.c_size_t], I),
         "dclno_batch_info": ([P, P, P], I),
+        "dclno_set_autotune": ([P, I], I),
+        "dclno_get_tuning": ([P, I, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -176,6 +179,19 @@ class Context:
         self._check(self.lib.dclno_batch_info(self.h, ctypes.cast(ctypes.byref(nb), ctypes.c_void_p),
                                               ctypes.cast(ctypes.byref(ws), ctypes.c_void_p)))
         return nb.value, ws.value
+
+    def set_autotune(self, on=True):
+        """Time the QL launch shape on each batch's first eager solve (default on)."""
+        self._check(self.lib.dclno_set_autotune(self.h, int(bool(on))))
+
+    def tuning(self, batch=0):
+        """(QL lanes per warp chosen for `batch` (0 = not tuned), timed ms of the candidates
+        4, 8, 12, 16, 24, 32 lanes (-1 = not tried))."""
+        lanes = ctypes.c_int()
+        ms = np.zeros(6, np.float32)
+        self._check(self.lib.dclno_get_tuning(self.h, int(batch), ctypes.cast(ctypes.byref(lanes), ctypes.c_void_p),
+                                              _ptr(ms)))
+        return lanes.value, ms
 
     # ---- the five calls of a DC-LNO step
     def build_clusters(self, pos, cell, pbc, norb, row_ptr, col, shift, blk_off, H, S, r_core, r_lno, k_lno):

@@ -62,6 +62,10 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_rho_out);
     dfree(c->d_err);
     dfree(c->d_hist);
+    dfree(c->d_tune);
+    c->tune_doubles = 0;
+    c->ql_lanes.clear();
+    c->ql_tune_ms.clear();
     c->hist_cap = 0;
     c->built = c->lnos_ready = c->solved = false;
 }
@@ -446,6 +450,9 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     }
     c->arena_doubles = (size_t)arena_max;
     c->resident = -1;
+    for (size_t k = 0; k < c->batches.size(); ++k) c->batches[k].index = (int)k;
+    c->ql_lanes.assign(c->batches.size(), 0);
+    c->ql_tune_ms.assign(c->batches.size() * DCLNO_QL_CANDIDATES, -1.0f);
 
     // ---- LNO storage offsets
     std::vector<long long> voff(N + 1), loff(N + 1), moff(N + 1);
@@ -633,6 +640,23 @@ extern "C" dclno_status dclno_set_workspace_limit(dclno_ctx* c, size_t bytes) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
     c->ws_limit = bytes;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_autotune(dclno_ctx* c, int on) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    c->autotune = on != 0;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_get_tuning(dclno_ctx* c, int batch, int* ql_lanes, float* candidate_ms) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->built || batch < 0 || batch >= (int)c->batches.size())
+        return set_err(c, DCLNO_ERR_ARG, "dclno_get_tuning: build clusters first; batch out of range");
+    if (ql_lanes) *ql_lanes = c->ql_lanes[batch];
+    if (candidate_ms)
+        for (int k = 0; k < DCLNO_QL_CANDIDATES; ++k) candidate_ms[k] = c->ql_tune_ms[batch * DCLNO_QL_CANDIDATES + k];
     return DCLNO_OK;
 }
 

@@ -46,6 +46,7 @@ __host__ __device__ inline int seg_len(const ClusterDesc& d, int s) {
     return d.split ? (s ? d.n - d.split : d.split) : (s ? 0 : d.n);
 }
 #define DCLNO_TEAR_MIN 64  // tear tridiagonal matrices of at least this dimension
+#define DCLNO_QL_CANDIDATES 6  // QL lanes per warp tried by the autotuner: 4, 8, 12, 16, 24, 32
 
 struct MemberDesc {
     int atom;   // j
@@ -87,6 +88,7 @@ struct Batch {
     long long mbeg = 0, mend = 0;   // their members
     int maxn = 0, mcmax = 1;
     long long arena_doubles = 0, iters = 0;
+    int index = 0;                  // position in dclno_ctx::batches
 };
 
 // ---------------------------------------------------------------------------
@@ -129,6 +131,12 @@ struct dclno_ctx {
     int resident = -1;                // batch whose solved workspace is in the arena
     dclno_precision solved_prec = DCLNO_FP64;
     size_t ws_limit = 0;              // workspace limit in bytes (0 = free device memory)
+    // launch-shape autotuner: QL lanes per warp chosen per batch by timing (0 = not yet)
+    bool autotune = true;
+    std::vector<int> ql_lanes;
+    std::vector<float> ql_tune_ms;    // per batch: the timed candidates (lanes 4, 8, 12, 16, 24, 32)
+    double* d_tune = nullptr;         // saved d, e of a batch while candidates are timed
+    size_t tune_doubles = 0;
     std::vector<MemberDesc> mem;
     long long total_dim = 0;
     ClusterDesc* d_cl = nullptr;

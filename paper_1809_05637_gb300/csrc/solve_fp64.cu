@@ -823,6 +823,84 @@ __global__ void k_weights(const ClusterDesc* __restrict__ cls, const int* __rest
 }
 
 
+static dclno_status launch_ql(dclno_ctx* c, const int* order, int N, int segp, int lanes) {
+    const size_t smq = (size_t)lanes * 3 * segp * sizeof(double);
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+    k_ql<<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
+                                                             c->d_iters, c->d_status);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+// save (dir 0) or restore (dir 1) d and e of a batch's clusters (the QL input)
+__global__ void k_save_de(const ClusterDesc* __restrict__ cls, const int* __restrict__ order, double* __restrict__ arena,
+                          double* __restrict__ buf, int stride, int dir) {
+    const ClusterDesc d = cls[order[blockIdx.x]];
+    double* dv = arena + d.aux_off;
+    double* bv = buf + (size_t)blockIdx.x * stride;
+    for (int t = threadIdx.x; t < d.n; t += blockDim.x) {
+        if (dir == 0) {
+            bv[t] = dv[t];
+            bv[d.n + t] = dv[d.ld + t];
+        } else {
+            dv[t] = bv[t];
+            dv[d.ld + t] = bv[d.n + t];
+        }
+    }
+}
+
+// Launch-shape autotuner for k_ql: a lane is one tridiagonal segment and a warp runs
+// its lanes in lockstep, so the lanes per warp trade the warp's mixed-phase overhead
+// against how many warps share an SM (its FP64 pipe and shared memory).  The best
+// count depends on the cluster count and segment lengths; each candidate is timed
+// once on this batch's own tridiagonal matrices (d and e restored before each try;
+// every lane's arithmetic is the same whatever the grouping, so the results are too).
+static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int N, int segp, int fit) {
+    static const int cand[DCLNO_QL_CANDIDATES] = {4, 8, 12, 16, 24, 32};
+    int ldmax = 0;
+    for (int i = b.id_lo; i < b.id_hi; ++i) ldmax = std::max(ldmax, c->cl[i].n);
+    const int stride = 2 * ldmax;
+    const size_t need = (size_t)N * stride;
+    if (c->tune_doubles < need) {
+        if (c->d_tune) cudaFree(c->d_tune);
+        c->d_tune = nullptr;
+        c->tune_doubles = 0;
+        DCLNO_CUDA(c, cudaMalloc(&c->d_tune, need * sizeof(double)));
+        c->tune_doubles = need;
+    }
+    k_save_de<<<N, 128, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_tune, stride, 0);
+    DCLNO_LAUNCHED(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DCLNO_CUDA(c, cudaEventCreate(&e0));
+    DCLNO_CUDA(c, cudaEventCreate(&e1));
+    int best = fit;
+    float best_ms = -1.0f;
+    dclno_status st = DCLNO_OK;
+    for (int k = 0; k < DCLNO_QL_CANDIDATES && st == DCLNO_OK; ++k) {
+        if (cand[k] > fit) continue;
+        k_save_de<<<N, 128, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_tune, stride, 1);
+        c->launches++;
+        cudaEventRecord(e0, c->stream);
+        st = launch_ql(c, order, N, segp, cand[k]);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.0f;
+        if (st == DCLNO_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            c->ql_tune_ms[b.index * DCLNO_QL_CANDIDATES + k] = ms;
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = cand[k];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != DCLNO_OK) return st;
+    k_save_de<<<N, 128, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_tune, stride, 1);
+    DCLNO_LAUNCHED(c);
+    c->ql_lanes[b.index] = best;
+    return DCLNO_OK;
+}
+
 template <bool EMU>
 static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     const int N = b.oend - b.obeg;  // clusters of the batch
@@ -857,18 +935,21 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     }
     DCLNO_LAUNCHED(c);
     {
-        ProfScope ps__(c, "k_ql");
         int segmax = 1;
         for (int i = b.id_lo; i < b.id_hi; ++i) segmax = std::max(segmax, std::max(seg_len(c->cl[i], 0), seg_len(c->cl[i], 1)));
         const int segp = segmax | 1;  // odd: lanes' arrays start in different banks
-        const int lanes = (int)std::max<long long>(1, std::min<long long>(32, (200LL * 1024) / (24LL * segp)));
-        const size_t smq = (size_t)lanes * 3 * segp * sizeof(double);
-        if (smq > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "tridiagonal segment too long for the QL kernel");
-        DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
-        k_ql<<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
-                                                                 c->d_iters, c->d_status);
+        const int fit = (int)std::min<long long>(32, (200LL * 1024) / (24LL * segp));  // shared memory bound
+        if (fit < 1) return set_err(c, DCLNO_ERR_ARG, "tridiagonal segment too long for the QL kernel");
+        int& lanes = c->ql_lanes[b.index];
+        if (lanes == 0 && c->autotune && !c->deferred) {
+            const dclno_status st = tune_ql(c, b, order, N, segp, fit);
+            if (st != DCLNO_OK) return st;
+        }
+        const int use = lanes > 0 ? std::min(lanes, fit) : fit;
+        ProfScope ps__(c, "k_ql");
+        const dclno_status st = launch_ql(c, order, N, segp, use);
+        if (st != DCLNO_OK) return st;
     }
-    DCLNO_LAUNCHED(c);
     {
         const dclno_status st = launch_merge(c, b);
         if (st != DCLNO_OK) return st;
