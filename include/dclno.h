@@ -113,6 +113,23 @@ dclno_status dclno_build_clusters(dclno_ctx *ctx, const dclno_system *sys,
                                   double r_core, double r_lno, int k_lno);
 
 /*
+ * The same with the paper's region rule (Sec. III, steps (i)-(iv)) instead of a
+ * fixed short-range radius: for each centre, the images within r_lno are split
+ * into first neighbouring atoms (their stored overlap block with the centre has
+ * an element of magnitude above s_fna; s_fna = 0 is the literal "non-zero
+ * overlap", the centre counts as one) and second neighbouring atoms; the
+ * short-range radius is the shell distance whose sphere holds a number of atoms
+ * closest to N_F + kappa N_S (ties: the larger sphere), the rest up to r_lno is
+ * the long-range (LNO) region.  The paper uses kappa = 3/10.  With Gaussian
+ * bases every atom within r_lno overlaps the centre unless s_fna is raised, and
+ * the rule then keeps every atom in the short-range region.
+ * Errors: as dclno_build_clusters; DCLNO_ERR_ARG for kappa outside [0, 1] or
+ * s_fna < 0.
+ */
+dclno_status dclno_build_clusters_kappa(dclno_ctx *ctx, const dclno_system *sys,
+                                        double r_lno, int k_lno, double kappa, double s_fna);
+
+/*
  * LNOs of every atom (Sec. II.B, steps (i)-(iii) of LNO generation):
  * Lambda_0i = sum_Rj rho_{0i,Rj} S_{Rj,0i} (Eq. (Lambda)) from the device density
  * matrix `rho` [nval] in the BSR pattern of S; eigenvalues of the nonsymmetric

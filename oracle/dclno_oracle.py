@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "cholesky", "jacobi", "gen_eig", "nonsym_eig", "inverse_iter",
-    "Cluster", "cluster_members", "lambda_blocks", "lnos", "compute_lnos",
+    "Cluster", "cluster_members", "kappa_radius", "lambda_blocks", "lnos", "compute_lnos",
     "assemble", "solve_cluster", "fermi", "n_of_mu", "find_mu", "density_rows",
     "dclno_solve", "finish_step", "energy_density", "plain_dc_density", "full_diag", "dense_matrices",
     "cluster_dim", "time_ratio", "NoBracket", "NotSPD",
@@ -157,11 +157,51 @@ def _shift_range(system, rmax):
     return np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, 3)
 
 
-def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int) -> Cluster:
+def kappa_radius(dist, fna, kappa):
+    """Short-range radius of the region rule of Sec. III, steps (ii)-(iii).
+
+    dist: distances of all images within r_L (the centre included); fna: True
+    for first neighbouring atoms (non-zero overlap with the centre, the centre
+    itself included), False for second neighbouring atoms.  The radius is the
+    shell distance whose sphere holds a number of atoms closest to
+    N_F + kappa N_S (ties: the larger sphere).
+    """
+    n_f = int(np.count_nonzero(fna))
+    n_s = len(fna) - n_f
+    target = n_f + kappa * n_s
+    best_r, best_gap, best_cnt = 0.0, math.inf, -1
+    for r in np.unique(dist):
+        cnt = int(np.count_nonzero(dist <= r + MEMBER_TOL))
+        gap = abs(cnt - target)
+        if gap < best_gap - 1e-12 or (abs(gap - best_gap) <= 1e-12 and cnt > best_cnt):
+            best_r, best_gap, best_cnt = float(r), gap, cnt
+    return best_r
+
+
+def _overlaps_centre(system, i, atoms, shifts, s_fna):
+    """Members whose stored S block with the centre has max |S| > s_fna."""
+    bidx = _BlockIndex(system)
+    out = np.zeros(len(atoms), dtype=bool)
+    mi = int(system.norb[i])
+    for m, (j, sh) in enumerate(zip(atoms, shifts)):
+        b = bidx.get(i, j, sh)
+        if b is None:
+            continue
+        mj = int(system.norb[j])
+        o = int(system.blk_off[b])
+        out[m] = float(np.max(np.abs(system.S[o:o + mi * mj]))) > s_fna
+    return out
+
+
+def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int, kappa: float | None = None,
+                    s_fna: float = 0.0) -> Cluster:
     """Members of the truncated cluster of atom i.
 
     Core (PAO) region: images (j, R) with |tau_j + R - tau_i| <= r_core;
     LNO region: r_core < d <= r_lno (membership tolerance MEMBER_TOL).
+    With kappa given, r_core is replaced by the radius of the region rule of
+    Sec. III (kappa_radius), first neighbouring atoms being those whose stored
+    overlap block with the centre exceeds s_fna in magnitude.
     Member order: distance descending, ties by (j, R), so the central atom
     is last.  Core members contribute M_j basis functions, LNO members k_lno.
     """
@@ -177,6 +217,8 @@ def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int) -> 
     atoms = j_idx[order].astype(np.int64)
     sh = sh[order].astype(np.int64)
     dist = dist[order]
+    if kappa is not None:
+        r_core = kappa_radius(dist, _overlaps_centre(system, i, atoms, sh, s_fna), kappa)
     core = dist <= r_core + MEMBER_TOL
     # the central atom itself (d = 0) must be the last member
     assert atoms[-1] == i and not np.any(sh[-1]), "central atom is not last"
@@ -469,16 +511,17 @@ def _threads():
 
 
 def dclno_solve(system, V: dict, r_core: float, r_lno: float, k_lno: int, atoms=None,
-                threads: int | None = None) -> dict:
+                threads: int | None = None, kappa: float | None = None, s_fna: float = 0.0) -> dict:
     """Clusters, assembly and eigen-solve for the given atoms (default all).
 
     Returns atom -> ClusterResult.  ``V`` must hold the LNOs of every atom that
-    appears in an LNO region (unused when r_lno == r_core).
+    appears in an LNO region (unused when r_lno == r_core).  kappa, s_fna: the
+    region rule of Sec. III instead of the fixed r_core (see cluster_members).
     """
     if atoms is None:
         atoms = list(range(system.natoms))
     bidx = _BlockIndex(system)
-    clusters = [cluster_members(system, i, r_core, r_lno, k_lno) for i in atoms]
+    clusters = [cluster_members(system, i, r_core, r_lno, k_lno, kappa, s_fna) for i in atoms]
     for cl in clusters:  # warm the per-row lookup tables outside the threads
         for j in set(int(a) for a in cl.atoms):
             bidx.row(j)

@@ -20,7 +20,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
-           "dclno_set_autotune", "dclno_get_tuning"]
+           "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa"]
 
 
 class DclnoError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library():
         "dclno_batch_info": ([P, P, P], I),
         "dclno_set_autotune": ([P, I], I),
         "dclno_get_tuning": ([P, I, P, P], I),
+        "dclno_build_clusters_kappa": ([P, ctypes.POINTER(dclno_system), D, I, D, D], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -194,7 +195,10 @@ class Context:
         return lanes.value, ms
 
     # ---- the five calls of a DC-LNO step
-    def build_clusters(self, pos, cell, pbc, norb, row_ptr, col, shift, blk_off, H, S, r_core, r_lno, k_lno):
+    def build_clusters(self, pos, cell, pbc, norb, row_ptr, col, shift, blk_off, H, S, r_core, r_lno, k_lno,
+                       kappa=None, s_fna=0.0):
+        """Truncated clusters with a fixed short-range radius r_core, or with the
+        paper's region rule (kappa, s_fna given; r_core is then ignored)."""
         host = dict(
             pos=np.ascontiguousarray(pos, dtype=np.float64), cell=np.ascontiguousarray(cell, dtype=np.float64),
             pbc=np.ascontiguousarray(np.asarray(pbc).astype(np.int32)),
@@ -206,7 +210,12 @@ class Context:
                          pbc=_ptr(host["pbc"]), norb=_ptr(host["norb"]), nnzb=len(host["col"]), nval=nval,
                          row_ptr=_ptr(host["row_ptr"]), col=_ptr(host["col"]), shift=_ptr(host["shift"]),
                          blk_off=_ptr(host["blk_off"]), H=_ptr(H), S=_ptr(S))
-        self._check(self.lib.dclno_build_clusters(self.h, ctypes.byref(s), float(r_core), float(r_lno), int(k_lno)))
+        if kappa is None:
+            self._check(self.lib.dclno_build_clusters(self.h, ctypes.byref(s), float(r_core), float(r_lno),
+                                                      int(k_lno)))
+        else:
+            self._check(self.lib.dclno_build_clusters_kappa(self.h, ctypes.byref(s), float(r_lno), int(k_lno),
+                                                            float(kappa), float(s_fna)))
         self._keep = [H, S]
         self.natoms = len(host["norb"])
         self.nval = nval

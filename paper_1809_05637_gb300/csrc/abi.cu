@@ -214,17 +214,76 @@ static dclno_status copy_to_device(dclno_ctx* c, void** dst, const void* src, si
     return DCLNO_OK;
 }
 
-extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* sys, double r_core,
-                                             double r_lno, int k_lno) {
-    if (!c) return DCLNO_ERR_ARG;
-    c->err.clear();
-    if (!sys || sys->natoms <= 0 || !sys->pos || !sys->cell || !sys->pbc || !sys->norb || !sys->row_ptr ||
-        !sys->col || !sys->shift || !sys->blk_off || !sys->H || !sys->S)
-        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters: null or empty system");
-    if (!(r_core >= 0.0) || !(r_lno >= r_core) || k_lno < 0)
-        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters: need 0 <= r_core <= r_lno and k_lno >= 0");
+// largest |S| of every stored block (the first-neighbour test of the region rule)
+__global__ void k_block_absmax(long long nnzb, const long long* __restrict__ off, const int* __restrict__ sz,
+                               const double* __restrict__ S, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; b < nnzb;
+         b += ((long long)gridDim.x * blockDim.x) >> 5) {
+        double m = 0.0;
+        for (int e = lane; e < sz[b]; e += 32) m = fmax(m, fabs(S[off[b] + e]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) out[b] = m;
+    }
+}
+
+static dclno_status block_absmax(dclno_ctx* c, const double* S, std::vector<double>& out) {
+    std::vector<int> sz(c->nnzb);
+    for (int i = 0; i < c->N; ++i)
+        for (long long b = c->row_ptr[i]; b < c->row_ptr[i + 1]; ++b) sz[b] = c->norb[i] * c->norb[c->col[b]];
+    long long* d_off = nullptr;
+    int* d_sz = nullptr;
+    double* d_out = nullptr;
+    out.assign(c->nnzb, 0.0);
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_off, sizeof(long long) * std::max<long long>(c->nnzb, 1))) == cudaSuccess &&
+        (e = cudaMalloc(&d_sz, sizeof(int) * std::max<long long>(c->nnzb, 1))) == cudaSuccess &&
+        (e = cudaMalloc(&d_out, sizeof(double) * std::max<long long>(c->nnzb, 1))) == cudaSuccess &&
+        (e = cudaMemcpy(d_off, c->blk_off.data(), sizeof(long long) * c->nnzb, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemcpy(d_sz, sz.data(), sizeof(int) * c->nnzb, cudaMemcpyHostToDevice)) == cudaSuccess) {
+        const int grid = (int)std::min<long long>((c->nnzb * 32 + 255) / 256, 152LL * 64);
+        k_block_absmax<<<std::max(grid, 1), 256, 0, c->stream>>>(c->nnzb, d_off, d_sz, S, d_out);
+        c->launches++;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(out.data(), d_out, sizeof(double) * c->nnzb, cudaMemcpyDeviceToHost);
+    }
+    if (d_off) cudaFree(d_off);
+    if (d_sz) cudaFree(d_sz);
+    if (d_out) cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_err(c, e, "overlap block maxima for the region rule");
+    return DCLNO_OK;
+}
+
+// Short-range radius of the region rule (Sec. III (ii)-(iii)): the shell whose sphere
+// holds a number of atoms closest to N_F + kappa N_S (ties: the larger sphere).  dd:
+// member distances ascending; fna: the same members' first-neighbour flags.
+static double kappa_radius(const std::vector<double>& dd, const std::vector<char>& fna, double kappa, double tol) {
+    long long nf = 0;
+    for (char f : fna) nf += f ? 1 : 0;
+    const double target = (double)nf + kappa * (double)((long long)dd.size() - nf);
+    double best_r = 0.0, best_gap = 1e300;
+    long long best_cnt = -1;
+    for (size_t k = 0; k < dd.size(); ++k) {
+        if (k > 0 && dd[k] == dd[k - 1]) continue;
+        const long long cnt = std::upper_bound(dd.begin(), dd.end(), dd[k] + tol) - dd.begin();
+        const double gap = std::fabs((double)cnt - target);
+        if (gap < best_gap - 1e-12 || (std::fabs(gap - best_gap) <= 1e-12 && cnt > best_cnt)) {
+            best_r = dd[k];
+            best_gap = gap;
+            best_cnt = cnt;
+        }
+    }
+    return best_r;
+}
+
+static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_core, double r_lno, int k_lno,
+                               double kappa, double s_fna) {
+    const bool rule = kappa >= 0.0;
     DCLNO_CUDA(c, cudaSetDevice(c->device));
     free_clusters(c);
+    const bool pao_only = k_lno == 0 || (!rule && r_lno <= r_core);  // plain PAO DC: no LNO region
 
     const int N = sys->natoms;
     c->N = N;
@@ -268,8 +327,14 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
             if (j == i && s0 == 0 && s1 == 0 && s2 == 0) onsite[i] = b;
         }
         if (onsite[i] < 0) return set_err(c, DCLNO_ERR_ARG, "missing on-site block of atom " + std::to_string(i));
-        if (r_lno > r_core && k_lno > 0 && (k_lno > c->norb[i] || c->norb[i] > DCLNO_MAX_M_LNO))
+        if (!pao_only && (k_lno > c->norb[i] || c->norb[i] > DCLNO_MAX_M_LNO))
             return set_err(c, DCLNO_ERR_ARG, "atom " + std::to_string(i) + ": LNOs need k_lno <= M_i <= 16");
+    }
+
+    std::vector<double> bmax;
+    if (rule) {
+        const dclno_status st = block_absmax(c, sys->S, bmax);
+        if (st != DCLNO_OK) return st;
     }
 
     // ---- clusters: membership by distance, order by distance descending (centre last)
@@ -303,6 +368,21 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
         });
         if (cand.empty() || cand.back().atom != i || cand.back().s0 || cand.back().s1 || cand.back().s2)
             return set_err(c, DCLNO_ERR_ARG, "cluster of atom " + std::to_string(i) + " does not end with its centre");
+        double r_short = r_core;
+        if (rule && !pao_only) {
+            // first neighbouring atoms: stored overlap block with the centre above s_fna
+            std::vector<double> dd(cand.size());
+            std::vector<char> fna(cand.size());
+            const auto kb = key.begin() + c->row_ptr[i], ke = key.begin() + c->row_ptr[i + 1];
+            for (size_t m = 0; m < cand.size(); ++m) {
+                const Cand& u = cand[cand.size() - 1 - m];  // ascending distance
+                dd[m] = u.d;
+                const long long want = block_key(u.atom, pack_shift(u.s0, u.s1, u.s2));
+                const auto it = std::lower_bound(kb, ke, want);
+                fna[m] = (it != ke && *it == want && bmax[it - key.begin()] > s_fna) ? 1 : 0;
+            }
+            r_short = kappa_radius(dd, fna, kappa, tol);
+        }
         ClusterDesc& d = c->cl[i];
         d.centre = i;
         d.nmem = (int)cand.size();
@@ -312,8 +392,8 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
         keys.reserve(cand.size());
         for (size_t m = 0; m < cand.size(); ++m) {
             const Cand& u = cand[m];
-            int core = (u.d <= r_core + tol) ? 1 : 0;
-            if (r_lno <= r_core || k_lno == 0) core = 1;  // plain PAO DC: no LNO region
+            int core = (u.d <= r_short + tol) ? 1 : 0;
+            if (pao_only) core = 1;
             if (!core) c->has_lno_region = true;
             MemberDesc md;
             md.atom = u.atom;
@@ -523,6 +603,35 @@ extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* s
     c->built = true;
     c->lnos_ready = !c->has_lno_region;
     return DCLNO_OK;
+}
+
+static dclno_status check_system(dclno_ctx* c, const dclno_system* sys, const char* who) {
+    if (!sys || sys->natoms <= 0 || !sys->pos || !sys->cell || !sys->pbc || !sys->norb || !sys->row_ptr ||
+        !sys->col || !sys->shift || !sys->blk_off || !sys->H || !sys->S)
+        return set_err(c, DCLNO_ERR_ARG, std::string(who) + ": null or empty system");
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_build_clusters(dclno_ctx* c, const dclno_system* sys, double r_core,
+                                             double r_lno, int k_lno) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    dclno_status st = check_system(c, sys, "dclno_build_clusters");
+    if (st != DCLNO_OK) return st;
+    if (!(r_core >= 0.0) || !(r_lno >= r_core) || k_lno < 0)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters: need 0 <= r_core <= r_lno and k_lno >= 0");
+    return build_impl(c, sys, r_core, r_lno, k_lno, -1.0, 0.0);
+}
+
+extern "C" dclno_status dclno_build_clusters_kappa(dclno_ctx* c, const dclno_system* sys, double r_lno, int k_lno,
+                                                   double kappa, double s_fna) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    dclno_status st = check_system(c, sys, "dclno_build_clusters_kappa");
+    if (st != DCLNO_OK) return st;
+    if (!(r_lno >= 0.0) || k_lno < 0 || !(kappa >= 0.0 && kappa <= 1.0) || !(s_fna >= 0.0))
+        return set_err(c, DCLNO_ERR_ARG, "dclno_build_clusters_kappa: need r_lno >= 0, k_lno >= 0, 0 <= kappa <= 1, s_fna >= 0");
+    return build_impl(c, sys, 0.0, r_lno, k_lno, kappa, s_fna);
 }
 
 extern "C" dclno_status dclno_compute_lnos(dclno_ctx* c, const double* rho) {

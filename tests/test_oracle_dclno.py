@@ -204,3 +204,40 @@ def test_energy_density_matrix(cfg1, cfg1_exact, lno_step):
         return D
 
     np.testing.assert_allclose(S @ dense(ed), H @ dense(rho_f), rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Region rule of Sec. III (kappa buffer): worked example on a simple-cubic lattice
+# ---------------------------------------------------------------------------
+def test_kappa_region_rule_worked_example():
+    """Periodic 8^3 SC lattice, spacing 1, one Gaussian (exponent 1) per atom, so the
+    overlap of two atoms at distance d is exp(-d^2/2).  r_L = 2.5 holds the shells
+    d^2 = 0, 1, 2, 3, 4, 5, 6 with 1, 6, 12, 8, 6, 24, 24 atoms (81).  With the
+    first neighbours taken as overlaps above 0.3 (d^2 <= 2: e^-1 = 0.37 > 0.3 >
+    e^-1.5 = 0.22): N_F = 19, N_S = 62, N_F + 3/10 N_S = 37.6.  Spheres hold
+    1, 7, 19, 27, 33, 57, 81 atoms; the closest is 33 (d^2 <= 4), so the short-range
+    region has 33 atoms and the long-range region 48."""
+    import tbsystems as T
+    s = T.small_lattice(8, 8, 8, a=1.0, exps=(1.0,), onsite=(0.0,), e_per_atom=1.0, r_core=1.0, r_lno=2.5,
+                        k_lno=1, periodic=True)
+    for i in (0, 137, 511):
+        cl = O.cluster_members(s, i, 0.0, 2.5, 1, kappa=0.3, s_fna=0.3)
+        assert len(cl.atoms) == 81
+        assert int(np.count_nonzero(cl.core)) == 33
+        assert np.max(cl.dist[cl.core]) == pytest.approx(2.0)
+        assert np.min(cl.dist[~cl.core]) == pytest.approx(np.sqrt(5.0))
+    # kappa = 0: the short-range region is the first neighbours (19); kappa = 1: all 81
+    assert int(np.count_nonzero(O.cluster_members(s, 0, 0.0, 2.5, 1, kappa=0.0, s_fna=0.3).core)) == 19
+    assert int(np.count_nonzero(O.cluster_members(s, 0, 0.0, 2.5, 1, kappa=1.0, s_fna=0.3).core)) == 81
+    # the literal "non-zero overlap" (any stored block): every atom within r_L overlaps
+    assert int(np.count_nonzero(O.cluster_members(s, 0, 0.0, 2.5, 1, kappa=0.3, s_fna=0.0).core)) == 81
+
+
+def test_kappa_radius_ties_go_to_the_larger_sphere():
+    # shells of 1, 3, 3 atoms; N_F = 1, N_S = 6, kappa = 0.5 -> target 4: spheres 1, 4, 7 -> 4;
+    # kappa = 1/3 -> target 3: |1-3| = 2 > |4-3| = 1 -> 4; target 5.5 (kappa 0.75): |4-5.5| = |7-5.5| -> 7
+    d = np.array([0.0, 1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
+    fna = np.array([True, False, False, False, False, False, False])
+    assert O.kappa_radius(d, fna, 0.5) == 1.0
+    assert O.kappa_radius(d, fna, 1.0 / 3.0) == 1.0
+    assert O.kappa_radius(d, fna, 0.75) == 2.0
