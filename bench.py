@@ -49,8 +49,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
-    p.add_argument("--workload", choices=["rocksalt1728", "small64"], default="rocksalt1728",
-                   help="small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels")
+    p.add_argument("--workload", choices=["rocksalt1728", "small64", "amorphous32000"], default="rocksalt1728",
+                   help="small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels; "
+                        "amorphous32000: the 32,000-atom random packing, generated row range by row range "
+                        "into device memory and solved through memory-admitted batches")
+    p.add_argument("--atoms", type=int, default=32000, help="atoms of the amorphous workload (same density)")
     return p.parse_args()
 
 
@@ -252,6 +255,113 @@ def measure_scf(world):
 
 
 # ---------------------------------------------------------------------------
+# the 32,000-atom amorphous workload, streamed
+# ---------------------------------------------------------------------------
+AMORPHOUS = ("DC-LNO step, {n}-atom amorphous two-species packing (random sequential addition at 0.012 "
+             "atoms/bohr^3, d_min 3.8 bohr, periodic cube), 13 s-Gaussians/atom, r_core=6, r_lno=10 bohr, "
+             "4 LNOs/atom, kT=0.01 Ha, memory-admitted batches")
+
+
+def run_streamed(args):
+    """One LNO step of the amorphous workload in FP64 and in mixed precision: S, H
+    and the input density are generated row range by row range straight into
+    device memory (the host never holds them), the context admits the cluster
+    workspace in batches; invariants on the device and sampled clusters against
+    the oracle (host blocks computed only for the rows those clusters touch)."""
+    import numpy as np
+    import torch
+
+    import tbsystems as T
+    from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context
+
+    t0 = time.perf_counter()
+    s = T.make_system_streamed(5, n_atoms=args.atoms)
+    t_struct = time.perf_counter() - t0
+    nval = len(s.S)
+    dev = torch.device("cuda", 0)
+    H = torch.empty(nval, dtype=torch.float64, device=dev)
+    S = torch.empty_like(H)
+    R = torch.empty_like(H)
+    for i0 in range(0, s.natoms, 512):
+        i1 = min(s.natoms, i0 + 512)
+        o0, sv, hv = T.row_values(s, i0, i1)
+        S[o0:o0 + len(sv)].copy_(torch.from_numpy(sv))
+        H[o0:o0 + len(hv)].copy_(torch.from_numpy(hv))
+        buf = np.empty(len(sv))
+        T.synthetic_density_rows(s, i0, i1, buf, seed=11, base=o0)
+        R[o0:o0 + len(buf)].copy_(torch.from_numpy(buf))
+    torch.cuda.synchronize()
+    t_fill = time.perf_counter() - t0 - t_struct
+    out = torch.zeros_like(H)
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context(stream=stream.cuda_stream)
+    ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
+                       s.r_core, s.r_lno, s.k_lno)
+    nb, ws = ctx.batch_info()
+    dims = ctx.cluster_info()[0]
+    res = {}
+    for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
+        ctx.step(R, out, s.n_electrons, s.kT, precision=prec)  # warm-up (tunes the QL launch shape)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mu, n, eb = ctx.step(R, out, s.n_electrons, s.kT, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": s.natoms / (ms / 1e3), "unit": "clusters/s", "ms_per_step": ms, "mu": mu,
+                     "n_electrons": n, "e_band": eb,
+                     "trace_rho_s_minus_n": abs(2.0 * float(torch.dot(out, S)) - n) / s.n_electrons,
+                     "trace_rho_h_minus_eband": abs(2.0 * float(torch.dot(out, H)) - eb) / abs(eb)}
+    # sampled clusters against the oracle (FP64 path, fixed mu)
+    import oracle as O
+
+    mu_fix = res["fp64"]["mu"]
+    ctx.step(R, out, s.n_electrons, s.kT, precision=DCLNO_FP64)
+    ctx.density_matrix(mu_fix, s.kT, out)
+    spec = ctx.spectrum()
+    sample = [0, s.natoms // 2]
+    cls = {i: O.cluster_members(s, i, s.r_core, s.r_lno, s.k_lno) for i in sample}
+    rows_needed = set()
+    for cl in cls.values():
+        rows_needed |= {int(a) for a in cl.atoms}
+    T.fill_rows(s, rows_needed)
+    rho_host = np.zeros(nval)  # untouched pages stay unallocated
+    for i in rows_needed:
+        T.synthetic_density_rows(s, i, i + 1, rho_host, seed=11)
+    need = set()
+    for cl in cls.values():
+        need |= {int(a) for a, c in zip(cl.atoms, cl.core) if not c}
+    lno = O.compute_lnos(s, rho_host, s.k_lno, atoms=sorted(need))
+    V = {j: v[0] for j, v in lno.items()}
+    ores = O.dclno_solve(s, V, s.r_core, s.r_lno, s.k_lno, atoms=sample, threads=len(sample))
+    out_rows = np.zeros(nval)
+    deps, deps_b, drho = 0.0, 0.0, 0.0
+    for i, r in ores.items():
+        d = np.abs(np.sort(spec[i][0]) - r.eps)
+        # first-order bound of a backward error n u in H^(i), S^(i) (c^T S c = 1)
+        bound = 1e-10 + 2.0 * len(r.eps) * 2.0 ** -53 * (r.h_norm + np.abs(r.eps) * r.s_norm) * np.einsum(
+            "am,am->m", r.C, r.C)
+        deps = max(deps, float(np.max(d)))
+        deps_b = max(deps_b, float(np.max(d / bound)))
+        O.density_rows(s, r.cluster, r.eps, r.C, V, mu_fix, s.kT, out_rows)
+        o0, o1 = int(s.blk_off[s.row_ptr[i]]), int(s.blk_off[s.row_ptr[i + 1]])
+        g = out[o0:o1].cpu().numpy()
+        drho = max(drho, float(np.max(np.abs(g - out_rows[o0:o1])) / np.max(np.abs(out_rows[o0:o1]))))
+    ctx.close()
+    line = {"workload": AMORPHOUS.format(n=s.natoms), "clusters": s.natoms, "cluster_dim_min": int(dims.min()),
+            "cluster_dim_max": int(dims.max()), "stored_blocks": int(len(s.col)), "matrix_gb": nval * 8 / 1e9,
+            "batches": nb, "workspace_gb": ws / 1e9, "host_structure_s": t_struct, "fill_s": t_fill,
+            "fp64": res["fp64"], "mixed": res["mixed"],
+            "e_band_diff_per_atom_mixed_vs_fp64": abs(res["mixed"]["e_band"] - res["fp64"]["e_band"]) / s.natoms,
+            "oracle_sample": {"clusters": sample, "max_abs_eps_diff": deps,
+                              "max_eps_diff_over_first_order_bound": deps_b, "max_rho_row_diff_rel_to_row_max": drho,
+                              "mu": mu_fix}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -411,6 +521,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "amorphous32000":
+        return run_streamed(args)
     return run_ours(args)
 
 

@@ -65,6 +65,7 @@ class System:
     r_core: float
     r_lno: float
     k_lno: int
+    source: object = None    # BsrRows of a system whose S, H are filled on demand (make_system_streamed)
 
     @property
     def natoms(self) -> int:
@@ -125,31 +126,36 @@ def _image_shifts(cell: np.ndarray, pbc: np.ndarray, rcut: float) -> np.ndarray:
     return g.astype(np.int64)
 
 
-def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
-    """Block-sparse S and H over all (i, j, R) pairs with a kept overlap entry."""
-    from scipy.spatial import cKDTree
+class BsrRows:
+    """Rows of the block-sparse S and H on demand: (i, j, R) pairs with a kept
+    overlap entry, Wolfsberg-Helmholz H.  One KD-tree over the periodic images."""
 
-    n = pos.shape[0]
-    norb = np.array([len(e) for e in exps], dtype=np.int32)
-    min_exp = min(float(np.min(e)) for e in exps)
-    rcut = overlap_cutoff(min_exp, drop_tol)
-    shifts = _image_shifts(cell, pbc, rcut)
-    imgpos = (pos[None, :, :] + (shifts @ cell)[:, None, :]).reshape(-1, 3)
-    tree = cKDTree(imgpos)
-    uniform = bool(np.all(norb == norb[0]))
+    def __init__(self, pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
+        from scipy.spatial import cKDTree
 
-    rows_col, rows_shift, rows_S, rows_H, rows_n = [], [], [], [], []
-    for i0 in range(0, n, 256):
-        i1 = min(n, i0 + 256)
-        lists = tree.query_ball_point(pos[i0:i1], rcut * (1 + 1e-12) + 1e-9)
+        self.pos, self.exps, self.onsite, self.drop_tol = pos, exps, onsite, drop_tol
+        self.n = pos.shape[0]
+        self.norb = np.array([len(e) for e in exps], dtype=np.int32)
+        min_exp = min(float(np.min(e)) for e in exps)
+        self.rcut = overlap_cutoff(min_exp, drop_tol)
+        self.shifts = _image_shifts(cell, pbc, self.rcut)
+        self.imgpos = (pos[None, :, :] + (self.shifts @ cell)[:, None, :]).reshape(-1, 3)
+        self.tree = cKDTree(self.imgpos)
+        self.uniform = bool(np.all(self.norb == self.norb[0]))
+
+    def rows(self, i0, i1):
+        """[(col, shift, S, H)] of rows i0 .. i1-1, blocks sorted by (col, shift)."""
+        n, pos, exps, onsite, drop_tol = self.n, self.pos, self.exps, self.onsite, self.drop_tol
+        out = []
+        lists = self.tree.query_ball_point(pos[i0:i1], self.rcut * (1 + 1e-12) + 1e-9)
         for ii, lst in enumerate(lists):
             i = i0 + ii
             idx = np.asarray(sorted(lst), dtype=np.int64)
             j = idx % n
-            sh = shifts[idx // n]
-            d = imgpos[idx] - pos[i]
+            sh = self.shifts[idx // n]
+            d = self.imgpos[idx] - pos[i]
             r2 = np.einsum("kd,kd->k", d, d)
-            if uniform:
+            if self.uniform:
                 a = exps[i][None, :, None]
                 b = np.stack([exps[jj] for jj in j])[:, None, :]
                 sblk = gaussian_overlap(a, b, r2[:, None, None])
@@ -162,11 +168,8 @@ def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
                 keep = np.any(sblk != 0.0, axis=(1, 2))
                 order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], j))
                 order = order[keep[order]]
-                rows_col.append(j[order].astype(np.int32))
-                rows_shift.append(sh[order].astype(np.int8))
-                rows_S.append(sblk[order].reshape(-1))
-                rows_H.append(hblk[order].reshape(-1))
-                rows_n.append(len(order))
+                out.append((j[order].astype(np.int32), sh[order].astype(np.int8), sblk[order].reshape(-1),
+                            hblk[order].reshape(-1)))
             else:  # ragged basis: per-block loop
                 blocks = []
                 for k in range(len(idx)):
@@ -181,23 +184,47 @@ def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
                     hb = kf * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
                     blocks.append((jj, tuple(int(x) for x in sh[k]), sb, hb))
                 blocks.sort(key=lambda t: (t[0],) + t[1])
-                rows_col.append(np.array([t[0] for t in blocks], dtype=np.int32))
-                rows_shift.append(np.array([t[1] for t in blocks], dtype=np.int8).reshape(-1, 3))
-                rows_S.append(np.concatenate([t[2].reshape(-1) for t in blocks]))
-                rows_H.append(np.concatenate([t[3].reshape(-1) for t in blocks]))
-                rows_n.append(len(blocks))
+                out.append((np.array([t[0] for t in blocks], dtype=np.int32),
+                            np.array([t[1] for t in blocks], dtype=np.int8).reshape(-1, 3),
+                            np.concatenate([t[2].reshape(-1) for t in blocks]),
+                            np.concatenate([t[3].reshape(-1) for t in blocks])))
+        return out
 
+    def structure(self, chunk=256):
+        """row_ptr, col, shift, blk_off of all rows (the values are not kept)."""
+        cols, shs, ns = [], [], []
+        for i0 in range(0, self.n, chunk):
+            for c, sh, _, _ in self.rows(i0, min(self.n, i0 + chunk)):
+                cols.append(c)
+                shs.append(sh)
+                ns.append(len(c))
+        return _layout(self.norb, ns, cols, shs)
+
+
+def _layout(norb, ns, cols, shs):
+    n = len(ns)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    row_ptr[1:] = np.cumsum(rows_n)
-    col = np.concatenate(rows_col)
-    shift = np.concatenate(rows_shift).reshape(-1, 3)
-    brow = np.repeat(np.arange(n), rows_n)
+    row_ptr[1:] = np.cumsum(ns)
+    col = np.concatenate(cols)
+    shift = np.concatenate(shs).reshape(-1, 3)
+    brow = np.repeat(np.arange(n), ns)
     sizes = norb[brow].astype(np.int64) * norb[col].astype(np.int64)
     blk_off = np.zeros(len(col), dtype=np.int64)
     blk_off[1:] = np.cumsum(sizes)[:-1]
-    S = np.concatenate(rows_S)
-    H = np.concatenate(rows_H)
-    return norb, row_ptr, col, shift, blk_off, S, H
+    return row_ptr, col, shift, blk_off
+
+
+def build_bsr(pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
+    """Block-sparse S and H over all (i, j, R) pairs with a kept overlap entry."""
+    b = BsrRows(pos, cell, pbc, exps, onsite, drop_tol)
+    rows = []
+    for i0 in range(0, b.n, 256):
+        rows += b.rows(i0, min(b.n, i0 + 256))
+    row_ptr, col, shift, blk_off = _layout(b.norb, [len(r[0]) for r in rows], [r[0] for r in rows],
+                                           [r[1] for r in rows])
+    S = np.concatenate([r[2] for r in rows])
+    H = np.concatenate([r[3] for r in rows])
+    return b.norb, row_ptr, col, shift, blk_off, S, H
 
 
 # --------------------------------------------------------------------------
@@ -210,7 +237,48 @@ def _sc_lattice(nx, ny, nz, a):
 
 
 def make_system(cfg: int, seed: int | None = None, n_atoms: int | None = None, **over) -> System:
-    """One of the five workloads; keyword overrides replace r_core, r_lno, k_lno.
+    """One of the five workloads (see workload_spec)."""
+    return assemble_system(**workload_spec(cfg, seed, n_atoms, **over))
+
+
+def make_system_streamed(cfg: int, seed: int | None = None, n_atoms: int | None = None, **over) -> System:
+    """A workload's geometry and BSR structure with S and H not computed: both are
+    full-length zero arrays (the operating system backs untouched pages lazily),
+    ``source`` produces the blocks of any row range (BsrRows.rows) and fill_rows
+    writes chosen rows.  For systems whose matrices do not fit host memory."""
+    sp = workload_spec(cfg, seed, n_atoms, **over)
+    pos = np.ascontiguousarray(sp["pos"], dtype=np.float64)
+    exps = [np.asarray(e, dtype=np.float64) for e in sp["exps"]]
+    onsite = [np.asarray(h, dtype=np.float64) for h in sp["onsite"]]
+    src = BsrRows(pos, np.asarray(sp["cell"], dtype=np.float64), np.asarray(sp["pbc"], dtype=bool), exps, onsite)
+    row_ptr, col, shift, blk_off = src.structure()
+    last = len(col) - 1
+    nval = int(blk_off[last] + src.norb[np.searchsorted(row_ptr, last, side="right") - 1] * src.norb[col[last]])
+    return System(name=sp["name"], pos=pos, cell=np.asarray(sp["cell"], dtype=np.float64),
+                  pbc=np.asarray(sp["pbc"], dtype=bool), species=np.asarray(sp["species"], np.int32), exps=exps,
+                  onsite=onsite, norb=src.norb, row_ptr=row_ptr, col=col, shift=shift, blk_off=blk_off,
+                  S=np.zeros(nval), H=np.zeros(nval), n_electrons=float(sp["n_electrons"]), kT=float(sp["kT"]),
+                  r_core=float(sp["r_core"]), r_lno=float(sp["r_lno"]), k_lno=int(sp["k_lno"]), source=src)
+
+
+def row_values(system: System, i0: int, i1: int):
+    """(offset, S, H) of the blocks of rows i0 .. i1-1 of a streamed system."""
+    rows = system.source.rows(i0, i1)
+    o0 = int(system.blk_off[system.row_ptr[i0]])
+    return o0, np.concatenate([r[2] for r in rows]), np.concatenate([r[3] for r in rows])
+
+
+def fill_rows(system: System, atoms) -> None:
+    """Compute the S and H blocks of the given rows of a streamed system in place."""
+    for i in sorted(set(int(a) for a in atoms)):
+        o0, sv, hv = row_values(system, i, i + 1)
+        system.S[o0:o0 + len(sv)] = sv
+        system.H[o0:o0 + len(hv)] = hv
+
+
+def workload_spec(cfg: int, seed: int | None = None, n_atoms: int | None = None, **over) -> dict:
+    """Geometry, basis and parameters of one of the five workloads; keyword
+    overrides replace r_core, r_lno, k_lno.
     n_atoms (workload 5 only) packs fewer atoms at the same density (a smaller cube).
 
     1  64-atom simple-cubic 4x4x4, a=2.5, open, 4 s-Gaussians, 2 e/atom.
@@ -277,7 +345,7 @@ def make_system(cfg: int, seed: int | None = None, n_atoms: int | None = None, *
     else:
         raise ValueError(f"unknown workload {cfg}")
     sys.update(over)
-    return assemble_system(**sys)
+    return sys
 
 
 def assemble_system(name, pos, cell, pbc, species, exps, onsite, n_electrons, kT,
@@ -371,18 +439,28 @@ def synthetic_density(system: System, seed: int = 11, width: float = 3.0) -> np.
     Symmetry rho_{0i,Rj} = rho_{0j,-Ri}^T holds by construction.  Only the
     pattern and the geometry are read from ``system``.
     """
+    rho = np.zeros_like(system.S)
+    synthetic_density_rows(system, 0, system.natoms, rho, seed, width)
+    return rho
+
+
+def synthetic_density_rows(system: System, i0: int, i1: int, out: np.ndarray, seed: int = 11,
+                           width: float = 3.0, base: int = 0) -> None:
+    """The blocks of rows i0 .. i1-1 of synthetic_density, written to out[blk_off - base]."""
     rng = np.random.default_rng(seed)
     n = system.natoms
     scale = rng.uniform(0.9, 1.1, size=n)
-    brow = system.block_rows()
-    col = system.col.astype(np.int64)
-    d = system.pos[col] + system.shift.astype(np.float64) @ system.cell - system.pos[brow]
+    b0, b1 = int(system.row_ptr[i0]), int(system.row_ptr[i1])
+    brow = np.repeat(np.arange(i0, i1), np.diff(system.row_ptr[i0:i1 + 1]))
+    col = system.col[b0:b1].astype(np.int64)
+    shift = system.shift[b0:b1]
+    d = system.pos[col] + shift.astype(np.float64) @ system.cell - system.pos[brow]
     r2 = np.einsum("kd,kd->k", d, d)
-    onsite = (brow == col) & ~np.any(system.shift != 0, axis=1)
+    onsite = (brow == col) & ~np.any(shift != 0, axis=1)
     amp = 0.05 * np.exp(-r2 / (width * width)) * np.sqrt(scale[brow] * scale[col])
-    rho = np.zeros_like(system.S)
     mi_all = system.norb[brow].astype(np.int64)
     mj_all = system.norb[col].astype(np.int64)
+    offs = system.blk_off[b0:b1] - base
     for mi in np.unique(mi_all):
         for mj in np.unique(mj_all):
             sel = np.nonzero((mi_all == mi) & (mj_all == mj))[0]
@@ -395,6 +473,5 @@ def synthetic_density(system: System, seed: int = 11, width: float = 3.0) -> np.
             if np.any(ons):
                 p = 0.9 * np.exp(-0.6 * np.arange(mi))
                 blocks[ons] = np.diag(p)[None, :, :] * scale[brow[sel[ons]], None, None]
-            idx = system.blk_off[sel][:, None] + np.arange(mi * mj)[None, :]
-            rho[idx] = blocks.reshape(len(sel), -1)
-    return rho
+            idx = offs[sel][:, None] + np.arange(mi * mj)[None, :]
+            out[idx] = blocks.reshape(len(sel), -1)

@@ -102,3 +102,25 @@ def test_synthetic_density_symmetric(mixed_system):
         i, j = int(brow[b]), int(s.col[b])
         mb = key[(j, i) + tuple(-int(x) for x in s.shift[b])]
         np.testing.assert_allclose(s.block(rho, b), s.block(rho, mb).T, rtol=1e-15, atol=0)
+
+
+def test_streamed_rows_equal_full_build():
+    """Row-range generation (for systems whose matrices exceed host memory) gives the
+    same structure, S, H and synthetic density as the one-shot build."""
+    a = T.make_system(5, n_atoms=300)
+    b = T.make_system_streamed(5, n_atoms=300)
+    for k in ("row_ptr", "col", "shift", "blk_off"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    assert len(a.S) == len(b.S) and not np.any(b.S)
+    for i0, i1 in ((0, 1), (17, 120), (290, 300)):
+        o0, sv, hv = T.row_values(b, i0, i1)
+        assert np.array_equal(sv, a.S[o0:o0 + len(sv)]) and np.array_equal(hv, a.H[o0:o0 + len(hv)])
+    rho = T.synthetic_density(a, seed=11)
+    o0, o1 = int(b.blk_off[b.row_ptr[40]]), int(b.blk_off[b.row_ptr[90]])
+    part = np.zeros(o1 - o0)
+    T.synthetic_density_rows(b, 40, 90, part, seed=11, base=o0)
+    assert np.array_equal(part, rho[o0:o1])
+    T.fill_rows(b, [3, 250])
+    for i in (3, 250):
+        o, e = int(b.blk_off[b.row_ptr[i]]), int(b.blk_off[b.row_ptr[i + 1]])
+        assert np.array_equal(b.S[o:e], a.S[o:e]) and np.array_equal(b.H[o:e], a.H[o:e])
