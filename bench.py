@@ -274,6 +274,9 @@ def run_streamed(args):
     import tbsystems as T
     from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context
 
+    def ddot(a, b, chunk=1 << 30):  # cuBLAS dot takes at most 2^31 - 1 elements
+        return sum(float(torch.dot(a[k:k + chunk], b[k:k + chunk])) for k in range(0, a.numel(), chunk))
+
     t0 = time.perf_counter()
     s = T.make_system_streamed(5, n_atoms=args.atoms)
     t_struct = time.perf_counter() - t0
@@ -311,8 +314,8 @@ def run_streamed(args):
         ms = e0.elapsed_time(e1)
         res[name] = {"value": s.natoms / (ms / 1e3), "unit": "clusters/s", "ms_per_step": ms, "mu": mu,
                      "n_electrons": n, "e_band": eb,
-                     "trace_rho_s_minus_n": abs(2.0 * float(torch.dot(out, S)) - n) / s.n_electrons,
-                     "trace_rho_h_minus_eband": abs(2.0 * float(torch.dot(out, H)) - eb) / abs(eb)}
+                     "trace_rho_s_minus_n": abs(2.0 * ddot(out, S) - n) / s.n_electrons,
+                     "trace_rho_h_minus_eband": abs(2.0 * ddot(out, H) - eb) / abs(eb)}
     # sampled clusters against the oracle (FP64 path, fixed mu)
     import oracle as O
 
