@@ -302,6 +302,8 @@ def run_streamed(args):
                        s.r_core, s.r_lno, s.k_lno)
     nb, ws = ctx.batch_info()
     dims = ctx.cluster_info()[0]
+    print(f"structure {t_struct:.0f} s, device fill {t_fill:.0f} s, {nb} batches of <= {ws / 1e9:.1f} GB",
+          file=sys.stderr, flush=True)
     res = {}
     for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
         ctx.step(R, out, s.n_electrons, s.kT, precision=prec)  # warm-up (tunes the QL launch shape)
