@@ -185,6 +185,22 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
 dclno_status dclno_get_tuning(dclno_ctx *ctx, int batch, int *ql_lanes_out, float *candidate_ms);
 
 /*
+ * Threshold selection of LNOs (Sec. II.B step (iii)): with on != 0, the next
+ * dclno_compute_lnos keeps for each atom the eigenvectors of Lambda whose
+ * eigenvalue has a real part >= lambda_th (the paper uses 0.1), at most the
+ * k_lno given to dclno_build_clusters (a conjugate pair qualifies as a whole; the
+ * cap may split it, as for a fixed count).  Each LNO-region member then carries its
+ * own count, so the cluster dimensions change with every LNO computation: the
+ * call re-derives them on the host (one synchronisation, no reallocation: the
+ * workspace stays laid out for k_lno).  With on = 0 every atom keeps k_lno.
+ * dclno_scf_run refuses threshold mode (its steps are captured without host
+ * work); loop over dclno_step instead.  dclno_get_lno_counts (host, [N])
+ * returns the counts of the last LNO computation (k_lno before any).
+ */
+dclno_status dclno_set_lno_threshold(dclno_ctx *ctx, int on, double lambda_th);
+dclno_status dclno_get_lno_counts(dclno_ctx *ctx, int *counts);
+
+/*
  * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
  * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
  * implicit QL on the tridiagonal matrix, and the central-atom rows of the

@@ -194,7 +194,7 @@ def _overlaps_centre(system, i, atoms, shifts, s_fna):
 
 
 def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int, kappa: float | None = None,
-                    s_fna: float = 0.0) -> Cluster:
+                    s_fna: float = 0.0, k_atoms=None) -> Cluster:
     """Members of the truncated cluster of atom i.
 
     Core (PAO) region: images (j, R) with |tau_j + R - tau_i| <= r_core;
@@ -203,7 +203,8 @@ def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int, kap
     Sec. III (kappa_radius), first neighbouring atoms being those whose stored
     overlap block with the centre exceeds s_fna in magnitude.
     Member order: distance descending, ties by (j, R), so the central atom
-    is last.  Core members contribute M_j basis functions, LNO members k_lno.
+    is last.  Core members contribute M_j basis functions, LNO members k_lno,
+    or k_atoms[j] when the LNO count differs per atom (threshold selection).
     """
     shifts = _shift_range(system, r_lno)
     img = (system.pos[None, :, :] + (shifts @ system.cell)[:, None, :])  # (nS, N, 3)
@@ -222,7 +223,8 @@ def cluster_members(system, i: int, r_core: float, r_lno: float, k_lno: int, kap
     core = dist <= r_core + MEMBER_TOL
     # the central atom itself (d = 0) must be the last member
     assert atoms[-1] == i and not np.any(sh[-1]), "central atom is not last"
-    sizes = np.where(core, system.norb[atoms], k_lno).astype(np.int64)
+    klno = np.full(len(atoms), k_lno) if k_atoms is None else np.array([int(k_atoms[int(j)]) for j in atoms])
+    sizes = np.where(core, system.norb[atoms], klno).astype(np.int64)
     offsets = np.zeros(len(atoms) + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
     return Cluster(i, atoms, sh, core, dist, offsets)
@@ -287,8 +289,12 @@ LNO_COMPLEX_SELECTED = 1   # a selected eigenvalue is complex
 LNO_PAIR_SPLIT = 2         # a complex pair straddles the cut; its real part was kept
 
 
-def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int):
+def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int, lambda_th: float | None = None):
     """LNOs of one atom from its Lambda block.
+
+    With lambda_th given (Sec. II.B step (iii)), only eigenvalues whose real part
+    is at least lambda_th are selected, at most k of them (a conjugate pair has one
+    real part, so both members qualify together).
 
     Eigenvalues by Hessenberg + Francis QR, sorted by real part descending
     (ties: positive imaginary part first).  The eigenvectors of the leading k
@@ -314,6 +320,8 @@ def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int):
     pos = 0
     while len(vecs) < k and pos < m:
         t = order[pos]
+        if lambda_th is not None and wr[t] < lambda_th:
+            break
         if wi[t] == 0.0:
             vecs.append(inverse_iter(lam, wr[t], 0.0).real)
             pos += 1
@@ -326,7 +334,7 @@ def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int):
         else:
             flags |= LNO_PAIR_SPLIT
         pos += 2  # skip the conjugate partner
-    V = np.column_stack(vecs[:k]) if k > 0 else np.zeros((m, 0))
+    V = np.column_stack(vecs[:k]) if vecs else np.zeros((m, 0))
     for _ in range(2):
         for c in range(V.shape[1]):
             v = V[:, c].copy()
@@ -340,10 +348,12 @@ def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int):
     return V, ev, flags
 
 
-def compute_lnos(system, rho: np.ndarray, k: int, atoms=None) -> dict:
-    """atom -> (V, eigenvalues, flags) for the given atoms (default: all)."""
+def compute_lnos(system, rho: np.ndarray, k: int, atoms=None, lambda_th: float | None = None) -> dict:
+    """atom -> (V, eigenvalues, flags) for the given atoms (default: all); with
+    lambda_th, each atom keeps the eigenvectors whose eigenvalue is >= lambda_th
+    (at most k), so V has that atom's own number of columns."""
     lam = lambda_blocks(system, rho, atoms)
-    return {i: lnos(L, _on_site_block(system, i), k) for i, L in lam.items()}
+    return {i: lnos(L, _on_site_block(system, i), k, lambda_th) for i, L in lam.items()}
 
 
 # --------------------------------------------------------------------------
@@ -511,17 +521,19 @@ def _threads():
 
 
 def dclno_solve(system, V: dict, r_core: float, r_lno: float, k_lno: int, atoms=None,
-                threads: int | None = None, kappa: float | None = None, s_fna: float = 0.0) -> dict:
+                threads: int | None = None, kappa: float | None = None, s_fna: float = 0.0,
+                k_atoms=None) -> dict:
     """Clusters, assembly and eigen-solve for the given atoms (default all).
 
     Returns atom -> ClusterResult.  ``V`` must hold the LNOs of every atom that
     appears in an LNO region (unused when r_lno == r_core).  kappa, s_fna: the
-    region rule of Sec. III instead of the fixed r_core (see cluster_members).
+    region rule of Sec. III instead of the fixed r_core (see cluster_members);
+    k_atoms: per-atom LNO counts (threshold selection; default k_lno for all).
     """
     if atoms is None:
         atoms = list(range(system.natoms))
     bidx = _BlockIndex(system)
-    clusters = [cluster_members(system, i, r_core, r_lno, k_lno, kappa, s_fna) for i in atoms]
+    clusters = [cluster_members(system, i, r_core, r_lno, k_lno, kappa, s_fna, k_atoms) for i in atoms]
     for cl in clusters:  # warm the per-row lookup tables outside the threads
         for j in set(int(a) for a in cl.atoms):
             bidx.row(j)

@@ -20,7 +20,8 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_get_spectrum", "dclno_get_lnos", "dclno_launch_count", "dclno_set_profiling",
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
-           "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa"]
+           "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
+           "dclno_get_lno_counts"]
 
 
 class DclnoError(RuntimeError):
@@ -85,6 +86,8 @@ def load_library():
         "dclno_set_autotune": ([P, I], I),
         "dclno_get_tuning": ([P, I, P, P], I),
         "dclno_build_clusters_kappa": ([P, ctypes.POINTER(dclno_system), D, I, D, D], I),
+        "dclno_set_lno_threshold": ([P, I, D], I),
+        "dclno_get_lno_counts": ([P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -180,6 +183,17 @@ class Context:
         self._check(self.lib.dclno_batch_info(self.h, ctypes.cast(ctypes.byref(nb), ctypes.c_void_p),
                                               ctypes.cast(ctypes.byref(ws), ctypes.c_void_p)))
         return nb.value, ws.value
+
+    def set_lno_threshold(self, lambda_th):
+        """Keep the LNOs with eigenvalue >= lambda_th (at most k_lno per atom); None = fixed k_lno."""
+        on = lambda_th is not None
+        self._check(self.lib.dclno_set_lno_threshold(self.h, int(on), float(lambda_th) if on else 0.0))
+
+    def lno_counts(self):
+        """LNOs per atom of the last LNO computation."""
+        k = np.zeros(self.natoms, np.int32)
+        self._check(self.lib.dclno_get_lno_counts(self.h, _ptr(k)))
+        return k
 
     def set_autotune(self, on=True):
         """Time the QL launch shape on each batch's first eager solve (default on)."""

@@ -63,6 +63,7 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_err);
     dfree(c->d_hist);
     dfree(c->d_tune);
+    dfree(c->d_kat);
     c->tune_doubles = 0;
     c->ql_lanes.clear();
     c->ql_tune_ms.clear();
@@ -574,6 +575,10 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     COPY(c->d_brow, brow32);
     COPY(c->d_tblk_off, tblk_off);
     COPY(c->d_rowblk_member, rowblk_member);
+    c->kat.assign(N, k_lno);
+    COPY(c->d_kat, c->kat);
+    c->layout_split.resize(N);
+    for (int i = 0; i < N; ++i) c->layout_split[i] = c->cl[i].split ? 1 : 0;
 #undef COPY
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_status, sizeof(int) * N)) != cudaSuccess ||
@@ -634,6 +639,58 @@ extern "C" dclno_status dclno_build_clusters_kappa(dclno_ctx* c, const dclno_sys
     return build_impl(c, sys, 0.0, r_lno, k_lno, kappa, s_fna);
 }
 
+// Cluster dimensions after a threshold selection of LNOs: member sizes M_j (short
+// range) or the atom's own LNO count; the workspace keeps the layout made for
+// k_lno, every new dimension being at most the laid-out one.
+dclno_status relayout_clusters(dclno_ctx* c) {
+    DCLNO_CUDA(c, cudaMemcpyAsync(c->kat.data(), c->d_kat, sizeof(int) * c->N, cudaMemcpyDeviceToHost, c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    long long eig = 0;
+    for (int i = 0; i < c->N; ++i) {
+        ClusterDesc& d = c->cl[i];
+        int off = 0;
+        for (int m = 0; m < d.nmem; ++m) {
+            MemberDesc& md = c->mem[d.mbeg + m];
+            md.off = off;
+            off += md.core ? c->norb[md.atom] : c->kat[md.atom];
+        }
+        if (off > d.ld) return set_err(c, DCLNO_ERR_ARG, "LNO counts exceed the laid-out cluster dimension");
+        d.n = off;
+        // keep tearing where the layout tore: the segment logs were sized for halves
+        d.split = (c->layout_split[i] && off >= 2) ? off / 2 : 0;
+        d.eig_off = eig;
+        eig += off;
+    }
+    c->total_dim = eig;
+    for (Batch& b : c->batches) {
+        b.maxn = 0;
+        for (int i = b.id_lo; i < b.id_hi; ++i) b.maxn = std::max(b.maxn, c->cl[i].n);
+    }
+    DCLNO_CUDA(c, cudaMemcpyAsync(c->d_cl, c->cl.data(), sizeof(ClusterDesc) * c->cl.size(), cudaMemcpyHostToDevice,
+                                  c->stream));
+    DCLNO_CUDA(c, cudaMemcpyAsync(c->d_mem, c->mem.data(), sizeof(MemberDesc) * c->mem.size(),
+                                  cudaMemcpyHostToDevice, c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->resident = -1;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_lno_threshold(dclno_ctx* c, int on, double lambda_th) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (on && !(lambda_th == lambda_th)) return set_err(c, DCLNO_ERR_ARG, "dclno_set_lno_threshold: lambda_th is NaN");
+    c->lno_th_on = on != 0;
+    c->lno_th = lambda_th;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_get_lno_counts(dclno_ctx* c, int* counts) {
+    if (!c) return DCLNO_ERR_ARG;
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_get_lno_counts: build clusters first");
+    if (counts) std::copy(c->kat.begin(), c->kat.end(), counts);
+    return DCLNO_OK;
+}
+
 extern "C" dclno_status dclno_compute_lnos(dclno_ctx* c, const double* rho) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
@@ -643,7 +700,11 @@ extern "C" dclno_status dclno_compute_lnos(dclno_ctx* c, const double* rho) {
         return DCLNO_OK;
     }
     if (!rho) return set_err(c, DCLNO_ERR_ARG, "dclno_compute_lnos: rho is NULL");
+    const bool counted = c->lno_th_on || c->relaid;  // the layout follows the counts of these LNOs
+    const bool th = c->lno_th_on;
     dclno_status st = launch_lambda_lno(c, rho);
+    if (st == DCLNO_OK && counted && !th) st = relayout_clusters(c);  // back to k_lno for every atom
+    c->relaid = th;
     if (st != DCLNO_OK) return st;
     c->lnos_ready = true;
     c->solved = false;
@@ -865,6 +926,9 @@ extern "C" dclno_status dclno_scf_run(dclno_ctx* c, double* rho, int nsteps, dou
     if (!rho || nsteps < 1 || !(kT > 0.0) || !(alpha > 0.0 && alpha <= 1.0))
         return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: need rho, nsteps >= 1, kT > 0, 0 < alpha <= 1");
     if (prec != DCLNO_FP64 && prec != DCLNO_MIXED) return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: unknown precision");
+    if (c->lno_th_on && c->has_lno_region)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: threshold-selected LNOs change the cluster dimensions every "
+                                         "step (a host re-layout); loop over dclno_step instead");
     if (use_graph && c->stream == nullptr)
         return set_err(c, DCLNO_ERR_ARG, "dclno_scf_run: graph capture needs a context on a non-default stream");
     const size_t bytes = (size_t)c->nval * sizeof(double);

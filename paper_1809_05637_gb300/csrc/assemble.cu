@@ -113,6 +113,7 @@ __global__ void k_lno_blocks(long long nnzb, int k, const int* __restrict__ brow
 __global__ void __launch_bounds__(128) k_assemble(long long mbeg, const ClusterDesc* __restrict__ cls,
                                                   const MemberDesc* __restrict__ mem,
                                                   const int* __restrict__ mem_cl, const int* __restrict__ norb,
+                                                  const int* __restrict__ kat,
                                                   const int* __restrict__ pairblk,
                                                   const long long* __restrict__ blk_off,
                                                   const long long* __restrict__ tblk_off, int k,
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(128) k_assemble(long long mbeg, const ClusterD
     const int m1 = (int)(g1 - d.mbeg);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int M1 = norb[a.atom];
-    const int n1 = a.core ? M1 : k;
+    const int n1 = a.core ? M1 : kat[a.atom];  // an LNO member's own count (<= k)
     double* Hc = arena + d.mat_off;
     double* Sc = Hc + (size_t)d.n * d.ld;
     const int ld = d.ld;
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(128) k_assemble(long long mbeg, const ClusterD
     for (int m2 = warp; m2 < d.nmem; m2 += nw) {
         const MemberDesc b = mem[d.mbeg + m2];
         const int M2 = norb[b.atom];
-        const int n2 = b.core ? M2 : k;
+        const int n2 = b.core ? M2 : kat[b.atom];
+        const int lds = b.core ? M2 : k;  // row length of the source block (LNO blocks are laid out for k)
         const long long blk = prow[m2];
         const double *sh = nullptr, *ss = nullptr;
         if (blk >= 0) {
@@ -157,8 +159,8 @@ __global__ void __launch_bounds__(128) k_assemble(long long mbeg, const ClusterD
         for (int e = lane; e < n1 * n2; e += 32) {
             const int p = e / n2, q = e % n2;
             const size_t o = (size_t)(a.off + p) * ld + b.off + q;
-            Hc[o] = sh ? sh[e] : 0.0;
-            Sc[o] = ss ? ss[e] : 0.0;
+            Hc[o] = sh ? sh[p * lds + q] : 0.0;
+            Sc[o] = ss ? ss[p * lds + q] : 0.0;
         }
     }
 }
@@ -189,7 +191,7 @@ dclno_status launch_assemble(dclno_ctx* c, const Batch& b) {
     if (nm == 0) return DCLNO_OK;
     {
         ProfScope ps__(c, "k_assemble");
-        k_assemble<<<(unsigned)nm, 128, 0, c->stream>>>(b.mbeg, c->d_cl, c->d_mem, c->d_mem_cl, c->d_norb,
+        k_assemble<<<(unsigned)nm, 128, 0, c->stream>>>(b.mbeg, c->d_cl, c->d_mem, c->d_mem_cl, c->d_norb, c->d_kat,
                                                         c->d_pairblk, c->d_blk_off, c->d_tblk_off, c->k_lno, c->H,
                                                         c->S, c->d_tblk, c->d_arena);
     }

@@ -165,6 +165,14 @@ struct dclno_ctx {
     double* d_lam_im = nullptr;
     double* d_Lambda = nullptr;
     int* d_lflags = nullptr;
+    // threshold selection of LNOs (Sec. II.B step (iii)): per-atom counts <= k_lno; the
+    // workspace is laid out for k_lno, the dimensions follow the counts of the last LNOs
+    bool lno_th_on = false;
+    double lno_th = 0.0;
+    int* d_kat = nullptr;               // LNOs of each atom (k_lno without a threshold)
+    std::vector<int> kat;
+    bool relaid = false;                // the layout follows threshold-selected counts
+    std::vector<char> layout_split;     // per cluster: laid out as a torn problem
 
     // solve / mu
     bool solved = false;
@@ -230,6 +238,7 @@ dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where);
 
 // kernels' host-side launchers (one per .cu file)
 dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
+dclno_status relayout_clusters(dclno_ctx* c);
 dclno_status launch_lno_blocks(dclno_ctx* c);
 dclno_status launch_assemble(dclno_ctx* c, const Batch& b);
 dclno_status launch_pair_index(dclno_ctx* c);

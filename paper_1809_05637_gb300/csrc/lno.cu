@@ -237,12 +237,13 @@ __device__ static void lu_solve(double* Mx, int n, double* b, double tiny) {
 // ---------------------------------------------------------------------------
 // One thread per atom
 // ---------------------------------------------------------------------------
-__global__ void k_lno_eig(int N, int k, const int* __restrict__ norb, const long long* __restrict__ loff,
+__global__ void k_lno_eig(int N, int k, int use_th, double lam_th, const int* __restrict__ norb,
+                          const long long* __restrict__ loff,
                           const long long* __restrict__ moff, const long long* __restrict__ voff,
                           const long long* __restrict__ onsite, const long long* __restrict__ blk_off,
                           const double* __restrict__ S, const double* __restrict__ Lam,
                           double* __restrict__ V, double* __restrict__ lam_re, double* __restrict__ lam_im,
-                          int* __restrict__ flags, int* __restrict__ status) {
+                          int* __restrict__ flags, int* __restrict__ kat, int* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int m = norb[i];
@@ -281,6 +282,7 @@ __global__ void k_lno_eig(int N, int k, const int* __restrict__ norb, const long
     const double tiny = 1e-300;
     while (got < k && pos < m) {
         const double lr = wr[ord[pos]], li = wi[ord[pos]];
+        if (use_th && lr < lam_th) break;  // threshold selection: eigenvalues >= lambda_th only
         const double sh = lr + 1e-13 * anorm;  // shifted off the eigenvalue to keep the solve regular
         if (li == 0.0) {
             double x[MM];
@@ -349,10 +351,14 @@ __global__ void k_lno_eig(int N, int k, const int* __restrict__ norb, const long
             pos += 2;
         }
     }
-    // S_ii-orthonormal basis of the span (Gram-Schmidt in eigenvalue order, twice)
+    // S_ii-orthonormal basis of the span (Gram-Schmidt in eigenvalue order, twice);
+    // the columns beyond this atom's count (threshold selection) are zero
+    const int kk = got;
+    for (int c = kk; c < k; ++c)
+        for (int r = 0; r < m; ++r) Vi[r * k + c] = 0.0;
     const double* Sii = S + blk_off[onsite[i]];
     for (int pass = 0; pass < 2; ++pass) {
-        for (int c = 0; c < k; ++c) {
+        for (int c = 0; c < kk; ++c) {
             for (int d = 0; d < c; ++d) {
                 // coefficient <v_d, v_c>_S
                 double h = 0.0;
@@ -377,7 +383,7 @@ __global__ void k_lno_eig(int N, int k, const int* __restrict__ norb, const long
             for (int r = 0; r < m; ++r) Vi[r * k + c] *= nn;
         }
     }
-    for (int c = 0; c < k; ++c) {
+    for (int c = 0; c < kk; ++c) {
         int jm = 0;
         for (int r = 1; r < m; ++r)
             if (fabs(Vi[r * k + c]) > fabs(Vi[jm * k + c])) jm = r;
@@ -385,6 +391,7 @@ __global__ void k_lno_eig(int N, int k, const int* __restrict__ norb, const long
             for (int r = 0; r < m; ++r) Vi[r * k + c] = -Vi[r * k + c];
     }
     flags[i] = fl;
+    kat[i] = kk;
     status[i] = ST_OK;
 }
 
@@ -398,9 +405,11 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_lno_eig");
-        k_lno_eig<<<(N + 63) / 64, 64, 0, c->stream>>>(N, c->k_lno, c->d_norb, c->d_loff, c->d_moff, c->d_voff,
-                                                   c->d_onsite, c->d_blk_off, c->S, c->d_Lambda, c->d_V,
-                                                   c->d_lam_re, c->d_lam_im, c->d_lflags, c->d_status);
+        const int use_th = c->lno_th_on ? 1 : 0;
+        k_lno_eig<<<(N + 63) / 64, 64, 0, c->stream>>>(N, c->k_lno, use_th, c->lno_th, c->d_norb, c->d_loff,
+                                                   c->d_moff, c->d_voff, c->d_onsite, c->d_blk_off, c->S,
+                                                   c->d_Lambda, c->d_V, c->d_lam_re, c->d_lam_im, c->d_lflags,
+                                                   c->d_kat, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     if (c->deferred) return launch_status_or(c);
@@ -413,5 +422,6 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
         if (st[i] != ST_OK)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "LNO basis of atom " + std::to_string(i) + " is degenerate");
     }
+    if (c->lno_th_on) return relayout_clusters(c);
     return DCLNO_OK;
 }

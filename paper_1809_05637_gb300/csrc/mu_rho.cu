@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDes
 __global__ void k_rho_scatter(int id_lo, const ClusterDesc* __restrict__ cls, const MemberDesc* __restrict__ mem,
                               const int* __restrict__ norb, const long long* __restrict__ row_ptr,
                               const long long* __restrict__ key, const long long* __restrict__ blk_off,
-                              const int* __restrict__ rowblk_member, const long long* __restrict__ voff, int k,
+                              const int* __restrict__ rowblk_member, const long long* __restrict__ voff,
+                              const int* __restrict__ kat, int k,
                               const double* __restrict__ V, const double* __restrict__ arena,
                               double* __restrict__ rho, double* __restrict__ e_out) {
     const int i = id_lo + blockIdx.y;
@@ -356,6 +357,7 @@ __global__ void k_rho_scatter(int id_lo, const ClusterDesc* __restrict__ cls, co
         }
         const MemberDesc md = mem[d.mbeg + m];
         const double* Vj = md.core ? nullptr : V + voff[j];
+        const int kj = md.core ? 0 : kat[j];  // the member's LNO count (V rows have stride k)
         for (int e = lane; e < mc * mj; e += 32) {
             const int a = e / mj, bb = e % mj;
             double s = 0.0, se = 0.0;
@@ -363,7 +365,7 @@ __global__ void k_rho_scatter(int id_lo, const ClusterDesc* __restrict__ cls, co
                 s = X[(size_t)(md.off + bb) * w + a];
                 if (oute) se = X[(size_t)(md.off + bb) * w + mc + a];
             } else {
-                for (int g = 0; g < k; ++g) {
+                for (int g = 0; g < kj; ++g) {
                     const double v = Vj[bb * k + g];
                     s = fma(X[(size_t)(md.off + g) * w + a], v, s);
                     if (oute) se = fma(X[(size_t)(md.off + g) * w + mc + a], v, se);
@@ -414,7 +416,7 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
         ProfScope ps__(c, "k_rho_scatter");
         k_rho_scatter<<<dim3(bx, N), wpb * 32, 0, c->stream>>>(b.id_lo, c->d_cl, c->d_mem, c->d_norb, c->d_row_ptr,
                                                           c->d_key, c->d_blk_off, c->d_rowblk_member, c->d_voff,
-                                                          c->k_lno, c->d_V, c->d_arena, rho_out, e_out);
+                                                          c->d_kat, c->k_lno, c->d_V, c->d_arena, rho_out, e_out);
     }
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;

@@ -241,3 +241,41 @@ def test_kappa_radius_ties_go_to_the_larger_sphere():
     assert O.kappa_radius(d, fna, 0.5) == 1.0
     assert O.kappa_radius(d, fna, 1.0 / 3.0) == 1.0
     assert O.kappa_radius(d, fna, 0.75) == 2.0
+
+
+# ---------------------------------------------------------------------------
+# Threshold selection of LNOs (Sec. II.B step (iii), lambda_th)
+# ---------------------------------------------------------------------------
+def test_lno_threshold_selects_eigenvalues_above_lambda_th():
+    """Lambda = X diag(lam) X^-1 with known real eigenvalues: the threshold keeps
+    exactly those >= lambda_th (capped at k), spanning their eigenvectors."""
+    rng = np.random.default_rng(4)
+    m = 6
+    lam = np.array([0.95, 0.6, 0.12, 0.1 + 1e-7, 0.1 - 1e-7, -0.02])
+    X = rng.normal(size=(m, m)) + 3 * np.eye(m)
+    L = X @ np.diag(lam) @ np.linalg.inv(X)
+    S = np.eye(m)
+    V, ev, fl = O.lnos(L, S, 5, lambda_th=0.1)
+    assert V.shape == (m, 4)  # 0.95, 0.6, 0.12 and 0.1 + 1e-7, not 0.1 - 1e-7
+    P = X[:, :4] @ np.linalg.pinv(X[:, :4])  # projector on the selected eigenvectors
+    np.testing.assert_allclose(P @ V, V, atol=1e-10)
+    assert O.lnos(L, S, 2, lambda_th=0.1)[0].shape == (m, 2)      # capped at k
+    assert O.lnos(L, S, 5, lambda_th=0.99)[0].shape == (m, 0)     # none qualifies
+    np.testing.assert_allclose(O.lnos(L, S, 4)[0] @ O.lnos(L, S, 4)[0].T, V @ V.T, atol=1e-10)
+
+
+def test_threshold_with_all_lnos_equals_plain_dc(cfg1):
+    """lambda_th below every eigenvalue and k = M: every atom keeps its whole basis,
+    the all-LNO identity again (Eq. (apop_Lambda) with every term kept)."""
+    s = cfg1
+    r = 6.0
+    rho0 = O.plain_dc_density(s, s.r_core)[2]
+    lno = O.compute_lnos(s, rho0, int(s.norb[0]), lambda_th=-1e9)
+    V = {j: v[0] for j, v in lno.items()}
+    kat = {j: v.shape[1] for j, v in V.items()}
+    assert set(kat.values()) == {int(s.norb[0])}
+    atoms = [0, 21, 63]
+    res = O.dclno_solve(s, V, 3.0, r, 2, atoms=atoms, k_atoms=kat)
+    ref = O.dclno_solve(s, V, r, r, 2, atoms=atoms)
+    for i in atoms:
+        np.testing.assert_allclose(res[i].eps, ref[i].eps, atol=1e-9)
