@@ -21,7 +21,7 @@ __all__ = [
     "cholesky", "jacobi", "gen_eig", "nonsym_eig", "inverse_iter",
     "Cluster", "cluster_members", "kappa_radius", "lambda_blocks", "lnos", "compute_lnos",
     "assemble", "solve_cluster", "fermi", "n_of_mu", "find_mu", "density_rows",
-    "dclno_solve", "finish_step", "energy_density", "plain_dc_density", "full_diag", "dense_matrices",
+    "dclno_solve", "finish_step", "energy_density", "density_rows_poles", "plain_dc_density", "full_diag", "dense_matrices",
     "cluster_dim", "time_ratio", "NoBracket", "NotSPD",
 ]
 
@@ -477,12 +477,49 @@ def density_rows(system, cl: Cluster, eps, C, V: dict, mu: float, kT: float,
     cluster are zero (only elements with S != 0 are kept).  Writes the rows into
     the BSR value array rho_out.
     """
-    i = cl.centre
     c = cl.centre_slice
     w = fermi((eps - mu) / kT)
     if energy:
         w = w * eps
     rcl = (C[c, :] * w[None, :]) @ C.T  # M_i x n
+    _scatter_rows(system, cl, rcl, V, rho_out)
+
+
+def density_rows_poles(system, cl: Cluster, Hc: np.ndarray, Sc: np.ndarray, V: dict, mu: float, kT: float,
+                       rho_out: np.ndarray, n_poles: int) -> None:
+    """The same rows from the Green function at the Matsubara poles (the
+    generalisation of Eq. (rho0j) to a non-orthogonal basis), with no eigenvectors:
+    f(x) = 1/2 + (2/beta) sum_{p>=0} Re 1/(i w_p - x), w_p = (2p+1) pi kT, so
+        rho^(i) = S^-1 / 2 + (2/beta) Re sum_{p>=0} (z_p S - H)^-1,  z_p = mu + i w_p.
+    The poles p >= n_poles are summed from the large-|z| expansion
+    Re (z_p S - H)^-1 = -A_1/w_p^2 + A_3/w_p^4 - A_5/w_p^6 + ...,
+    A_k = S^-1 ((H - mu S) S^-1)^k, with sum_{p>=P} w_p^-2m = (pi kT)^-2m zeta(2m, P + 1/2) / 4^m
+    (Hurwitz zeta); this needs w_P well above the cluster's spectral radius about mu."""
+    from scipy.special import zeta
+
+    beta = 1.0 / kT
+    n = Hc.shape[0]
+    Sinv = np.linalg.inv(Sc)
+    acc = np.zeros((n, n))
+    for p in range(n_poles):
+        z = mu + 1j * (2 * p + 1) * math.pi * kT
+        acc += np.linalg.solve(z * Sc - Hc, np.eye(n)).real
+    Bm = (Hc - mu * Sc) @ Sinv
+    A1 = Sinv @ Bm
+    A3 = A1 @ Bm @ Bm
+    A5 = A3 @ Bm @ Bm
+    def tail(m):  # sum_{p >= n_poles} w_p^-2m
+        return (math.pi * kT) ** (-2 * m) * float(zeta(2 * m, n_poles + 0.5)) / 4 ** m
+    acc += -A1 * tail(1) + A3 * tail(2) - A5 * tail(3)
+    rho_c = 0.5 * Sinv + (2.0 / beta) * acc
+    c = cl.centre_slice
+    _scatter_rows(system, cl, rho_c[c, :], V, rho_out)
+
+
+def _scatter_rows(system, cl: Cluster, rcl: np.ndarray, V: dict, rho_out: np.ndarray) -> None:
+    """Central rows rcl (M_i x n, cluster basis) into the BSR rows of atom i: LNO
+    columns back to PAOs with V_j, zero outside the cluster."""
+    i = cl.centre
     where = {(int(cl.atoms[m]),) + tuple(int(x) for x in cl.shifts[m]): m for m in range(len(cl.atoms))}
     mi = int(system.norb[i])
     for b in range(int(system.row_ptr[i]), int(system.row_ptr[i + 1])):

@@ -17,6 +17,7 @@ import pytest
 import scipy.linalg as sl
 
 import oracle as O
+import tbsystems as T
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -279,3 +280,27 @@ def test_threshold_with_all_lnos_equals_plain_dc(cfg1):
     ref = O.dclno_solve(s, V, r, r, 2, atoms=atoms)
     for i in atoms:
         np.testing.assert_allclose(res[i].eps, ref[i].eps, atol=1e-9)
+
+
+def test_density_rows_equal_matsubara_pole_sum():
+    """Eq. (dm) through the spectral form Eq. (Gi) equals the Green function summed
+    over the Matsubara poles (Eq. (rho0j), non-orthogonal form) for every cluster of
+    a small system with a narrow spectrum (two Gaussians per atom), the poles taken
+    until w_P is 40 times the cluster's spectral radius about mu."""
+    s = T.small_lattice(3, 3, 3, a=2.5, exps=(0.5, 1.5), onsite=(-0.4, 0.2), e_per_atom=2.0, r_core=3.0,
+                        r_lno=6.0, k_lno=1)
+    rho0 = O.plain_dc_density(s, s.r_core)[2]
+    lno = O.compute_lnos(s, rho0, 1)
+    V = {j: v[0] for j, v in lno.items()}
+    res = O.dclno_solve(s, V, s.r_core, s.r_lno, 1)
+    mu = O.finish_step(s, res, V, s.n_electrons, s.kT)[0]
+    a = np.zeros_like(s.S)
+    b = np.zeros_like(s.S)
+    assert any(not np.all(r.cluster.core) for r in res.values())  # LNO members take part
+    for i, r in res.items():
+        Hc, Sc = O.assemble(s, r.cluster, V)
+        rad = float(np.max(np.abs(r.eps - mu)))
+        n_poles = int(40.0 * rad / (2 * np.pi * s.kT)) + 1
+        O.density_rows(s, r.cluster, r.eps, r.C, V, mu, s.kT, a)
+        O.density_rows_poles(s, r.cluster, Hc, Sc, V, mu, s.kT, b, n_poles)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-11)
