@@ -39,40 +39,31 @@ __device__ __forceinline__ int eg_exp(double x) {
 
 // Split rows [r0, r0+64) x k [k0, k0+32) of X (row-major, ld) into EG_SL slice tiles
 // of bf16 in shared memory; expo[row] receives the row exponent.  Rows >= nrows and
-// k >= K are zero.
+// k >= K are zero.  A warp takes one row at a time, a lane one k: each element is
+// read from global memory once and the row's exponent is a warp maximum.
 __device__ __forceinline__ void eg_slice_tile(const double* __restrict__ X, int ld, int r0, int nrows, int k0,
                                               int K, __nv_bfloat16* sl, int* expo) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // row exponents: one warp per row, lanes over the 32 k values
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = warp; r < EG_M; r += nw) {
-        int e = -100000;
         const int gr = r0 + r, gk = k0 + lane;
-        if (gr < nrows && gk < K) e = eg_exp(X[(size_t)gr * ld + gk]);
+        const double x = (gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.0;
+        const long long b = __double_as_longlong(x);
+        const int ebits = (int)((b >> 52) & 0x7ff);
+        int e = ebits == 0 ? -100000 : ebits - 1023;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
         if (lane == 0) expo[r] = e;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < EG_M * EG_K; idx += blockDim.x) {
-        const int r = idx / EG_K, kk = idx % EG_K;
-        const int gr = r0 + r, gk = k0 + kk;
         unsigned long long al = 0ull;
-        bool neg = false;
-        if (gr < nrows && gk < K) {
-            const double x = X[(size_t)gr * ld + gk];
-            const long long b = __double_as_longlong(x);
-            const int eb = (int)((b >> 52) & 0x7ff);
-            if (eb != 0) {
-                neg = b < 0;
-                const unsigned long long man = ((unsigned long long)b & 0xfffffffffffffull) | 0x10000000000000ull;
-                const int sh = expo[r] - (eb - 1023);
-                al = sh >= 64 ? 0ull : ((man << 11) >> sh);
-            }
+        if (ebits != 0) {
+            const unsigned long long man = ((unsigned long long)b & 0xfffffffffffffull) | 0x10000000000000ull;
+            const int sh = e - (ebits - 1023);
+            al = sh >= 64 ? 0ull : ((man << 11) >> sh);
         }
+        const bool neg = b < 0;
 #pragma unroll
         for (int t = 0; t < EG_SL; ++t) {
             const int v = (int)((al >> (56 - 8 * t)) & 0xffull);
-            sl[(t * EG_M + r) * EG_LDS + kk] = __float2bfloat16_rn((float)(neg ? -v : v));
+            sl[(t * EG_M + r) * EG_LDS + lane] = __float2bfloat16_rn((float)(neg ? -v : v));
         }
     }
 }
@@ -93,11 +84,15 @@ __device__ void cta_gemm_nt_sub_emu(double* __restrict__ C, int ldc, const doubl
     const int wc = (warp & 3) * 16;   // warp's cols (0, 16, 32, 48)
     const int g = lane >> 2, tg = lane & 3;
     const int tilesM = (M + EG_M - 1) / EG_M, tilesN = (N + EG_N - 1) / EG_N;
+    int sliced_ti = -1;  // A's slices stay in shared memory while the tile row is the same
     for (int tix = 0; tix < tilesM * tilesN; ++tix) {
         const int ti = tix / tilesN, tj = tix % tilesN;
         const int r0 = ti * EG_M, c0 = tj * EG_N;
         if (LOWER && r0 + EG_M - 1 + diag < c0) continue;  // uniform across the CTA
-        eg_slice_tile(A, lda, r0, M, 0, K, As, ea);
+        if (ti != sliced_ti) {
+            eg_slice_tile(A, lda, r0, M, 0, K, As, ea);
+            sliced_ti = ti;
+        }
         eg_slice_tile(B, ldb, c0, N, 0, K, Bs, eb);
         __syncthreads();
         // sum_L acc_L 2^-8L in units of 2^-32 (levels 5-7 lose bits below 2^-56 of the largest term)
