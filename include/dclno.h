@@ -203,7 +203,9 @@ dclno_status dclno_get_lno_counts(dclno_ctx *ctx, int *counts);
 /*
  * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
  * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
- * implicit QL on the tridiagonal matrix, and the central-atom rows of the
+ * implicit QL on the two halves of the tridiagonal matrix torn at n/2 (Cuppen's
+ * divide and conquer, the halves merged through the secular equation), and the
+ * central-atom rows of the
  * eigenvectors C = L^-T Q Z.  Keeps per cluster the eigenvalues eps_mu,
  * the weights q_mu = sum_{alpha in i} C_{alpha mu} (S^(i) C)_{alpha mu}
  * (sum_mu q_mu = M_i) and what dclno_density_matrix needs.

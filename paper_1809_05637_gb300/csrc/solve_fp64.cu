@@ -3,11 +3,17 @@
 //
 //   k_cholesky     S^(i) = L L^T                 blocked right-looking, DMMA trailing updates
 //   k_congruence   A = L^-1 H^(i) L^-T           two blocked right-side triangular solves
-//   k_tridiag      A = Q T Q^T                   blocked Householder (DFMA symv, DMMA rank-2k)
-//   k_ql           T = Z Theta Z^T               implicit QL; rotations logged, not accumulated
+//   k_tridiag      A = Q T Q^T                   blocked Householder (DFMA symv, DMMA rank-2k);
+//                                                 T torn at n/2 into two halves (Cuppen)
+//   k_ql           T1, T2 = Z_k Theta_k Z_k^T    implicit QL per half; rotations logged, not accumulated
+//   k_merge        (merge.cu)                    rank-one merge: eigenvalues of T and the merge matrix M
 //   k_apply_q_rows P <- P Q                       central rows [L_cc^-T | L_c,:] times Q
-//   k_replay_fwd   P <- P Z                       the logged rotations applied to P's columns
+//   k_replay_fwd   P <- P diag(Z1, Z2)            the logged rotations applied to P's columns
+//   k_mgemm        P <- P M                       (Z = diag(Z1, Z2) M)
 //   k_weights      q_mu = sum_a (C_c)_{a mu} (S C)_{c a, mu}, eigenvalues out
+// The same kernels with EMU = true are the mixed path: the tile updates of
+// Cholesky, congruence, tridiagonalisation and the merge products run on BF16
+// tensor cores with FP64 emulated by 8-bit slices (emu_gemm.cuh).
 //
 // The central atom is the last member of its cluster, so the central rows of
 // C = L^-T Q Z are L_cc^-T (Q Z)_c and those of S C = L Q Z are L_c,: Q Z: both
