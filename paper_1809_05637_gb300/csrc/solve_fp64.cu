@@ -24,6 +24,10 @@
 
 #define NB DCLNO_NB
 #define DK_LD 33
+// CTAs per SM the cubic kernels are compiled for: the FP64 tiles gain from a third
+// CTA (latency hiding), the emulated ones lose by it (their slicing needs registers);
+// measured on the 1728-atom step.
+#define DCLNO_CTAS_PER_SM(EMU) ((EMU) ? 2 : 3)
 
 // The cubic steps' tile update: FP64 mma.sync tiles (FP64 path) or FP64 emulated
 // on BF16 tensor cores (mixed path).
@@ -75,7 +79,7 @@ __device__ static void load_diag_block(const double* L, int ld, int kb, int nb, 
 // Cholesky of S^(i) in place (lower); sets ST_NOT_SPD on a non-positive pivot.
 // ---------------------------------------------------------------------------
 template <bool EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_cholesky(const ClusterDesc* __restrict__ cls,
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_cholesky(const ClusterDesc* __restrict__ cls,
                                                                   const int* __restrict__ order,
                                                                   double* __restrict__ arena,
                                                                   int* __restrict__ status) {
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_cholesky(const Clust
 // Y = H L^-T (all rows), transpose, then A = Y^T L^-T restricted to the lower part.
 // ---------------------------------------------------------------------------
 template <bool EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_congruence(const ClusterDesc* __restrict__ cls,
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_congruence(const ClusterDesc* __restrict__ cls,
                                                                     const int* __restrict__ order,
                                                                     double* __restrict__ arena,
                                                                     const int* __restrict__ status) {
@@ -207,7 +211,7 @@ __device__ static double block_sum(double v, double* red) {
 }
 
 template <bool EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_tridiag(const ClusterDesc* __restrict__ cls,
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_tridiag(const ClusterDesc* __restrict__ cls,
                                                                  const int* __restrict__ order,
                                                                  double* __restrict__ arena,
                                                                  const int* __restrict__ status) {
