@@ -19,7 +19,8 @@ from . import build as _build
 
 __all__ = [
     "cholesky", "jacobi", "gen_eig", "nonsym_eig", "inverse_iter",
-    "Cluster", "cluster_members", "kappa_radius", "lambda_blocks", "lnos", "compute_lnos",
+    "Cluster", "cluster_members", "kappa_radius", "lambda_blocks", "projector_blocks", "lnos", "lnos_sym",
+    "compute_lnos",
     "assemble", "solve_cluster", "fermi", "n_of_mu", "find_mu", "density_rows",
     "dclno_solve", "finish_step", "energy_density", "density_rows_poles", "plain_dc_density", "full_diag", "dense_matrices",
     "cluster_dim", "time_ratio", "NoBracket", "NotSPD",
@@ -335,6 +336,13 @@ def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int, lambda_th: float | None = No
             flags |= LNO_PAIR_SPLIT
         pos += 2  # skip the conjugate partner
     V = np.column_stack(vecs[:k]) if vecs else np.zeros((m, 0))
+    return _canonical_basis(V, s_ii), ev, flags
+
+
+def _canonical_basis(V: np.ndarray, s_ii: np.ndarray) -> np.ndarray:
+    """The columns of V made S_ii-orthonormal by Gram-Schmidt in their order (two
+    passes), each with its largest-magnitude component positive."""
+    V = V.copy()
     for _ in range(2):
         for c in range(V.shape[1]):
             v = V[:, c].copy()
@@ -345,13 +353,77 @@ def lnos(lam: np.ndarray, s_ii: np.ndarray, k: int, lambda_th: float | None = No
         jm = int(np.argmax(np.abs(V[:, c])))
         if V[jm, c] < 0:
             V[:, c] = -V[:, c]
-    return V, ev, flags
+    return V
 
 
-def compute_lnos(system, rho: np.ndarray, k: int, atoms=None, lambda_th: float | None = None) -> dict:
+def projector_blocks(system, rho: np.ndarray, atoms=None) -> dict:
+    """(S rho S)_{0i,0i} = sum_{Ra} sum_{Rb} S_{0i,Ra} rho_{Ra,Rb} S_{Rb,0i}, M_i x M_i.
+
+    The on-site block of the occupied-space projector in the PAO metric: with
+    rho = C f C^T (Eq. (dm)), <chi_0i|P|chi_0i> = S C f C^T S, the symmetric
+    counterpart of Lambda_0i = (rho S)_{0i,0i} (Eq. (Lambda), Sec. II.B).
+
+    rho_{Ra,Rb} = rho_{0a,(Rb-Ra)b} by translation invariance: block (a, t1) of
+    row i and block (b, t2) of row a reach atom b in cell t1 + t2, whose overlap
+    with the centre is block (b, t1 + t2) of row i, transposed (S is symmetric);
+    terms whose block is absent from the pattern are zero.
+    """
+    if atoms is None:
+        atoms = range(system.natoms)
+    bidx = _BlockIndex(system)
+    out = {}
+    for i in atoms:
+        i = int(i)
+        mi = int(system.norb[i])
+        G = np.zeros((mi, mi))
+        for p in range(int(system.row_ptr[i]), int(system.row_ptr[i + 1])):
+            a = int(system.col[p])
+            ma = int(system.norb[a])
+            t1 = system.shift[p]
+            W = np.zeros((ma, mi))
+            for q in range(int(system.row_ptr[a]), int(system.row_ptr[a + 1])):
+                b = int(system.col[q])
+                r = bidx.get(i, b, t1 + system.shift[q])
+                if r is None:
+                    continue
+                W += system.block(rho, q) @ system.block(system.S, r).T
+            G += system.block(system.S, p) @ W
+        out[i] = G
+    return out
+
+
+def lnos_sym(G: np.ndarray, s_ii: np.ndarray, k: int, lambda_th: float | None = None):
+    """LNOs of one atom from the symmetric-definite problem G v = lambda S_ii v,
+    G = (S rho S)_ii (projector_blocks).
+
+    Only the symmetric part of G enters: it is the block of S rho_s S with
+    rho_s = (rho + rho^T)/2 (S is symmetric), the projector of the symmetrised
+    density matrix; the raw rows of a DC step are not exactly symmetric.
+    Eigenpairs by Cholesky + congruence + Jacobi, eigenvalues descending; the
+    leading k are kept (with lambda_th, those >= lambda_th, at most k) and
+    returned in the canonical basis of lnos().  Returns (V, eigenvalues (complex
+    dtype, zero imaginary parts), flags = 0).
+    """
+    Gs = 0.5 * (G + G.T)
+    w, C = gen_eig(Gs, s_ii)
+    w, C = w[::-1].copy(), C[:, ::-1]
+    kk = min(k, len(w))
+    if lambda_th is not None:
+        kk = min(kk, int(np.sum(w >= lambda_th)))
+    return _canonical_basis(C[:, :kk], s_ii), w.astype(np.complex128), 0
+
+
+def compute_lnos(system, rho: np.ndarray, k: int, atoms=None, lambda_th: float | None = None,
+                 mode: str = "paper") -> dict:
     """atom -> (V, eigenvalues, flags) for the given atoms (default: all); with
     lambda_th, each atom keeps the eigenvectors whose eigenvalue is >= lambda_th
-    (at most k), so V has that atom's own number of columns."""
+    (at most k), so V has that atom's own number of columns.  mode "paper" takes
+    the nonsymmetric Lambda (lnos), mode "sym" the projector form (lnos_sym)."""
+    if mode == "sym":
+        G = projector_blocks(system, rho, atoms)
+        return {i: lnos_sym(g, _on_site_block(system, i), k, lambda_th) for i, g in G.items()}
+    if mode != "paper":
+        raise ValueError(f"unknown LNO mode {mode!r}")
     lam = lambda_blocks(system, rho, atoms)
     return {i: lnos(L, _on_site_block(system, i), k, lambda_th) for i, L in lam.items()}
 
