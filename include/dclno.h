@@ -63,6 +63,12 @@ typedef enum {
                          8-bit slices (FP64-level accuracy); everything else FP64 */
 } dclno_precision;
 
+/* Eigenproblem of the LNOs (dclno_set_lno_mode). */
+typedef enum {
+    DCLNO_LNO_PAPER = 0,  /* the nonsymmetric Lambda_0i = (rho S)_{0i,0i} of Eq. (Lambda) */
+    DCLNO_LNO_SYM = 1     /* the projector form (S rho S)_{0i,0i} v = lambda S_ii v */
+} dclno_lno_mode;
+
 /* LNO eigenvalue flags returned by dclno_get_lnos (bit set per atom). */
 #define DCLNO_LNO_COMPLEX_SELECTED 1 /* a selected eigenvalue of Lambda is complex */
 #define DCLNO_LNO_PAIR_SPLIT 2       /* a complex pair straddles the cut; its real part was kept */
@@ -201,6 +207,26 @@ dclno_status dclno_set_lno_threshold(dclno_ctx *ctx, int on, double lambda_th);
 dclno_status dclno_get_lno_counts(dclno_ctx *ctx, int *counts);
 
 /*
+ * Eigenproblem of the next dclno_compute_lnos.  DCLNO_LNO_PAPER (the default) is
+ * the paper's nonsymmetric Lambda_0i (Eq. (Lambda), Eq. (eigendecomp)).
+ * DCLNO_LNO_SYM takes the same selection from the symmetric-definite projector
+ * form: G_i v = lambda S_ii v with G_i = (S rho S)_{0i,0i} =
+ * sum_{Ra,Rb} S_{0i,Ra} rho_{Ra,Rb} S_{Rb,0i}, the on-site block of the
+ * occupied-space projector in the PAO metric (Sec. II.B); only the symmetric part
+ * of G_i enters (the block for (rho + rho^T)/2).  Its eigenvalues are real and lie
+ * in [0, 1] when rho is a Fermi projector; the leading k_lno eigenvectors (or
+ * those >= lambda_th in threshold mode) are kept, in the same canonical basis.
+ * Eigenpairs by Cholesky of S_ii, congruence and cyclic Jacobi.  G_i costs
+ * |row i| x |row a| block products per atom (about the square of the neighbour
+ * count: far more than Lambda_0i).  Row i's block keys are held in shared memory:
+ * a row longer than about 24,000 blocks is refused (DCLNO_ERR_ARG) at
+ * dclno_compute_lnos.  An S_ii that is not positive definite fails with
+ * DCLNO_ERR_NOT_SPD (atom in the message).  Errors: DCLNO_ERR_ARG for another
+ * mode value.
+ */
+dclno_status dclno_set_lno_mode(dclno_ctx *ctx, dclno_lno_mode mode);
+
+/*
  * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
  * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
  * implicit QL on the two halves of the tridiagonal matrix torn at n/2 (Cuppen's
@@ -321,7 +347,9 @@ dclno_status dclno_get_spectrum(dclno_ctx *ctx, double *eps_out, double *q_out);
 /*
  * LNOs after dclno_compute_lnos, atom by atom: V_out [sum_i M_i k] (host, the
  * M_i x k block of atom i row-major), lam_re/lam_im [sum_i M_i] (host, Lambda
- * eigenvalues sorted by real part descending), flags [N] (host).  All nullable.
+ * eigenvalues sorted by real part descending; in DCLNO_LNO_SYM mode the
+ * eigenvalues of G_i v = lambda S_ii v, imaginary parts 0), flags [N] (host).
+ * All nullable.
  */
 dclno_status dclno_get_lnos(dclno_ctx *ctx, double *V_out, double *lam_re,
                             double *lam_im, int *flags);

@@ -19,9 +19,10 @@ One step on device arrays (``s`` holds the BSR structure and values of H, S)::
 or ``ctx.step(rho_in, rho_out, n_electrons, kT)`` for all of it, and
 ``ctx.scf_run(rho, nsteps, 0.3, n_electrons, kT, use_graph=True)`` for an SCF
 loop with linear mixing.  ``set_workspace_limit`` (memory-admitted batches),
-``set_lno_threshold`` (lambda_th selection) and ``set_autotune`` adjust the run.
+``set_lno_threshold`` (lambda_th selection), ``set_lno_mode`` (the symmetric
+projector form of the LNO eigenproblem) and ``set_autotune`` adjust the run.
 """
 from ._lib import (  # noqa: F401
-    DCLNO_FP64, DCLNO_MIXED, LIB_PATH, Context, DclnoError, STATUS_NAMES, exported_symbols, load_library,
+    DCLNO_FP64, DCLNO_MIXED, DCLNO_LNO_PAPER, DCLNO_LNO_SYM, LIB_PATH, Context, DclnoError, STATUS_NAMES, exported_symbols, load_library,
     find_mu_noalloc, measure_fp64_peaks,
 )

@@ -11,6 +11,8 @@ LIB_PATH = os.path.join(_HERE, "libdclno.so")
 
 DCLNO_FP64 = 0
 DCLNO_MIXED = 1
+DCLNO_LNO_PAPER = 0
+DCLNO_LNO_SYM = 1
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD", 5: "ERR_NO_BRACKET",
                 6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT", 8: "ERR_NO_LNOS"}
 
@@ -21,7 +23,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
-           "dclno_get_lno_counts"]
+           "dclno_get_lno_counts", "dclno_set_lno_mode"]
 
 
 class DclnoError(RuntimeError):
@@ -87,6 +89,7 @@ def load_library():
         "dclno_get_tuning": ([P, I, P, P], I),
         "dclno_build_clusters_kappa": ([P, ctypes.POINTER(dclno_system), D, I, D, D], I),
         "dclno_set_lno_threshold": ([P, I, D], I),
+        "dclno_set_lno_mode": ([P, I], I),
         "dclno_get_lno_counts": ([P, P], I),
     }
     for name, (args, res) in sigs.items():
@@ -188,6 +191,10 @@ class Context:
         """Keep the LNOs with eigenvalue >= lambda_th (at most k_lno per atom); None = fixed k_lno."""
         on = lambda_th is not None
         self._check(self.lib.dclno_set_lno_threshold(self.h, int(on), float(lambda_th) if on else 0.0))
+
+    def set_lno_mode(self, mode):
+        """DCLNO_LNO_PAPER (Lambda_0i, the default) or DCLNO_LNO_SYM ((S rho S)_ii v = lambda S_ii v)."""
+        self._check(self.lib.dclno_set_lno_mode(self.h, int(mode)))
 
     def lno_counts(self):
         """LNOs per atom of the last LNO computation."""

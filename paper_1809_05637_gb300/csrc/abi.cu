@@ -290,6 +290,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     c->N = N;
     c->nnzb = sys->nnzb;
     c->nval = sys->nval;
+    c->max_row = 0;
     c->norb.assign(sys->norb, sys->norb + N);
     c->row_ptr.assign(sys->row_ptr, sys->row_ptr + N + 1);
     c->col.assign(sys->col, sys->col + sys->nnzb);
@@ -328,6 +329,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
             if (j == i && s0 == 0 && s1 == 0 && s2 == 0) onsite[i] = b;
         }
         if (onsite[i] < 0) return set_err(c, DCLNO_ERR_ARG, "missing on-site block of atom " + std::to_string(i));
+        c->max_row = std::max(c->max_row, c->row_ptr[i + 1] - c->row_ptr[i]);
         if (!pao_only && (k_lno > c->norb[i] || c->norb[i] > DCLNO_MAX_M_LNO))
             return set_err(c, DCLNO_ERR_ARG, "atom " + std::to_string(i) + ": LNOs need k_lno <= M_i <= 16");
     }
@@ -600,6 +602,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
         return cuda_err(c, e, "cudaMalloc (cluster workspace)");
     }
     st = launch_pair_index(c);
+    if (st == DCLNO_OK && c->has_lno_region) st = prepare_lno_kernels(c);
     if (st != DCLNO_OK) {
         free_clusters(c);
         return st;
@@ -681,6 +684,15 @@ extern "C" dclno_status dclno_set_lno_threshold(dclno_ctx* c, int on, double lam
     if (on && !(lambda_th == lambda_th)) return set_err(c, DCLNO_ERR_ARG, "dclno_set_lno_threshold: lambda_th is NaN");
     c->lno_th_on = on != 0;
     c->lno_th = lambda_th;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_lno_mode(dclno_ctx* c, dclno_lno_mode mode) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (mode != DCLNO_LNO_PAPER && mode != DCLNO_LNO_SYM)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_set_lno_mode: unknown mode " + std::to_string((int)mode));
+    c->lno_mode = (int)mode;
     return DCLNO_OK;
 }
 

@@ -172,6 +172,9 @@ struct dclno_ctx {
     int* d_kat = nullptr;               // LNOs of each atom (k_lno without a threshold)
     std::vector<int> kat;
     bool relaid = false;                // the layout follows threshold-selected counts
+    // LNO eigenproblem: 0 = the paper's nonsymmetric Lambda, 1 = (S rho S)_ii v = lambda S_ii v
+    int lno_mode = 0;
+    long long max_row = 0;              // longest BSR row (blocks)
     std::vector<char> layout_split;     // per cluster: laid out as a torn problem
 
     // solve / mu
@@ -237,6 +240,7 @@ dclno_status cuda_err(dclno_ctx* c, cudaError_t e, const char* where);
     } while (0)
 
 // kernels' host-side launchers (one per .cu file)
+dclno_status prepare_lno_kernels(dclno_ctx* c);
 dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho);
 dclno_status relayout_clusters(dclno_ctx* c);
 dclno_status launch_lno_blocks(dclno_ctx* c);

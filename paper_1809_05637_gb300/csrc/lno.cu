@@ -4,6 +4,11 @@
 //              double-shift QR), eigenvectors of the k eigenvalues of largest real part by
 //              inverse iteration in real arithmetic (Eq. (eigendecomp), Eq. (apop_Lambda)),
 //              returned as an S_ii-orthonormal basis of their span; one thread per atom.
+// Symmetric mode (the projector form of the same selection):
+//   k_projector  G_i = (S rho S)_{0i,0i} = sum_{Ra,Rb} S_{0i,Ra} rho_{Ra,Rb} S_{Rb,0i}; one CTA
+//                per atom
+//   k_lno_eig<true>  G_i v = lambda S_ii v for the symmetric part of G_i (Cholesky of S_ii,
+//                congruence, cyclic Jacobi), the leading k eigenvectors v = L^-T y.
 #include "dclno_internal.cuh"
 
 #define MM DCLNO_MAX_M_LNO
@@ -43,6 +48,126 @@ __global__ void k_lambda(int N, const int* __restrict__ norb, const long long* _
     for (int t = 0; t < MM * MM / 32; ++t) {
         const int e = lane + 32 * t;
         if (e < mi * mi) Lam[loff[i] + e] = acc[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Projector blocks.  rho_{Ra,Rb} = rho_{0a,(Rb-Ra)b}: block (a, t1) of row i and block
+// (b, t2) of row a reach atom b in cell t1 + t2; its overlap with the centre is block
+// (b, t1 + t2) of row i, transposed.  So G_i = sum_p S_p W_p with
+// W_p = sum_q rho_q S_{r(q)}^T (M_a x M_i), r(q) found by binary search among row i's
+// keys (held in shared memory); absent blocks contribute nothing.  Warps take the
+// blocks p of row i; the lanes of a warp look up 32 blocks q at a time and then walk
+// the hits in lane order, each lane owning entries of W_p and of G_i.
+// ---------------------------------------------------------------------------
+#define PROJ_WARPS 8
+
+__device__ inline int add_packed_shift(int p, int q) {
+    int a0, a1, a2, b0, b1, b2;
+    unpack_shift(p, a0, a1, a2);
+    unpack_shift(q, b0, b1, b2);
+    const int s0 = a0 + b0, s1 = a1 + b1, s2 = a2 + b2;
+    if (s0 < -128 || s0 > 127 || s1 < -128 || s1 > 127 || s2 < -128 || s2 > 127) return -1;
+    return pack_shift(s0, s1, s2);
+}
+
+__device__ inline int find_key(const long long* keys, int len, long long want) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < want)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < len && keys[lo] == want) ? lo : -1;
+}
+
+__global__ void __launch_bounds__(PROJ_WARPS * 32)
+    k_projector(const int* __restrict__ norb, const long long* __restrict__ row_ptr,
+                const long long* __restrict__ key, const long long* __restrict__ blk_off,
+                const long long* __restrict__ loff, const double* __restrict__ rho,
+                const double* __restrict__ S, double* __restrict__ G) {
+    extern __shared__ long long sh_key[];          // keys of row i, sorted
+    __shared__ double sh_w[PROJ_WARPS][MM * MM];   // W_p of each warp (M_a x M_i)
+    __shared__ double sh_g[PROJ_WARPS][MM * MM];   // partial G_i of each warp
+    const unsigned full = 0xffffffffu;
+    const int i = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r0 = row_ptr[i];
+    const int len = (int)(row_ptr[i + 1] - r0);
+    for (int t = threadIdx.x; t < len; t += blockDim.x) sh_key[t] = key[r0 + t];
+    __syncthreads();
+    const int mi = norb[i];
+    double g[MM * MM / 32];
+#pragma unroll
+    for (int t = 0; t < MM * MM / 32; ++t) g[t] = 0.0;
+    for (int p = warp; p < len; p += PROJ_WARPS) {
+        const long long kp = sh_key[p];
+        const int a = (int)(kp >> 24), t1 = (int)(kp & 0xffffff);
+        const int ma = norb[a];
+        double w[MM * MM / 32];
+#pragma unroll
+        for (int t = 0; t < MM * MM / 32; ++t) w[t] = 0.0;
+        const long long q1 = row_ptr[a + 1];
+        for (long long qb = row_ptr[a]; qb < q1; qb += 32) {
+            const long long q = qb + lane;
+            int r = -1, b = 0;
+            if (q < q1) {
+                const long long kq = key[q];
+                b = (int)(kq >> 24);
+                const int ps = add_packed_shift(t1, (int)(kq & 0xffffff));
+                if (ps >= 0) r = find_key(sh_key, len, block_key(b, ps));
+            }
+            unsigned hit = __ballot_sync(full, r >= 0);
+            while (hit) {
+                const int src = __ffs(hit) - 1;
+                hit &= hit - 1;
+                const long long qs = __shfl_sync(full, q, src);
+                const int rs = __shfl_sync(full, r, src);
+                const int mb = norb[__shfl_sync(full, b, src)];
+                const double* rq = rho + blk_off[qs];     // rho_{0a,t2 b}: M_a x M_b
+                const double* sr = S + blk_off[r0 + rs];  // S_{0i,(t1+t2) b}: M_i x M_b
+#pragma unroll
+                for (int t = 0; t < MM * MM / 32; ++t) {
+                    const int e = lane + 32 * t;
+                    if (e < ma * mi) {
+                        const int x = e / mi, cc = e % mi;
+                        double s = 0.0;
+                        for (int u = 0; u < mb; ++u) s = fma(rq[x * mb + u], sr[cc * mb + u], s);
+                        w[t] += s;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < MM * MM / 32; ++t) {
+            const int e = lane + 32 * t;
+            if (e < ma * mi) sh_w[warp][e] = w[t];
+        }
+        __syncwarp();
+        const double* sp = S + blk_off[r0 + p];  // S_{0i,t1 a}: M_i x M_a
+#pragma unroll
+        for (int t = 0; t < MM * MM / 32; ++t) {
+            const int e = lane + 32 * t;
+            if (e < mi * mi) {
+                const int y = e / mi, cc = e % mi;
+                double s = 0.0;
+                for (int x = 0; x < ma; ++x) s = fma(sp[y * ma + x], sh_w[warp][x * mi + cc], s);
+                g[t] += s;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < MM * MM / 32; ++t) {
+        const int e = lane + 32 * t;
+        if (e < mi * mi) sh_g[warp][e] = g[t];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < mi * mi; e += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < PROJ_WARPS; ++w) s += sh_g[w][e];
+        G[loff[i] + e] = s;
     }
 }
 
@@ -234,9 +359,55 @@ __device__ static void lu_solve(double* Mx, int n, double* b, double tiny) {
     }
 }
 
+// Cyclic Jacobi (Golub & Van Loan, Sec. 8.5) on the symmetric m x m matrix A: the
+// eigenvalues are left on its diagonal, the rotations accumulate in Y (eigenvectors in
+// columns).  Returns 0 once the off-diagonal mass is below 1e-30 of the total.
+__device__ static int jacobi_sym(double* A, double* Y, int m) {
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) Y[r * m + c] = (r == c) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) {
+                const double v = A[r * m + c] * A[r * m + c];
+                tot += v;
+                if (r != c) off += v;
+            }
+        if (off <= 1e-30 * tot) return 0;
+        for (int p = 0; p + 1 < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                // rotation J (J_pp = J_qq = cs, J_pq = sn, J_qp = -sn) with (J^T A J)_pq = 0
+                const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                double tn = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+                if (theta < 0.0) tn = -tn;
+                const double cs = 1.0 / sqrt(tn * tn + 1.0), sn = tn * cs;
+                for (int u = 0; u < m; ++u) {
+                    const double up = A[u * m + p], uq = A[u * m + q];
+                    A[u * m + p] = cs * up - sn * uq;
+                    A[u * m + q] = sn * up + cs * uq;
+                }
+                for (int u = 0; u < m; ++u) {
+                    const double pu = A[p * m + u], qu = A[q * m + u];
+                    A[p * m + u] = cs * pu - sn * qu;
+                    A[q * m + u] = sn * pu + cs * qu;
+                }
+                for (int u = 0; u < m; ++u) {
+                    const double yp = Y[u * m + p], yq = Y[u * m + q];
+                    Y[u * m + p] = cs * yp - sn * yq;
+                    Y[u * m + q] = sn * yp + cs * yq;
+                }
+            }
+    }
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
-// One thread per atom
+// One thread per atom.  SYM = false: Lam holds Lambda_0i (the paper's problem);
+// SYM = true: Lam holds G_i = (S rho S)_{0i,0i} (k_projector).
 // ---------------------------------------------------------------------------
+template <bool SYM>
 __global__ void k_lno_eig(int N, int k, int use_th, double lam_th, const int* __restrict__ norb,
                           const long long* __restrict__ loff,
                           const long long* __restrict__ moff, const long long* __restrict__ voff,
@@ -250,105 +421,184 @@ __global__ void k_lno_eig(int N, int k, int use_th, double lam_th, const int* __
     double A[MM * MM], wr[MM], wi[MM];
     int ord[MM];
     const double* L = Lam + loff[i];
-    double anorm = 0.0;
-    for (int e = 0; e < m * m; ++e) {
-        A[e] = L[e];
-        anorm += L[e] * L[e];
-    }
-    anorm = sqrt(anorm);
-    if (anorm == 0.0) anorm = 1.0;
-    hessenberg_reduce(A, m);
-    if (francis_qr(A, m, wr, wi) != 0) {
-        status[i] = ST_NOT_CONVERGED;
-        return;
-    }
-    // order: real part descending, then imaginary part descending
-    for (int t = 0; t < m; ++t) ord[t] = t;
-    for (int a = 1; a < m; ++a) {
-        int v = ord[a], b = a - 1;
-        while (b >= 0 && (wr[ord[b]] < wr[v] || (wr[ord[b]] == wr[v] && wi[ord[b]] < wi[v]))) {
-            ord[b + 1] = ord[b];
-            --b;
-        }
-        ord[b + 1] = v;
-    }
-    for (int t = 0; t < m; ++t) {
-        lam_re[moff[i] + t] = wr[ord[t]];
-        lam_im[moff[i] + t] = wi[ord[t]];
-    }
-    // eigenvectors of the leading eigenvalues
     double* Vi = V + voff[i];  // m x k, row-major
-    int fl = 0, got = 0, pos = 0;
-    const double tiny = 1e-300;
-    while (got < k && pos < m) {
-        const double lr = wr[ord[pos]], li = wi[ord[pos]];
-        if (use_th && lr < lam_th) break;  // threshold selection: eigenvalues >= lambda_th only
-        const double sh = lr + 1e-13 * anorm;  // shifted off the eigenvalue to keep the solve regular
-        if (li == 0.0) {
+    const double* Sii = S + blk_off[onsite[i]];
+    int fl = 0, got = 0;
+    if constexpr (SYM) {
+        double Lc[MM * MM], Y[MM * MM];
+        // S_ii = Lc Lc^T
+        for (int j = 0; j < m; ++j) {
+            double s = Sii[j * m + j];
+            for (int u = 0; u < j; ++u) s -= Lc[j * m + u] * Lc[j * m + u];
+            if (!(s > 0.0)) {
+                status[i] = ST_NOT_SPD;
+                return;
+            }
+            Lc[j * m + j] = sqrt(s);
+            for (int r = j + 1; r < m; ++r) {
+                double v = Sii[r * m + j];
+                for (int u = 0; u < j; ++u) v -= Lc[r * m + u] * Lc[j * m + u];
+                Lc[r * m + j] = v / Lc[j * m + j];
+            }
+            for (int r = 0; r < j; ++r) Lc[r * m + j] = 0.0;
+        }
+        // A = Lc^-1 Gs Lc^-T with Gs the symmetric part of G: two forward substitutions
+        // (Lc^-1 Gs, transposed, Lc^-1 again), then symmetrised
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) A[r * m + c] = 0.5 * (L[r * m + c] + L[c * m + r]);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int c = 0; c < m; ++c)
+                for (int r = 0; r < m; ++r) {
+                    double v = A[r * m + c];
+                    for (int u = 0; u < r; ++u) v -= Lc[r * m + u] * A[u * m + c];
+                    A[r * m + c] = v / Lc[r * m + r];
+                }
+            for (int r = 0; r < m; ++r)
+                for (int c = r + 1; c < m; ++c) {
+                    const double x = A[r * m + c];
+                    A[r * m + c] = A[c * m + r];
+                    A[c * m + r] = x;
+                }
+        }
+        for (int r = 0; r < m; ++r)
+            for (int c = r + 1; c < m; ++c) {
+                const double x = 0.5 * (A[r * m + c] + A[c * m + r]);
+                A[r * m + c] = x;
+                A[c * m + r] = x;
+            }
+        if (jacobi_sym(A, Y, m) != 0) {
+            status[i] = ST_NOT_CONVERGED;
+            return;
+        }
+        // eigenvalues descending (ties: lower index first)
+        for (int t = 0; t < m; ++t) {
+            wr[t] = A[t * m + t];
+            ord[t] = t;
+        }
+        for (int a = 1; a < m; ++a) {
+            int v = ord[a], b = a - 1;
+            while (b >= 0 && wr[ord[b]] < wr[v]) {
+                ord[b + 1] = ord[b];
+                --b;
+            }
+            ord[b + 1] = v;
+        }
+        for (int t = 0; t < m; ++t) {
+            lam_re[moff[i] + t] = wr[ord[t]];
+            lam_im[moff[i] + t] = 0.0;
+        }
+        // the leading k (with the threshold: those >= lambda_th), v = Lc^-T y
+        while (got < k && got < m && !(use_th && wr[ord[got]] < lam_th)) {
+            const int col = ord[got];
             double x[MM];
-            for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * r;
-            for (int it = 0; it < 4; ++it) {
-                for (int e = 0; e < m * m; ++e) A[e] = L[e];
-                for (int r = 0; r < m; ++r) A[r * m + r] -= sh;
-                lu_solve(A, m, x, tiny * anorm);
-                double nr = 0.0;
-                for (int r = 0; r < m; ++r) nr += x[r] * x[r];
-                nr = rsqrt(nr);
-                for (int r = 0; r < m; ++r) x[r] *= nr;
+            for (int r = m - 1; r >= 0; --r) {
+                double v = Y[r * m + col];
+                for (int u = r + 1; u < m; ++u) v -= Lc[u * m + r] * x[u];
+                x[r] = v / Lc[r * m + r];
             }
             for (int r = 0; r < m; ++r) Vi[r * k + got] = x[r];
             ++got;
-            ++pos;
-        } else {
-            // (Lambda - (sh + i li) I)(x + i y) = b in real form:
-            // [[Lambda - sh I, li I], [-li I, Lambda - sh I]] [x; y] = [br; bi]
-            fl |= DCLNO_LNO_COMPLEX_SELECTED;
-            double B[4 * MM * MM];
-            double z[2 * MM];
-            const int n2 = 2 * m;
-            for (int r = 0; r < n2; ++r) z[r] = (r < m) ? 1.0 + 0.01 * r : 0.02 * (r - m);
-            for (int it = 0; it < 4; ++it) {
-                for (int r = 0; r < m; ++r)
-                    for (int c = 0; c < m; ++c) {
-                        const double a = L[r * m + c] - (r == c ? sh : 0.0);
-                        B[r * n2 + c] = a;
-                        B[(r + m) * n2 + c + m] = a;
-                        B[r * n2 + c + m] = (r == c) ? li : 0.0;
-                        B[(r + m) * n2 + c] = (r == c) ? -li : 0.0;
-                    }
-                lu_solve(B, n2, z, tiny * anorm);
-                double nr = 0.0;
-                for (int r = 0; r < n2; ++r) nr += z[r] * z[r];
-                nr = rsqrt(nr);
-                for (int r = 0; r < n2; ++r) z[r] *= nr;
+        }
+    } else {
+        double anorm = 0.0;
+        for (int e = 0; e < m * m; ++e) {
+            A[e] = L[e];
+            anorm += L[e] * L[e];
+        }
+        anorm = sqrt(anorm);
+        if (anorm == 0.0) anorm = 1.0;
+        hessenberg_reduce(A, m);
+        if (francis_qr(A, m, wr, wi) != 0) {
+            status[i] = ST_NOT_CONVERGED;
+            return;
+        }
+        // order: real part descending, then imaginary part descending
+        for (int t = 0; t < m; ++t) ord[t] = t;
+        for (int a = 1; a < m; ++a) {
+            int v = ord[a], b = a - 1;
+            while (b >= 0 && (wr[ord[b]] < wr[v] || (wr[ord[b]] == wr[v] && wi[ord[b]] < wi[v]))) {
+                ord[b + 1] = ord[b];
+                --b;
             }
-            // phase: largest-magnitude component real and positive
-            int jm = 0;
-            double best = -1.0;
-            for (int r = 0; r < m; ++r) {
-                double a2 = z[r] * z[r] + z[r + m] * z[r + m];
-                if (a2 > best) {
-                    best = a2;
-                    jm = r;
+            ord[b + 1] = v;
+        }
+        for (int t = 0; t < m; ++t) {
+            lam_re[moff[i] + t] = wr[ord[t]];
+            lam_im[moff[i] + t] = wi[ord[t]];
+        }
+        // eigenvectors of the leading eigenvalues
+        int pos = 0;
+        const double tiny = 1e-300;
+        while (got < k && pos < m) {
+            const double lr = wr[ord[pos]], li = wi[ord[pos]];
+            if (use_th && lr < lam_th) break;  // threshold selection: eigenvalues >= lambda_th only
+            const double sh = lr + 1e-13 * anorm;  // shifted off the eigenvalue to keep the solve regular
+            if (li == 0.0) {
+                double x[MM];
+                for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * r;
+                for (int it = 0; it < 4; ++it) {
+                    for (int e = 0; e < m * m; ++e) A[e] = L[e];
+                    for (int r = 0; r < m; ++r) A[r * m + r] -= sh;
+                    lu_solve(A, m, x, tiny * anorm);
+                    double nr = 0.0;
+                    for (int r = 0; r < m; ++r) nr += x[r] * x[r];
+                    nr = rsqrt(nr);
+                    for (int r = 0; r < m; ++r) x[r] *= nr;
                 }
-            }
-            const double pr = z[jm], pi = z[jm + m], pn = rsqrt(pr * pr + pi * pi);
-            const double cr = pr * pn, ci = -pi * pn;  // multiply by conj(z_jm)/|z_jm|
-            for (int r = 0; r < m; ++r) {
-                const double xr = z[r] * cr - z[r + m] * ci;
-                const double xi = z[r] * ci + z[r + m] * cr;
-                z[r] = xr;
-                z[r + m] = xi;
-            }
-            for (int r = 0; r < m; ++r) Vi[r * k + got] = z[r];
-            ++got;
-            if (got < k) {
-                for (int r = 0; r < m; ++r) Vi[r * k + got] = z[r + m];
+                for (int r = 0; r < m; ++r) Vi[r * k + got] = x[r];
                 ++got;
+                ++pos;
             } else {
-                fl |= DCLNO_LNO_PAIR_SPLIT;
+                // (Lambda - (sh + i li) I)(x + i y) = b in real form:
+                // [[Lambda - sh I, li I], [-li I, Lambda - sh I]] [x; y] = [br; bi]
+                fl |= DCLNO_LNO_COMPLEX_SELECTED;
+                double B[4 * MM * MM];
+                double z[2 * MM];
+                const int n2 = 2 * m;
+                for (int r = 0; r < n2; ++r) z[r] = (r < m) ? 1.0 + 0.01 * r : 0.02 * (r - m);
+                for (int it = 0; it < 4; ++it) {
+                    for (int r = 0; r < m; ++r)
+                        for (int c = 0; c < m; ++c) {
+                            const double a = L[r * m + c] - (r == c ? sh : 0.0);
+                            B[r * n2 + c] = a;
+                            B[(r + m) * n2 + c + m] = a;
+                            B[r * n2 + c + m] = (r == c) ? li : 0.0;
+                            B[(r + m) * n2 + c] = (r == c) ? -li : 0.0;
+                        }
+                    lu_solve(B, n2, z, tiny * anorm);
+                    double nr = 0.0;
+                    for (int r = 0; r < n2; ++r) nr += z[r] * z[r];
+                    nr = rsqrt(nr);
+                    for (int r = 0; r < n2; ++r) z[r] *= nr;
+                }
+                // phase: largest-magnitude component real and positive
+                int jm = 0;
+                double best = -1.0;
+                for (int r = 0; r < m; ++r) {
+                    double a2 = z[r] * z[r] + z[r + m] * z[r + m];
+                    if (a2 > best) {
+                        best = a2;
+                        jm = r;
+                    }
+                }
+                const double pr = z[jm], pi = z[jm + m], pn = rsqrt(pr * pr + pi * pi);
+                const double cr = pr * pn, ci = -pi * pn;  // multiply by conj(z_jm)/|z_jm|
+                for (int r = 0; r < m; ++r) {
+                    const double xr = z[r] * cr - z[r + m] * ci;
+                    const double xi = z[r] * ci + z[r + m] * cr;
+                    z[r] = xr;
+                    z[r + m] = xi;
+                }
+                for (int r = 0; r < m; ++r) Vi[r * k + got] = z[r];
+                ++got;
+                if (got < k) {
+                    for (int r = 0; r < m; ++r) Vi[r * k + got] = z[r + m];
+                    ++got;
+                } else {
+                    fl |= DCLNO_LNO_PAIR_SPLIT;
+                }
+                pos += 2;
             }
-            pos += 2;
         }
     }
     // S_ii-orthonormal basis of the span (Gram-Schmidt in eigenvalue order, twice);
@@ -356,7 +606,6 @@ __global__ void k_lno_eig(int N, int k, int use_th, double lam_th, const int* __
     const int kk = got;
     for (int c = kk; c < k; ++c)
         for (int r = 0; r < m; ++r) Vi[r * k + c] = 0.0;
-    const double* Sii = S + blk_off[onsite[i]];
     for (int pass = 0; pass < 2; ++pass) {
         for (int c = 0; c < kk; ++c) {
             for (int d = 0; d < c; ++d) {
@@ -395,9 +644,27 @@ __global__ void k_lno_eig(int N, int k, int use_th, double lam_th, const int* __
     status[i] = ST_OK;
 }
 
+// row i's keys sit in dynamic shared memory beside the 32 KB of static tiles; the
+// limit is raised once per build, outside any stream capture
+#define PROJ_MAX_DYN ((size_t)227 * 1024 - 2 * PROJ_WARPS * MM * MM * sizeof(double))
+
+dclno_status prepare_lno_kernels(dclno_ctx* c) {
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_projector, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJ_MAX_DYN));
+    return DCLNO_OK;
+}
+
 dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
     const int N = c->N;
-    {
+    const bool sym = c->lno_mode == DCLNO_LNO_SYM;
+    if (sym) {
+        const size_t dyn = sizeof(long long) * (size_t)std::max<long long>(c->max_row, 1);
+        if (dyn > PROJ_MAX_DYN)
+            return set_err(c, DCLNO_ERR_ARG, "symmetric LNO mode: a BSR row of " + std::to_string(c->max_row) +
+                                                 " blocks does not fit in shared memory");
+        ProfScope ps__(c, "k_projector");
+        k_projector<<<N, PROJ_WARPS * 32, dyn, c->stream>>>(c->d_norb, c->d_row_ptr, c->d_key, c->d_blk_off,
+                                                             c->d_loff, rho, c->S, c->d_Lambda);
+    } else {
         ProfScope ps__(c, "k_lambda");
         k_lambda<<<(N * 32 + 127) / 128, 128, 0, c->stream>>>(N, c->d_norb, c->d_row_ptr, c->d_key, c->d_blk_off,
                                                           c->d_loff, rho, c->S, c->d_Lambda);
@@ -406,10 +673,10 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
     {
         ProfScope ps__(c, "k_lno_eig");
         const int use_th = c->lno_th_on ? 1 : 0;
-        k_lno_eig<<<(N + 63) / 64, 64, 0, c->stream>>>(N, c->k_lno, use_th, c->lno_th, c->d_norb, c->d_loff,
-                                                   c->d_moff, c->d_voff, c->d_onsite, c->d_blk_off, c->S,
-                                                   c->d_Lambda, c->d_V, c->d_lam_re, c->d_lam_im, c->d_lflags,
-                                                   c->d_kat, c->d_status);
+        auto kern = sym ? k_lno_eig<true> : k_lno_eig<false>;
+        kern<<<(N + 63) / 64, 64, 0, c->stream>>>(N, c->k_lno, use_th, c->lno_th, c->d_norb, c->d_loff, c->d_moff,
+                                                 c->d_voff, c->d_onsite, c->d_blk_off, c->S, c->d_Lambda, c->d_V,
+                                                 c->d_lam_re, c->d_lam_im, c->d_lflags, c->d_kat, c->d_status);
     }
     DCLNO_LAUNCHED(c);
     if (c->deferred) return launch_status_or(c);
@@ -419,6 +686,8 @@ dclno_status launch_lambda_lno(dclno_ctx* c, const double* rho) {
     for (int i = 0; i < N; ++i) {
         if (st[i] == ST_NOT_CONVERGED)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "LNO eigenvalues of atom " + std::to_string(i) + " did not converge");
+        if (st[i] == ST_NOT_SPD)
+            return set_err(c, DCLNO_ERR_NOT_SPD, "on-site overlap of atom " + std::to_string(i) + " is not positive definite");
         if (st[i] != ST_OK)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "LNO basis of atom " + std::to_string(i) + " is degenerate");
     }
