@@ -37,7 +37,7 @@ CPU_SAMPLE_CLUSTERS = 8
 # DRAM read + write of one FP64 k_tridiag launch, captured by ncu on each workload
 # itself (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture; see
 # profiles/k_tridiag_fp64_rocksalt1728.md and profiles/k_tridiag_fp64_small.md)
-TRIDIAG_TRAFFIC = {"rocksalt1728": 842008137216.0 + 60257138176.0, "small64": 384489728.0 + 284888320.0}
+TRIDIAG_TRAFFIC = {"rocksalt1728": 928106789376.0 + 63594331904.0, "small64": 371203584.0 + 286477056.0}
 
 
 def parse():

@@ -269,6 +269,34 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Householder reflector k of the tridiagonalisation, H_k = I - tau v v^T with v_{k+1} = 1
+// and v_t (t > k+1) = v[t] (row k of the matrix's upper triangle, where k_tridiag keeps a
+// contiguous copy), applied as x <- x - tau (x . v) v to the R consecutive rows of the
+// shared-memory matrix X (row stride ldx) that this warp owns.  Each lane touches the
+// entries t = lane (mod 32) only, so the rows need no synchronisation between
+// successive reflectors.
+#define DCLNO_RPW 4  // rows per warp at most
+template <int R>
+__device__ __forceinline__ void warp_reflect(double* X, int ldx, int k, int n, const double* __restrict__ v,
+                                             double tau) {
+    const int lane = threadIdx.x & 31;
+    double u[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) u[j] = 0.0;
+    for (int t = k + 1 + lane; t < n; t += 32) {
+        const double vt = v[t];
+#pragma unroll
+        for (int j = 0; j < R; ++j) u[j] = fma(X[(size_t)j * ldx + t], vt, u[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) u[j] = tau * warp_sum(u[j]);
+    for (int t = k + 1 + lane; t < n; t += 32) {
+        const double vt = v[t];
+#pragma unroll
+        for (int j = 0; j < R; ++j) X[(size_t)j * ldx + t] = fma(-u[j], vt, X[(size_t)j * ldx + t]);
+    }
+}
+
 // One logged QL sweep applied to a strided vector x_t = X[t * stride]:
 // rotations u = 0 .. cnt-1 act on (i, i+1) with i = i0 - u, as column updates
 //   x_{i+1} <- s x_i + c x_{i+1},  x_i <- c x_i - s x_{i+1}

@@ -280,48 +280,77 @@ __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, co
     }
 }
 
-// G <- Q G = H_0 H_1 ... H_{n-3} G (reflectors applied from the last one), then
-// X = L^-T G by back substitution; X overwrites G.
+// X = L^-T Q G for the columns of G ([n][w] at aux_off + 3 ld, w = mc or 2 mc): the
+// reflectors applied in reverse order (Q = H_0 ... H_{n-3}), then L^T X = G by back
+// substitution.  Columns are independent: chunks of rch columns are held in shared
+// memory (one row of stride n per column), each warp carries its columns through all
+// reflectors and the triangular solve (rho_qx_warp), with no block barriers.
+// R columns owned by one warp (rows of X, stride n): X <- H_0 ... H_{n-3} X (the
+// reflectors from the last one), then L^T X_new = X by back substitution.
+template <int R>
+__device__ static void rho_qx_warp(double* X, int n, const double* __restrict__ A, const double* __restrict__ L,
+                                   int ld, const double* __restrict__ tau, const double* __restrict__ invd) {
+    const int lane = threadIdx.x & 31;
+    for (int k = n - 3; k >= 0; --k) {
+        const double tk = tau[k];
+        if (tk != 0.0) warp_reflect<R>(X, n, k, n, A + (size_t)k * ld, tk);
+    }
+    // x_t = g_t / L[t][t], then g_s -= L[t][s] x_t for s < t
+    for (int t = n - 1; t >= 0; --t) {
+        const double it = invd[t];
+        double xt[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) xt[j] = X[(size_t)j * n + t] * it;
+        __syncwarp();
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < R; ++j) X[(size_t)j * n + t] = xt[j];
+        const double* Lt = L + (size_t)t * ld;
+        for (int s = lane; s < t; s += 32) {
+            const double l = Lt[s];
+#pragma unroll
+            for (int j = 0; j < R; ++j) X[(size_t)j * n + s] = fma(-l, xt[j], X[(size_t)j * n + s]);
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDesc* __restrict__ cls,
                                                                 const int* __restrict__ order,
-                                                                double* __restrict__ arena, int with_e) {
+                                                                double* __restrict__ arena, int with_e, int rch) {
     extern __shared__ double sm[];
     const ClusterDesc d = cls[order[blockIdx.x]];
-    const int n = d.n, ld = d.ld, mc = with_e ? 2 * d.mc : d.mc;  // mc here: columns of G
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n = d.n, ld = d.ld, mcw = with_e ? 2 * d.mc : d.mc;  // columns of G
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
     const double* tau = arena + d.aux_off + 2 * ld;
     double* G = arena + d.aux_off + 3 * ld;
-    double* vsh = sm;           // n
-    double* part = sm + n;      // nw x 32
-    for (int k = n - 3; k >= 0; --k) {
-        const double tk = tau[k];
-        if (tk == 0.0) continue;
-        for (int t = k + 1 + threadIdx.x; t < n; t += blockDim.x) vsh[t] = A[(size_t)t * ld + k];
-        __syncthreads();
-        double u = 0.0;
-        if (lane < mc)
-            for (int t = k + 1 + warp; t < n; t += nw) u = fma(vsh[t], G[(size_t)t * mc + lane], u);
-        part[warp * 32 + lane] = u;
-        __syncthreads();
-        if (lane < mc) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += part[w * 32 + lane];
-            s *= tk;
-            for (int t = k + 1 + warp; t < n; t += nw) G[(size_t)t * mc + lane] = fma(-s, vsh[t], G[(size_t)t * mc + lane]);
+    double* invd = sm;      // n: 1 / L[t][t]
+    double* Xs = sm + n;    // rch x n
+    for (int t = threadIdx.x; t < n; t += blockDim.x) invd[t] = 1.0 / L[(size_t)t * ld + t];
+    for (int a0 = 0; a0 < mcw; a0 += rch) {
+        const int cols = min(rch, mcw - a0);
+        for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+            const int t = e / cols, a = e % cols;
+            Xs[(size_t)a * n + t] = G[(size_t)t * mcw + a0 + a];
         }
         __syncthreads();
-    }
-    // L^T X = G: X[t] = G[t] / L[t][t]; then G[s] -= L[t][s] X[t] for s < t
-    for (int t = n - 1; t >= 0; --t) {
-        const double ltt = L[(size_t)t * ld + t];
-        if (threadIdx.x < mc) G[(size_t)t * mc + threadIdx.x] /= ltt;
+        {  // each warp owns a block of consecutive columns (at most DCLNO_RPW)
+            const int rpw = (cols + nw - 1) / nw, r0 = warp * rpw, my = min(rpw, cols - r0);
+            double* Xw = Xs + (size_t)max(r0, 0) * n;
+            switch (my) {
+                case 1: rho_qx_warp<1>(Xw, n, A, L, ld, tau, invd); break;
+                case 2: rho_qx_warp<2>(Xw, n, A, L, ld, tau, invd); break;
+                case 3: rho_qx_warp<3>(Xw, n, A, L, ld, tau, invd); break;
+                case 4: rho_qx_warp<4>(Xw, n, A, L, ld, tau, invd); break;
+                default: break;
+            }
+        }
         __syncthreads();
-        const double* Lt = L + (size_t)t * ld;
-        for (int e = threadIdx.x; e < t * mc; e += blockDim.x) {
-            const int s = e / mc, a = e % mc;
-            G[(size_t)s * mc + a] = fma(-Lt[s], G[(size_t)t * mc + a], G[(size_t)s * mc + a]);
+        for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+            const int t = e / cols, a = e % cols;
+            G[(size_t)t * mcw + a0 + a] = Xs[(size_t)a * n + t];
         }
         __syncthreads();
     }
@@ -403,11 +432,16 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
                                                                       c->d_order + b.obeg, c->d_arena, c->d_iters);
     }
     DCLNO_LAUNCHED(c);
-    const size_t sm = (size_t)(maxn + 32 * (DCLNO_SOLVE_THREADS / 32)) * sizeof(double);
+    // columns per shared-memory chunk of k_rho_qx: at most DCLNO_RPW per warp, within 200 KB
+    const int wcols = with_e ? 2 * b.mcmax : b.mcmax;
+    const int rch = (int)std::min<long long>(std::min(wcols, DCLNO_RPW * (DCLNO_SOLVE_THREADS / 32)),
+                                             200LL * 1024 / 8 / std::max(maxn, 1) - 1);
+    if (rch < 1) return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the density kernel");
+    const size_t sm = (size_t)(rch + 1) * maxn * sizeof(double);
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_rho_qx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
         ProfScope ps__(c, "k_rho_qx");
-        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, with_e);
+        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, with_e, rch);
     }
     DCLNO_LAUNCHED(c);
     const int wpb = 8;

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
             for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) {
                 double v = (r == c + 1) ? 1.0 : A[(size_t)r * ld + c] * scale;
                 if (r > c + 1) A[(size_t)r * ld + c] = v;
+                A[(size_t)c * ld + r] = v;  // contiguous copy in row c of the unused upper triangle
                 vs[r] = v;
             }
             if (threadIdx.x == 0) {
@@ -619,25 +620,36 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
 
 // ---------------------------------------------------------------------------
 // Central strips: P ([n][2 mc], column t holds the 2 mc values of the strips at t)
-// initialised to R1 = (L^-T)_c,: = [0 | L_cc^-T] and R2 = L_c,:, then P <- P Q.
+// initialised to R1 = (L^-T)_c,: = [0 | L_cc^-T] and R2 = L_c,:, then P <- P Q with
+// Q = H_0 H_1 ... H_{n-3}.  Each strip row is independent: chunks of rch rows are held
+// in shared memory (row-major, stride n) and each warp applies every reflector to the
+// rows it owns (q_rows_warp), so there is no block barrier per reflector.
 // ---------------------------------------------------------------------------
+// X <- X H_0 H_1 ... H_{n-3} on R rows owned by one warp
+template <int R>
+__device__ static void q_rows_warp(double* X, int n, const double* __restrict__ A, int ld, const double* __restrict__ tau) {
+    for (int k = 0; k + 2 < n; ++k) {
+        const double tk = tau[k];
+        if (tk != 0.0) warp_reflect<R>(X, n, k, n, A + (size_t)k * ld, tk);
+    }
+}
+
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const ClusterDesc* __restrict__ cls,
                                                                       const int* __restrict__ order,
                                                                       double* __restrict__ arena,
-                                                                      const int* __restrict__ status) {
+                                                                      const int* __restrict__ status, int rch) {
     extern __shared__ double sm[];
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld, mc = d.mc, w2 = 2 * mc, c0 = n - mc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
     const double* tau = arena + d.aux_off + 2 * ld;
     double* P = arena + d.cc_off;
-    double* Li = sm;              // mc x mc inverse of L_cc
-    double* vsh = sm + DCLNO_MAX_M * DCLNO_MAX_M;  // n
-    double* part = vsh + n;       // nw x 64
+    double* Li = sm;                               // mc x mc inverse of L_cc
+    double* Xs = sm + DCLNO_MAX_M * DCLNO_MAX_M;   // rch x n strip rows
     // L_cc^-1 by forward substitution, one column per thread
     if (threadIdx.x < mc) {
         const int col = threadIdx.x;
@@ -648,36 +660,31 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const Clus
         }
     }
     __syncthreads();
-    for (size_t e = threadIdx.x; e < (size_t)n * w2; e += blockDim.x) {
-        const int t = (int)(e / w2), r = (int)(e % w2);
-        double v;
-        if (r < mc) v = (t >= c0) ? Li[(t - c0) * DCLNO_MAX_M + r] : 0.0;  // (L_cc^-T)[r][t-c0] = Li[t-c0][r]
-        else v = (t <= c0 + (r - mc)) ? L[(size_t)(c0 + r - mc) * ld + t] : 0.0;
-        P[e] = v;
-    }
-    __syncthreads();
-    for (int k = 0; k + 2 < n; ++k) {
-        const double tk = tau[k];
-        if (tk == 0.0) continue;  // uniform
-        for (int t = k + 1 + threadIdx.x; t < n; t += blockDim.x) vsh[t] = A[(size_t)t * ld + k];
-        __syncthreads();
-        // u_r = sum_t P[t][r] v_t ; warps split t, lanes own rows (two passes if w2 > 32)
-        for (int r0 = 0; r0 < w2; r0 += 32) {
-            const int r = r0 + lane;
-            double u = 0.0;
-            if (r < w2)
-                for (int t = k + 1 + warp; t < n; t += nw) u = fma(P[(size_t)t * w2 + r], vsh[t], u);
-            part[warp * 64 + r0 + lane] = u;
+    for (int rc0 = 0; rc0 < w2; rc0 += rch) {
+        const int rows = min(rch, w2 - rc0);
+        for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+            const int r = rc0 + e / n, t = e % n;
+            double v;
+            if (r < mc) v = (t >= c0) ? Li[(t - c0) * DCLNO_MAX_M + r] : 0.0;  // (L_cc^-T)[r][t-c0] = Li[t-c0][r]
+            else v = (t <= c0 + (r - mc)) ? L[(size_t)(c0 + r - mc) * ld + t] : 0.0;
+            Xs[e] = v;
         }
         __syncthreads();
-        for (int r0 = 0; r0 < w2; r0 += 32) {
-            const int r = r0 + lane;
-            if (r < w2) {
-                double u = 0.0;
-                for (int w = 0; w < nw; ++w) u += part[w * 64 + r];
-                u *= tk;
-                for (int t = k + 1 + warp; t < n; t += nw) P[(size_t)t * w2 + r] = fma(-u, vsh[t], P[(size_t)t * w2 + r]);
+        {  // each warp owns a block of consecutive rows (at most DCLNO_RPW)
+            const int rpw = (rows + nw - 1) / nw, r0 = warp * rpw, my = min(rpw, rows - r0);
+            double* Xw = Xs + (size_t)max(r0, 0) * n;
+            switch (my) {
+                case 1: q_rows_warp<1>(Xw, n, A, ld, tau); break;
+                case 2: q_rows_warp<2>(Xw, n, A, ld, tau); break;
+                case 3: q_rows_warp<3>(Xw, n, A, ld, tau); break;
+                case 4: q_rows_warp<4>(Xw, n, A, ld, tau); break;
+                default: break;
             }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+            const int t = e / rows, rr = e % rows;
+            P[(size_t)t * w2 + rc0 + rr] = Xs[(size_t)rr * n + t];
         }
         __syncthreads();
     }
@@ -921,12 +928,15 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     const size_t gemm_doubles = EMU ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
     size_t sm_chol = (size_t)(NB * DK_LD + NB + gemm_doubles) * sizeof(double);
     size_t sm_tri = std::max(gemm_doubles, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
-    size_t sm_q = (size_t)(DCLNO_MAX_M * DCLNO_MAX_M + maxn + nw * 64) * sizeof(double);
+    // strip rows per shared-memory chunk of k_apply_q_rows: at most DCLNO_RPW per warp, within 200 KB
+    const int rch = (int)std::min<long long>(std::min(2 * b.mcmax, DCLNO_RPW * nw),
+                                             (200LL * 1024 / 8 - DCLNO_MAX_M * DCLNO_MAX_M) / std::max(maxn, 1));
+    size_t sm_q = (size_t)(DCLNO_MAX_M * DCLNO_MAX_M + (size_t)std::max(rch, 1) * maxn) * sizeof(double);
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_cholesky<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_congruence<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_tridiag<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tri));
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_apply_q_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_q));
-    if (sm_tri > 227 * 1024 || sm_q > 227 * 1024)
+    if (sm_tri > 227 * 1024 || sm_q > 227 * 1024 || rch < 1)
         return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the FP64 solver (n = " + std::to_string(maxn) + ")");
 
     {
@@ -966,7 +976,7 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     }
     {
         ProfScope ps__(c, "k_apply_q_rows");
-        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, rch);
     }
     DCLNO_LAUNCHED(c);
     {
