@@ -12,7 +12,9 @@
 //   * the K remaining roots of the secular equation 1 + rho sum_i z_i^2/(d_i - lam) = 0,
 //     one in each (d_j, d_{j+1}) and one above d_K, by a safeguarded iteration on a
 //     model with the two nearest poles, with lam stored as pole + offset so that every
-//     difference d_i - lam is formed without cancellation;
+//     difference d_i - lam is formed without cancellation; the first model steps of
+//     each root run on an FP32 preview of the sums (GB300's FP32 rate is many times
+//     its FP64 rate), the bracket and the converged root on FP64 sums;
 //   * z recomputed from the computed roots (Gu and Eisenstat 1995),
 //     z_i^2 = prod_j (lam_j - d_i) / (rho prod_{j != i} (d_j - d_i)), which makes the
 //     eigenvectors u_j = (z_i / (d_i - lam_j))_i / norm numerically orthogonal.
@@ -48,29 +50,59 @@ __device__ static SecVal sec_eval(int K, const double* dk, const double* w, int 
     return v;
 }
 
+// FP32 preview of the same sums, for the first model steps of a root: d is held as a
+// pair of floats (dh + dl = d to about 2^-48 relative), so each difference d_i - d_o
+// keeps about 24 correct bits even where d_i and d_o nearly coincide.  Only the root's
+// starting point comes from it; every bracket update and the final root use sec_eval.
+struct SecValF {
+    float psi, dpsi, phi, dphi;
+};
+
+__device__ static SecValF sec_eval_f(int K, const float* dh, const float* dl, const float* wf, int o, float tau,
+                                     int j) {
+    SecValF v = {0.f, 0.f, 0.f, 0.f};
+    const float ho = dh[o], lo = dl[o];
+    for (int i = 0; i <= j; ++i) {
+        const float r = __fdividef(1.0f, ((dh[i] - ho) + (dl[i] - lo)) - tau);
+        const float t = wf[i] * r;
+        v.psi += t;
+        v.dpsi = fmaf(t, r, v.dpsi);
+    }
+    for (int i = j + 1; i < K; ++i) {
+        const float r = __fdividef(1.0f, ((dh[i] - ho) + (dl[i] - lo)) - tau);
+        const float t = wf[i] * r;
+        v.phi += t;
+        v.dphi = fmaf(t, r, v.dphi);
+    }
+    return v;
+}
+
 // root h of A h^2 - B h + C = 0 inside (lo, hi); NaN if none (the caller bisects)
-__device__ static double quad_root_in(double A, double B, double C, double lo, double hi) {
-    if (A == 0.0) return (B != 0.0) ? C / B : nan("");
-    const double disc = fma(B, B, -4.0 * A * C);
-    if (!(disc >= 0.0)) return nan("");
-    const double sq = sqrt(disc);
-    double h1, h2;
-    if (B >= 0.0) {
-        h1 = (B + sq) / (2.0 * A);
-        h2 = (B + sq != 0.0) ? 2.0 * C / (B + sq) : nan("");
+template <typename T>
+__device__ static T quad_root_in(T A, T B, T C, T lo, T hi) {
+    const T nan_ = T(nan(""));
+    if (A == T(0)) return (B != T(0)) ? C / B : nan_;
+    const T disc = fma(B, B, -T(4) * A * C);
+    if (!(disc >= T(0))) return nan_;
+    const T sq = sqrt(disc);
+    T h1, h2;
+    if (B >= T(0)) {
+        h1 = (B + sq) / (T(2) * A);
+        h2 = (B + sq != T(0)) ? T(2) * C / (B + sq) : nan_;
     } else {
-        h1 = 2.0 * C / (B - sq);
-        h2 = (B - sq) / (2.0 * A);
+        h1 = T(2) * C / (B - sq);
+        h2 = (B - sq) / (T(2) * A);
     }
     if (h2 > lo && h2 < hi) return h2;
     if (h1 > lo && h1 < hi) return h1;
-    return nan("");
+    return nan_;
 }
+
 
 // Root j of 1 + sum_i w_i/(d_i - lam) = 0 (d ascending, w > 0, wsum = sum w):
 // lam = d_o + tau.  Returns the number of iterations (> 100: not converged).
-__device__ static int sec_root(int K, const double* dk, const double* w, double wsum, int j, double& tau_out,
-                               int& org_out) {
+__device__ static int sec_root(int K, const double* dk, const double* w, const float* dh, const float* dl,
+                               const float* wf, double wsum, int j, double& tau_out, int& org_out) {
     const double u = 1.1102230246251565e-16;  // 2^-53
     int o;
     double lo, hi, tau;
@@ -96,6 +128,40 @@ __device__ static int sec_root(int K, const double* dk, const double* w, double 
         hi = wsum;  // f(d_K + sum w) >= 0
         tau = 0.5 * wsum;
         v = sec_eval(K, dk, w, o, tau, j);
+    }
+    // up to three model steps on the FP32 preview, from the FP64 value at the start;
+    // the FP64 iteration below then starts where they end (if that lies in its bracket)
+    {
+        float tf = (float)tau, lof = (float)lo, hif = (float)hi;
+        SecValF vf = {(float)v.psi, (float)v.dpsi, (float)v.phi, (float)v.dphi};
+        const float dpj = (float)(dk[j] - dk[o]);
+        const float dqj = (j < K - 1) ? (float)(dk[j + 1] - dk[o]) : 0.f;
+        for (int s = 0; s < 3; ++s) {
+            if (s > 0) vf = sec_eval_f(K, dh, dl, wf, o, tf, j);
+            const float f = 1.0f + vf.psi + vf.phi;
+            if (f < 0.f) lof = tf;
+            else hif = tf;
+            const float dp = dpj - tf;
+            const float b1 = vf.dpsi * dp * dp, a1 = vf.psi - b1 / dp;
+            float h;
+            if (j < K - 1) {
+                const float dq = dqj - tf;
+                const float b2 = vf.dphi * dq * dq, a2 = vf.phi - b2 / dq;
+                const float A = 1.0f + a1 + a2;
+                h = quad_root_in<float>(A, A * (dp + dq) + b1 + b2, dp * dq * f, dp, dq);
+            } else {
+                h = (1.0f + a1 > 0.f) ? dp + b1 / (1.0f + a1) : nanf("");
+            }
+            float tn = tf + h;
+            if (!(tn > lof && tn < hif)) tn = 0.5f * (lof + hif);
+            if (tn == tf) break;
+            tf = tn;
+        }
+        const double ts = (double)tf;
+        if (ts > lo && ts < hi && ts != tau) {
+            tau = ts;
+            v = sec_eval(K, dk, w, o, tau, j);
+        }
     }
     int it = 0;
     for (; it < 100; ++it) {
@@ -154,6 +220,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
     int* org = kidx + n;      // origin pole of root j
     int* colc = org + n;      // deflated column -> coordinate
     int* gpq = colc + n;      // rotation coordinate pairs (2 n)
+    float* dhf = reinterpret_cast<float*>(gpq + 2 * n);  // d as float pairs (dh + dl) and w in float
+    float* dlf = dhf + n;
+    float* wff = dlf + n;
     __shared__ double red[MG_THREADS / 32][2];
     __shared__ int sK, sND, sNG, sFail;
     __shared__ double sRho, sWsum;
@@ -256,7 +325,13 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
     __syncthreads();
     const int K = sK, nd = sND, ng = sNG;
     const double rho = sRho;
-    for (int i = tid; i < K; i += MG_THREADS) w[i] = rho * zk[i] * zk[i];
+    for (int i = tid; i < K; i += MG_THREADS) {
+        w[i] = rho * zk[i] * zk[i];
+        const float h = (float)dk[i];
+        dhf[i] = h;
+        dlf[i] = (float)(dk[i] - (double)h);
+        wff[i] = (float)w[i];
+    }
     __syncthreads();
     if (tid == 0) {
         double s = 0.0;
@@ -268,20 +343,30 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
     for (int j = tid; j < K; j += MG_THREADS) {
         double t;
         int o;
-        if (sec_root(K, dk, w, sWsum, j, t, o) > 100) sFail = 1;
+        if (sec_root(K, dk, w, dhf, dlf, wff, sWsum, j, t, o) > 100) sFail = 1;
         tau[j] = t;
         org[j] = o;
     }
     __syncthreads();
-    // z from the computed roots (Gu-Eisenstat), ratios paired to stay near 1
+    // z from the computed roots (Gu-Eisenstat): numerator and denominator products
+    // accumulated separately (one division per z instead of one per factor), their
+    // exponents moved into integers every 16 factors so that neither over- nor underflows
     for (int i = tid; i < K; i += MG_THREADS) {
         const double di = dk[i];
-        double prod = ((dk[org[K - 1]] - di) + tau[K - 1]) / rho;
+        double pn = (dk[org[K - 1]] - di) + tau[K - 1], pd = rho;
+        int en = 0, ed = 0;
         for (int j = 0; j < K - 1; ++j) {
-            const double num = (dk[org[j]] - di) + tau[j];
-            const double den = (j < i) ? (dk[j] - di) : (dk[j + 1] - di);
-            prod *= num / den;
+            pn *= (dk[org[j]] - di) + tau[j];
+            pd *= (j < i) ? (dk[j] - di) : (dk[j + 1] - di);
+            if ((j & 15) == 15) {
+                int e;
+                pn = frexp(pn, &e);
+                en += e;
+                pd = frexp(pd, &e);
+                ed += e;
+            }
         }
+        const double prod = ldexp(pn / pd, en - ed);
         zh[i] = copysign(sqrt(fmax(prod, 0.0)), zk[i]);
     }
     // M = 0
@@ -334,7 +419,7 @@ dclno_status launch_merge(dclno_ctx* c, const Batch& b) {
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
-    const size_t sm = (size_t)b.maxn * (10 * sizeof(double) + 6 * sizeof(int));
+    const size_t sm = (size_t)b.maxn * (10 * sizeof(double) + 6 * sizeof(int) + 3 * sizeof(float));
     if (sm > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the merge step");
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
