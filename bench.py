@@ -37,7 +37,7 @@ CPU_SAMPLE_CLUSTERS = 8
 # DRAM read + write of one FP64 k_tridiag launch, captured by ncu on each workload
 # itself (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture; see
 # profiles/k_tridiag_fp64_rocksalt1728.md and profiles/k_tridiag_fp64_small.md)
-TRIDIAG_TRAFFIC = {"rocksalt1728": 928106789376.0 + 63594331904.0, "small64": 371203584.0 + 286477056.0}
+TRIDIAG_TRAFFIC = {"rocksalt1728": 928311876352.0 + 66767048960.0, "small64": 385863936.0 + 362590464.0}
 
 
 def parse():

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 import oracle as O  # noqa: E402
 import tbsystems as T  # noqa: E402
 from gpu_helpers import eps_tol, gpu_context, spectral_moments, to_dev  # noqa: E402
-from paper_1809_05637_gb300 import DclnoError  # noqa: E402
+from paper_1809_05637_gb300 import Context, DclnoError  # noqa: E402
 
 
 def _compare_spectra(ctx, res, kT, mus):
@@ -169,3 +169,22 @@ def test_errors_are_reported(cfg1):
         ctx.solve_clusters()
     assert e.value.status == 4
     ctx.close()
+
+
+def test_empty_system_and_call_order_are_refused():
+    """No atoms: refused with an argument error (no kernel runs); calls out of order
+    on an unbuilt context are refused the same way."""
+    ctx = Context()
+    empty = torch.zeros(0, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(DclnoError) as e:
+        ctx.build_clusters(np.zeros((0, 3)), np.eye(3) * 10.0, np.zeros(3, bool), np.zeros(0, np.int32),
+                           np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros((0, 3), np.int8),
+                           np.zeros(0, np.int64), empty, empty, 3.0, 6.0, 2)
+    assert e.value.status == 1 and "empty" in str(e.value)
+    for call in (lambda: ctx.compute_lnos(empty), lambda: ctx.solve_clusters(),
+                 lambda: ctx.find_mu(2.0, 0.01)):
+        with pytest.raises(DclnoError) as e:
+            call()
+        assert e.value.status == 1
+    ctx.close()
+
