@@ -280,11 +280,6 @@ __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, co
     }
 }
 
-// X = L^-T Q G for the columns of G ([n][w] at aux_off + 3 ld, w = mc or 2 mc): the
-// reflectors applied in reverse order (Q = H_0 ... H_{n-3}), then L^T X = G by back
-// substitution.  Columns are independent: chunks of rch columns are held in shared
-// memory (one row of stride n per column), each warp carries its columns through all
-// reflectors and the triangular solve (rho_qx_warp), with no block barriers.
 // R columns owned by one warp (rows of X, stride n): X <- H_0 ... H_{n-3} X (the
 // reflectors from the last one), then L^T X_new = X by back substitution.
 template <int R>
@@ -315,6 +310,11 @@ __device__ static void rho_qx_warp(double* X, int n, const double* __restrict__ 
     }
 }
 
+// X = L^-T Q G for the columns of G ([n][w] at aux_off + 3 ld, w = mc or 2 mc): the
+// reflectors applied in reverse order (Q = H_0 ... H_{n-3}), then L^T X = G by back
+// substitution.  Columns are independent: chunks of rch columns are held in shared
+// memory (one row of stride n per column), each warp carries its columns through all
+// reflectors and the triangular solve (rho_qx_warp), with no block barriers.
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDesc* __restrict__ cls,
                                                                 const int* __restrict__ order,
                                                                 double* __restrict__ arena, int with_e, int rch) {
