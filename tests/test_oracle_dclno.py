@@ -304,3 +304,22 @@ def test_density_rows_equal_matsubara_pole_sum():
         O.density_rows(s, r.cluster, r.eps, r.C, V, mu, s.kT, a)
         O.density_rows_poles(s, r.cluster, Hc, Sc, V, mu, s.kT, b, n_poles)
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-11)
+
+
+def test_periodic_invariants():
+    """A periodic cell (several images of every pair stored): sum_mu q_mu = M_i,
+    2 Tr(rho S) = N(mu) and 2 Tr(rho H) = E_band hold for a DC-LNO step, which
+    needs each row block scattered to its own image (atom, cell shift)."""
+    s = T.small_lattice(4, 4, 4, a=2.5, jitter=0.05, periodic=True, r_core=4.0, r_lno=6.0, k_lno=2)
+    assert len(np.unique(s.shift, axis=0)) > 27  # pairs reach beyond the nearest images
+    rho0 = O.plain_dc_density(s, s.r_core)[2]
+    lno = O.compute_lnos(s, rho0, s.k_lno)
+    V = {i: v[0] for i, v in lno.items()}
+    res = O.dclno_solve(s, V, s.r_core, s.r_lno, s.k_lno)
+    mu, n_mu, rho, e_band = O.finish_step(s, res, V, s.n_electrons, s.kT)
+    for i, r in res.items():
+        assert abs(r.q.sum() - s.norb[i]) < 1e-10
+    assert abs(n_mu - s.n_electrons) <= 1e-10 * s.n_electrons
+    assert abs(2 * _pair_trace(s, rho, s.S) - n_mu) < 1e-9
+    assert abs(2 * _pair_trace(s, rho, s.H) - e_band) < 1e-9 * abs(e_band)
+
