@@ -33,11 +33,8 @@ METRIC = "DC-LNO clusters/s at 1 GB300; mixed vs FP64 at ≤1e-6 Ha/atom, % of r
 WORKLOAD = ("DC-LNO step, 1728-atom gapped rock-salt (12^3 SC sites, a=3.0 bohr, jitter 0.05, "
             "9 s-Gaussians/atom, r_core=6, r_lno=10 bohr, 3 LNOs/atom, kT=0.01 Ha), FP64")
 DOMINANT = "k_tridiag"
-CPU_SAMPLE_CLUSTERS = 8
-# DRAM read + write of one FP64 k_tridiag launch, captured by ncu on each workload
-# itself (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture; see
-# profiles/k_tridiag_fp64_rocksalt1728.md and profiles/k_tridiag_fp64_small.md)
-TRIDIAG_TRAFFIC = {"rocksalt1728": 928311876352.0 + 66767048960.0, "small64": 385863936.0 + 362590464.0}
+# oracle sample: one cluster per host core (at least 8, at most 32), evenly spaced atoms
+CPU_SAMPLE_CLUSTERS = max(8, min(32, os.cpu_count() or 1))
 
 
 def parse():
@@ -49,8 +46,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
-    p.add_argument("--workload", choices=["rocksalt1728", "small64", "amorphous32000"], default="rocksalt1728",
-                   help="small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels; "
+    p.add_argument("--workload", choices=["rocksalt1728", "rocksalt512", "small64", "amorphous32000"],
+                   default="rocksalt1728",
+                   help="rocksalt512: the same rock-salt recipe on 8^3 sites (the same cluster dimensions, one "
+                        "wave of clusters in flight: the case for ncu captures of the cubic kernels); "
+                        "small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels; "
                         "amorphous32000: the 32,000-atom random packing, generated row range by row range "
                         "into device memory and solved through memory-admitted batches")
     p.add_argument("--atoms", type=int, default=32000, help="atoms of the amorphous workload (same density)")
@@ -63,6 +63,8 @@ def make_workload(name):
         return T.small_lattice(4, 4, 4, a=2.5, jitter=0.05, exps=(0.1, 0.2, 0.45, 1.0, 2.2, 5.0),
                                onsite=(-0.6, -0.4, -0.2, 0.0, 0.2, 0.4), e_per_atom=3.0, r_core=5.0, r_lno=8.0,
                                k_lno=3, periodic=True, name="small64")
+    if name == "rocksalt512":
+        return T.make_system(2, n_cells=8)
     return T.make_system(2)
 
 
@@ -122,17 +124,18 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(s, rho_in, mu_fixed, threads):
+def oracle_sample(s, rho_in, mu_fixed, threads, detail=False):
     """Per-cluster DC-LNO work of the oracle on a sample of clusters: LNOs of the
     LNO-region atoms, assembly, FP64 generalised eigensolve, weights and the
     central density-matrix rows at a fixed chemical potential.  Returns the
-    number of clusters and the wall time."""
+    number of clusters and the wall time (and, with detail, the LNOs, the
+    per-cluster results and the rows, for comparisons made after the timing)."""
     import numpy as np
 
     import oracle as O
 
     n = s.natoms
-    sample = [int(x) for x in np.linspace(0, n - 1, CPU_SAMPLE_CLUSTERS)]
+    sample = sorted({int(x) for x in np.linspace(0, n - 1, CPU_SAMPLE_CLUSTERS)})
     t0 = time.perf_counter()
     need = set()
     for i in sample:
@@ -144,17 +147,43 @@ def oracle_sample(s, rho_in, mu_fixed, threads):
     rows = np.zeros_like(s.S)
     for r in res.values():
         O.density_rows(s, r.cluster, r.eps, r.C, V, mu_fixed, s.kT, rows)
-    return len(sample), time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    if detail:
+        return len(sample), wall, V, res, rows
+    return len(sample), wall
 
 
 def cpu_threads():
     return max(1, min(CPU_SAMPLE_CLUSTERS, os.cpu_count() or 1))
 
 
-def sample_text():
-    return (f"{CPU_SAMPLE_CLUSTERS} of the 1728 clusters (evenly spaced atoms): LNOs of their LNO-region atoms, "
-            "assembly, FP64 Cholesky+Jacobi eigensolve, weights and central density rows at a fixed mu; "
+def sample_text(natoms=1728):
+    return (f"{CPU_SAMPLE_CLUSTERS} of the {natoms} clusters (evenly spaced atoms): LNOs of their LNO-region "
+            "atoms, assembly, FP64 Cholesky+Jacobi eigensolve, weights and central density rows at a fixed mu; "
             "the global mu search needs every cluster and is not in the sample")
+
+
+def oracle_errors(s, res, orows, spec, rows_gpu):
+    """A GPU solve against the oracle on the sampled clusters: the largest
+    eigenvalue difference (Ha), the same over each state's first-order bound (a
+    backward error n u in H^(i), S^(i), c^T S c = 1), and the largest density-row
+    difference relative to the row's largest element."""
+    import numpy as np
+
+    deps = dbound = drho = 0.0
+    for i, r in res.items():
+        d = np.abs(np.sort(spec[i][0]) - r.eps)
+        bound = 1e-10 + 2.0 * len(r.eps) * 2.0 ** -53 * (r.h_norm + np.abs(r.eps) * r.s_norm) * np.einsum(
+            "am,am->m", r.C, r.C)
+        deps = max(deps, float(np.max(d)))
+        dbound = max(dbound, float(np.max(d / bound)))
+        b0, b1 = int(s.row_ptr[i]), int(s.row_ptr[i + 1])
+        o0 = int(s.blk_off[b0])
+        o1 = int(s.blk_off[b1 - 1] + s.norb[i] * s.norb[s.col[b1 - 1]])
+        big = float(np.max(np.abs(orows[o0:o1])))
+        drho = max(drho, float(np.max(np.abs(rows_gpu[o0:o1] - orows[o0:o1]))) / big)
+    return {"clusters": sorted(res), "max_abs_eps_diff_ha": deps, "max_eps_diff_over_first_order_bound": dbound,
+            "max_rho_row_diff_rel_to_row_max": drho}
 
 
 def run_reference(args):
@@ -179,8 +208,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_clusters_per_step": ncl},
-            "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": th, "kind": "oracle",
-                             "sample": sample_text()},
+            "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": th, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample_text(s.natoms)},
             "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -367,6 +396,70 @@ def run_streamed(args):
 
 
 # ---------------------------------------------------------------------------
+# rooflines
+# ---------------------------------------------------------------------------
+SLICE_PRODUCTS = 36  # BF16 slice products per emulated FP64 multiply-add (levels t + u <= 7 of 8 x 8 slices)
+
+
+def bf16_peak():
+    """Dense BF16 tensor rate (TFLOP/s) the emulated contractions are measured against:
+    the sustained cuBLAS figure of MEASURED_PEAKS.json (the kernels run inside a
+    seconds-long step), else the fallback of one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops_sustained"])
+        return v, "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback (1.7 PFLOP/s sustained bf16, an earlier GB300 measurement)"
+
+
+def roofline_report(kernel, path, n3, k_ms, k_n, dfma, dmma, bf16, bf16_src):
+    """Roofline of one launch of the Householder tridiagonalisation (4 n^3 / 3
+    algorithmic flops per cluster): half symmetric matrix-vector products, which
+    run on the FP64 FMA pipe in both paths, half rank-2k trailing updates, on FP64
+    MMA (FP64 path) or emulated on BF16 tensor cores at 36 slice products per FP64
+    multiply-add (mixed path).  floor = the time of that mix at the measured peaks;
+    frac = floor / measured launch time; peak = algorithmic flops / floor (the
+    kernel's own effective peak, in FP64-equivalent TFLOP/s)."""
+    flops = float(n3.sum() * 4.0 / 3.0)
+    half = flops / 2.0
+    if path == "fp64":
+        floor_s = half / (dfma * 1e12) + half / (dmma * 1e12)
+        src = (f"measured in-process: FP64 FMA {dfma:.3f} TFLOP/s (symv half) and FP64 MMA {dmma:.3f} TFLOP/s "
+               "(rank-2k half)")
+    else:
+        floor_s = half / (dfma * 1e12) + SLICE_PRODUCTS * half / (bf16 * 1e12)
+        src = (f"symv half on measured FP64 FMA {dfma:.3f} TFLOP/s; rank-2k half as {SLICE_PRODUCTS} BF16 slice "
+               f"products per FP64 multiply-add at {bf16:.0f} TFLOP/s BF16, {bf16_src}")
+    launch_s = k_ms / max(k_n, 1) / 1e3 if k_n else None
+    achieved = flops / launch_s / 1e12 if launch_s else None
+    peak = flops / floor_s / 1e12
+    return {"bound": "alu", "kernel": kernel, "path": path, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s (FP64-equivalent)" if path == "mixed" else "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "traffic_source": "not measured in this run: DRAM bytes per launch are in profiles/ from a one-wave "
+                              "capture (the per-cluster traffic depends on how many clusters share L2)",
+            "peak_source": src, "flops_per_launch": flops, "floor_ms": floor_s * 1e3,
+            "launch_ms": launch_s * 1e3 if launch_s else None}
+
+
+def step_fmin_report(path, n3, step_ms, dfma, dmma, bf16):
+    """The whole step against its algorithmic minimum F_min = sum 8 n^3 / 3 (Cholesky
+    n^3/3, symmetric congruence n^3, tridiagonalisation 4 n^3/3): FP64 path at the
+    1:1 FP64 FMA/MMA rate; mixed path with the tridiagonalisation's symv half
+    (2 n^3/3) on FP64 FMA and the rest emulated at 36 BF16 slice products per FP64
+    multiply-add."""
+    fmin = float(n3.sum() * 8.0 / 3.0)
+    if path == "fp64":
+        floor_s = fmin / (1e12 / (0.5 / dfma + 0.5 / dmma))
+    else:
+        f64 = float(n3.sum() * 2.0 / 3.0)
+        floor_s = f64 / (dfma * 1e12) + SLICE_PRODUCTS * (fmin - f64) / (bf16 * 1e12)
+    return {"fmin_flops": fmin, "achieved_tflops": fmin / (step_ms / 1e3) / 1e12, "floor_ms": floor_s * 1e3,
+            "frac": floor_s * 1e3 / step_ms}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -424,6 +517,14 @@ def run_ours(args):
     k_ms, k_n = ctx.kernel_time(DOMINANT)
     ctx.set_profiling(False)
     clocks = clk.summary()
+    gpu_samples = {}  # per path: spectra and the density rows at the FP64 step's mu (oracle comparison)
+
+    def keep_sample(name):
+        out = torch.zeros_like(rho_in)
+        ctx.density_matrix(mu, s.kT, out)
+        gpu_samples[name] = (ctx.spectrum(), out.cpu().numpy())
+
+    keep_sample("fp64")
     ms = max_over_ranks(ms, world, dev)
     value = replica_throughput(world, ncl, args.steps, ms / 1e3)
 
@@ -446,6 +547,7 @@ def run_ours(args):
     kmx_ms, kmx_n = ctx.kernel_time(DOMINANT)
     ctx.set_profiling(False)
     ms_mx = max_over_ranks(ms_mx, world, dev)
+    keep_sample("mixed")
 
     # e2e: the C-ABI step with host buffers (H2D of rho_in and D2H of rho_out inside)
     e2e = None
@@ -467,31 +569,20 @@ def run_ours(args):
                "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
-    # roofline of the dominant kernel: algorithmic flops of Householder tridiagonalisation,
-    # 4 n^3 / 3 per cluster, half symmetric matrix-vector products (FP64 FMA pipe),
-    # half rank-2k updates (FP64 tensor-core MMA)
-    flops = float(np.sum(4.0 * dims.astype(np.float64) ** 3 / 3.0))
+    # roofline of the dominant kernel of each path, against that kernel's own floor
+    # (see roofline_report); the whole step's algorithmic minimum F_min beside it
     dfma, dmma = measure_fp64_peaks()
-    peak = 1.0 / (0.5 / dfma + 0.5 / dmma)
-    achieved = flops / (k_ms / max(k_n, 1) / 1e3) / 1e12 if k_n else None
-    traffic = TRIDIAG_TRAFFIC.get(args.workload)
-    roofline = {"bound": "alu", "kernel": DOMINANT, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 k_tridiag launch "
-                                  "on this workload",
-                "peak_source": f"measured in-process: FP64 FMA {dfma:.3f} and FP64 MMA {dmma:.3f} TFLOP/s, "
-                               "weighted 1:1 by the kernel's flop mix (symv on FMA, rank-2k on MMA)",
-                "flops_per_launch": flops, "launch_ms": k_ms / max(k_n, 1)}
-
-    achieved_mx = flops / (kmx_ms / max(kmx_n, 1) / 1e3) / 1e12 if kmx_n else None
-    mixed = {"value": replica_throughput(world, ncl, args.steps, ms_mx / 1e3), "unit": "clusters/s", "ms_per_step": ms_mx / args.steps,
+    bf16, bf16_src = bf16_peak()
+    n3 = dims.astype(np.float64) ** 3
+    roofline = roofline_report(DOMINANT, "fp64", n3, k_ms, k_n, dfma, dmma, bf16, bf16_src)
+    roofline["step_fmin"] = step_fmin_report("fp64", n3, ms / args.steps, dfma, dmma, bf16)
+    mixed = {"value": replica_throughput(world, ncl, args.steps, ms_mx / 1e3), "unit": "clusters/s",
+             "ms_per_step": ms_mx / args.steps,
              "speedup_vs_fp64": ms / ms_mx, "e_band_err_per_atom_vs_fp64": abs(e_mx - e_band) / s.natoms,
-             "mu_diff_vs_fp64": abs(mu_mx - mu), "dtype": "bf16 slices (8 x 8 bit) emulating f64 contractions; f64 elsewhere",
-             "roofline": {"bound": "alu", "kernel": DOMINANT, "achieved": achieved_mx, "peak": dfma, "unit": "TFLOP/s",
-                          "frac": (achieved_mx / dfma) if achieved_mx else None, "traffic": None,
-                          "peak_source": "measured in-process native FP64 FMA rate: FP64-equivalent throughput of the "
-                                         "mixed kernel against the native FP64 roofline",
-                          "launch_ms": kmx_ms / max(kmx_n, 1)}}
+             "mu_diff_vs_fp64": abs(mu_mx - mu),
+             "dtype": "bf16 slices (8 x 8 bit) emulating f64 contractions; f64 elsewhere",
+             "roofline": roofline_report(DOMINANT, "mixed", n3, kmx_ms, kmx_n, dfma, dmma, bf16, bf16_src)}
+    mixed["roofline"]["step_fmin"] = step_fmin_report("mixed", n3, ms_mx / args.steps, dfma, dmma, bf16)
 
     scf = None
     if not args.no_scf:
@@ -501,8 +592,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         th = cpu_threads()
-        ncs, wall = oracle_sample(s, rho_host, mu, th)
-        cpu = {"value": ncs / wall, "unit": "clusters/s", "cores": th, "kind": "oracle", "sample": sample_text()}
+        ncs, wall, _, ores, orows = oracle_sample(s, rho_host, mu, th, detail=True)
+        cpu = {"value": ncs / wall, "unit": "clusters/s", "cores": th, "host_cores": os.cpu_count(),
+               "kind": "oracle", "sample": sample_text(s.natoms)}
+        # both GPU paths against the oracle on the sampled clusters (rows at the FP64 step's mu)
+        line_err = {}
+        for name, (spec_g, rows_g) in gpu_samples.items():
+            line_err[name] = oracle_errors(s, ores, orows, spec_g, rows_g)
+        roofline["oracle_sample"] = line_err["fp64"]
+        mixed["oracle_sample"] = line_err["mixed"]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,

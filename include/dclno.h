@@ -286,21 +286,25 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
 
 /*
  * The chemical-potential search of dclno_find_mu without any device
- * allocation, for callers that cannot call cudaMalloc: code that runs while a
- * stream is captured into a CUDA graph, applications whose pool allocator owns
- * all device memory, control loops that must not allocate once running.  The
- * paper has no counterpart: this is an interface for such callers.
+ * allocation, for callers that cannot call cudaMalloc: applications whose own
+ * pool allocator has taken all device memory up front, and control loops that
+ * must not allocate once they are running (an allocation can block, fail or
+ * fragment memory at a bad moment).  The paper has no counterpart: this is an
+ * interface for such callers.
  * Inputs: eps, q: device arrays of `count` eigenvalue / weight pairs (for
- * example a copy of dclno_get_spectrum's output); n_electrons, kT as in
- * dclno_find_mu.  Outputs: mu_out, nelec_out (host scalars, nullable).  Work is
- * ordered on `cuda_stream` (NULL = legacy default stream); the call
- * synchronises it.
+ * example a copy of dclno_get_spectrum's output), both contiguous FP64, both
+ * holding at least `count` elements, on the device that is current for the
+ * calling thread; the library cannot check any of this and reads past a
+ * shorter array.  n_electrons, kT as in dclno_find_mu.  Outputs: mu_out,
+ * nelec_out (host scalars, nullable), copied to the host at the end of the
+ * call.  Work is ordered on `cuda_stream` (NULL = legacy default stream); the
+ * call synchronises it.
  * Scratch: a file-scope device array of about 165 KB inside the library,
  * allocated on every GPU that loads the library and kept until exit; it
  * covers at most 8,388,608 pairs (4096 blocks x 256 threads x 8), and a larger
  * count returns DCLNO_ERR_ARG without touching the GPU.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the one array:
+ * device looks up the array's device address (cudaGetSymbolAddress) once and
+ * keeps it.  All calls share the one array:
  * calls whose GPU work overlaps (other threads or streams) race and must be
  * serialised by the caller.
  * Errors: DCLNO_ERR_ARG (null pointers, count < 1 or too large, kT <= 0),

@@ -119,10 +119,22 @@ def measure_fp64_peaks():
 def find_mu_noalloc(eps, q, n_electrons, kT, stream=None):
     """dclno_find_mu_noalloc on device arrays eps, q (torch, float64); returns (mu, N(mu)).
 
-    The library allocates nothing in this call (see include/dclno.h)."""
+    The library allocates nothing in this call (see include/dclno.h).  The C entry
+    point reads `count` doubles from each pointer and cannot check them, so the
+    arrays are checked here: contiguous torch.float64 CUDA tensors of the same
+    length on the current device."""
+    import torch
+
     lib = load_library()
+    for name, t in (("eps", eps), ("q", q)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"find_mu_noalloc: {name} must be a contiguous torch.float64 CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"find_mu_noalloc: {name} is on {t.device}, not on the current device "
+                             f"cuda:{torch.cuda.current_device()}")
+    if eps.numel() != q.numel():
+        raise ValueError(f"find_mu_noalloc: eps has {eps.numel()} elements, q has {q.numel()}")
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     mu, n = ctypes.c_double(), ctypes.c_double()
     st = lib.dclno_find_mu_noalloc(_ptr(eps), _ptr(q), int(eps.numel()), float(n_electrons), float(kT),

@@ -78,7 +78,8 @@ extern "C" dclno_status dclno_create(dclno_ctx** out, void* cuda_stream) {
     if (!c) return DCLNO_ERR_OOM;
     c->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
-    if (e != cudaSuccess) {
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess || c->nsm < 1) {
         delete c;
         return DCLNO_ERR_CUDA;
     }
@@ -243,7 +244,7 @@ static dclno_status block_absmax(dclno_ctx* c, const double* S, std::vector<doub
         (e = cudaMalloc(&d_out, sizeof(double) * std::max<long long>(c->nnzb, 1))) == cudaSuccess &&
         (e = cudaMemcpy(d_off, c->blk_off.data(), sizeof(long long) * c->nnzb, cudaMemcpyHostToDevice)) == cudaSuccess &&
         (e = cudaMemcpy(d_sz, sz.data(), sizeof(int) * c->nnzb, cudaMemcpyHostToDevice)) == cudaSuccess) {
-        const int grid = (int)std::min<long long>((c->nnzb * 32 + 255) / 256, 152LL * 64);
+        const int grid = (int)std::min<long long>((c->nnzb * 32 + 255) / 256, (long long)c->nsm * 64);
         k_block_absmax<<<std::max(grid, 1), 256, 0, c->stream>>>(c->nnzb, d_off, d_sz, S, d_out);
         c->launches++;
         e = cudaGetLastError();

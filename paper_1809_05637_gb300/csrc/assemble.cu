@@ -178,7 +178,7 @@ dclno_status launch_lno_blocks(dclno_ctx* c) {
     if (!c->has_lno_region) return DCLNO_OK;
     ProfScope ps__(c, "k_lno_blocks");
     const long long warps = c->nnzb;
-    const int grid = (int)std::min<long long>((warps * 32 + 255) / 256, 152LL * 64);
+    const int grid = (int)std::min<long long>((warps * 32 + 255) / 256, (long long)c->nsm * 64);
     k_lno_blocks<<<grid, 256, 0, c->stream>>>(c->nnzb, c->k_lno, c->d_brow, c->d_key, c->d_norb, c->d_blk_off,
                                               c->d_voff, c->d_tblk_off, c->H, c->S, c->d_V, c->d_tblk);
     DCLNO_LAUNCHED(c);

@@ -99,6 +99,7 @@ struct dclno_ctx {
     std::string err;
     long long launches = 0;
     int device = 0;
+    int nsm = 1;  // streaming multiprocessors of the device (grid sizes are multiples of it)
 
     // system (host copies of the structure, device pointers of the values)
     int N = 0;

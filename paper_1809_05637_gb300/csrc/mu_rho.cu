@@ -52,12 +52,30 @@ __global__ void k_mu_bracket(long long total, const double* __restrict__ eps, do
     }
 }
 
+// Fixed-order sum of part[b * stride] over b < nblk by one warp: lane l adds the
+// blocks l, l + 32, ... in order, then a butterfly over the lanes (the same order on
+// every run, so the bits of N(mu) are reproducible).
+__device__ __forceinline__ double warp_ordered_sum(const double* __restrict__ part, int nblk, int stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * stride];
+    return warp_sum(s);
+}
+
+// one warp: extremes of the per-block minima and maxima, then the bracket
 __global__ void k_mu_init(int nblk, const double* __restrict__ part, double* __restrict__ scal, double kT, double ne) {
+    const int lane = threadIdx.x & 31;
     double a = 1e300, b = -1e300;
-    for (int t = 0; t < nblk; ++t) {
+    for (int t = lane; t < nblk; t += 32) {
         a = fmin(a, part[2 * t]);
         b = fmax(b, part[2 * t + 1]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (lane != 0) return;
     scal[0] = a - 40.0 * kT;
     scal[1] = b + 40.0 * kT;
     scal[2] = 0.5 * (scal[0] + scal[1]);
@@ -102,18 +120,19 @@ __global__ void k_mu_partial(long long total, const double* __restrict__ eps, co
     }
 }
 
-// fixed-order reduction of the partial sums; narrows [lo, hi]; status in scal[7]
+// fixed-order reduction of the partial sums (warp p sums trial point p); narrows [lo, hi]
 __global__ void k_mu_update(int nblk, const double* __restrict__ part, double* __restrict__ scal, int first, int last) {
-    if (threadIdx.x != 0) return;
     const int np = KSEC + 2;
-    if (scal[4] != 0.0) return;
-    const double lo = scal[0], hi = scal[1], ne = scal[6];
-    double N[KSEC + 2];
-    for (int p = 0; p < np; ++p) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * np + p];
-        N[p] = 2.0 * s;
+    __shared__ double N[KSEC + 2];
+    if (scal[4] != 0.0) return;  // uniform: every thread reads the same flag
+    const int warp = threadIdx.x >> 5;
+    if (warp < np) {
+        const double v = warp_ordered_sum(part + warp, nblk, np);
+        if ((threadIdx.x & 31) == 0) N[warp] = 2.0 * v;
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double lo = scal[0], hi = scal[1], ne = scal[6];
     if (first) {
         scal[8] = N[0];
         scal[9] = N[np - 1];
@@ -162,10 +181,8 @@ __global__ void k_mu_final_partial(long long total, const double* __restrict__ e
 }
 
 __global__ void k_mu_final(int nblk, const double* __restrict__ part, double* __restrict__ scal) {
-    if (threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[b];
-    scal[3] = 2.0 * s;
+    const double v = warp_ordered_sum(part, nblk, 1);
+    if (threadIdx.x == 0) scal[3] = 2.0 * v;
 }
 
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, double* nmu_out) {
@@ -178,7 +195,7 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
     DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_mu_init");
-        k_mu_init<<<1, 1, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, kT, ne);
+        k_mu_init<<<1, 32, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, kT, ne);
     }
     DCLNO_LAUNCHED(c);
     for (int pass = 0; pass < MU_PASSES; ++pass) {
@@ -189,7 +206,7 @@ dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu_out, 
         DCLNO_LAUNCHED(c);
         {
             ProfScope ps__(c, "k_mu_update");
-            k_mu_update<<<1, 32, 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, pass == 0, pass == MU_PASSES - 1);
+            k_mu_update<<<1, 32 * (KSEC + 2), 0, c->stream>>>(nblk, c->d_mu_work, c->d_scalars, pass == 0, pass == MU_PASSES - 1);
         }
         DCLNO_LAUNCHED(c);
     }
@@ -503,7 +520,7 @@ dclno_status launch_status_or(dclno_ctx* c) {
 dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha) {
     k_scf_record<<<1, 32, 0, c->stream>>>(c->N, c->d_scalars, c->d_eband, c->d_err, c->d_hist, c->hist_cap);
     DCLNO_LAUNCHED(c);
-    k_mix<<<152 * 8, 256, 0, c->stream>>>(c->nval, rho, rho_out, alpha);
+    k_mix<<<c->nsm * 8, 256, 0, c->stream>>>(c->nval, rho, rho_out, alpha);
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
@@ -511,10 +528,9 @@ dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, d
 // ---------------------------------------------------------------------------
 // Chemical potential without any device allocation (dclno_find_mu_noalloc).
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a stream is
-// being captured into a CUDA graph, applications that hand every byte of device
-// memory to their own pool allocator, and control loops that must not allocate
-// once they are running.  This variant keeps its scratch (the per-block partial
+// Some callers cannot call cudaMalloc at all: applications that hand every byte
+// of device memory to their own pool allocator up front, and control loops that
+// must not allocate once they are running.  This variant keeps its scratch (the per-block partial
 // sums of the k-section and its bracket scalars) in the file-scope array below,
 // which every GPU that loads the library holds until the process exits.  The
 // caller passes the (eps, q) pairs; one partial sum per block of
@@ -557,10 +573,10 @@ extern "C" dclno_status dclno_find_mu_noalloc(const double* eps, const double* q
     // every scratch word that is read is written first in this call: k_mu_init sets all
     // bracket scalars (the done flag to 0), each pass rewrites the partial sums it reads
     k_mu_bracket<<<nblk, 256, 0, st>>>(count, eps, part);
-    k_mu_init<<<1, 1, 0, st>>>(nblk, part, scal, kT, n_electrons);
+    k_mu_init<<<1, 32, 0, st>>>(nblk, part, scal, kT, n_electrons);
     for (int pass = 0; pass < MU_PASSES; ++pass) {
         k_mu_partial<<<nblk, 256, 0, st>>>(count, eps, q, scal, part, pass == 0);
-        k_mu_update<<<1, 32, 0, st>>>(nblk, part, scal, pass == 0, pass == MU_PASSES - 1);
+        k_mu_update<<<1, 32 * (KSEC + 2), 0, st>>>(nblk, part, scal, pass == 0, pass == MU_PASSES - 1);
     }
     k_mu_final_partial<<<nblk, 256, 0, st>>>(count, eps, q, scal, part);
     k_mu_final<<<1, 32, 0, st>>>(nblk, part, scal);

@@ -279,7 +279,8 @@ def fill_rows(system: System, atoms) -> None:
 def workload_spec(cfg: int, seed: int | None = None, n_atoms: int | None = None, **over) -> dict:
     """Geometry, basis and parameters of one of the five workloads; keyword
     overrides replace r_core, r_lno, k_lno.
-    n_atoms (workload 5 only) packs fewer atoms at the same density (a smaller cube).
+    n_atoms (workload 5 only) packs fewer atoms at the same density (a smaller cube);
+    n_cells (workload 2 only) sets the sites per edge of the periodic rock-salt cube.
 
     1  64-atom simple-cubic 4x4x4, a=2.5, open, 4 s-Gaussians, 2 e/atom.
     2  1,728-atom rock-salt arrangement on SC 12^3, a=3.0, periodic, jitter 0.05,
@@ -300,14 +301,15 @@ def workload_spec(cfg: int, seed: int | None = None, n_atoms: int | None = None,
                    n_electrons=2.0 * n, kT=0.01, r_core=5.0, r_lno=8.0, k_lno=2)
     elif cfg in (2, 3):
         rng = np.random.default_rng(1001 if seed is None else seed)
-        pos, ijk = _sc_lattice(12, 12, 12, 3.0)
+        nc = int(over.pop("n_cells", 12))  # sites per edge (12 in the recipe; even keeps the rock-salt order)
+        pos, ijk = _sc_lattice(nc, nc, nc, 3.0)
         pos = pos + rng.normal(0.0, 0.05, size=pos.shape)
         n = len(pos)
         species = (ijk.sum(1) % 2).astype(np.int32)  # 0 = A (even x+y+z), 1 = B
         e = np.geomspace(0.1, 5.0, 9)
         base = np.linspace(-0.6, 0.5, 9)
         onsite = [base + (-0.3 if s == 0 else 0.3) for s in species]
-        sys = dict(name="cfg2_rocksalt1728", pos=pos, cell=np.eye(3) * 36.0,
+        sys = dict(name=f"cfg2_rocksalt{n}", pos=pos, cell=np.eye(3) * (3.0 * nc),
                    pbc=np.ones(3, bool), species=species,
                    exps=[e.copy() for _ in range(n)], onsite=onsite,
                    n_electrons=4.5 * n, kT=0.01, r_core=6.0, r_lno=10.0, k_lno=3)

@@ -57,3 +57,56 @@ def rho_row_tol(r, big):
     n = len(r.eps)
     kappa = r.s_norm * float(np.max(np.einsum("am,am->m", r.C, r.C)))
     return 1e-9 + n * U * kappa * big
+
+
+def oracle_sample(s, rho_in, sample):
+    """The oracle's LNOs (of the sampled clusters' LNO members) and its solve of the
+    sampled clusters, from the same input density: (lno, V, results)."""
+    import oracle as O
+
+    need = set()
+    for i in sample:
+        cl = O.cluster_members(s, i, s.r_core, s.r_lno, s.k_lno)
+        need |= {int(a) for a, c in zip(cl.atoms, cl.core) if not c}
+    lno = O.compute_lnos(s, rho_in, s.k_lno, atoms=sorted(need))
+    V = {j: v[0] for j, v in lno.items()}
+    res = O.dclno_solve(s, V, s.r_core, s.r_lno, s.k_lno, atoms=list(sample), threads=len(sample))
+    return lno, V, res
+
+
+def row_range(s, i):
+    """Value range [o0, o1) of the BSR row of atom i."""
+    b0, b1 = s.row_ptr[i], s.row_ptr[i + 1]
+    return int(s.blk_off[b0]), int(s.blk_off[b1 - 1] + s.norb[i] * s.norb[s.col[b1 - 1]])
+
+
+def check_sampled_clusters(s, V, res, spec, rho_test, mu_test, row_tol, mus):
+    """Sampled clusters of a GPU solve against the oracle: eigenvalues within the
+    first-order bound of each state (state_tol), weights through smooth spectral
+    sums with that bound propagated through f', and the density rows at the fixed
+    chemical potential mu_test within row_tol(r, big) (big = the row's largest
+    element).  Returns the largest eigenvalue difference over its bound and the
+    largest row difference over the row's largest element (for reports)."""
+    import oracle as O
+
+    worst_eps, worst_rho = 0.0, 0.0
+    for i, r in res.items():
+        e_gpu, q_gpu = spec[i]
+        assert len(e_gpu) == len(r.eps), f"cluster {i}: dimension"
+        tol = state_tol(r)
+        d = np.abs(np.sort(e_gpu) - r.eps)
+        worst_eps = max(worst_eps, float(np.max(d / tol)))
+        assert np.all(d <= tol), f"cluster {i}: eigenvalues (worst {np.max(d / tol):.3g} of the bound)"
+        for x in mus:
+            g = spectral_moments(e_gpu, q_gpu, [x], s.kT)[0]
+            o = spectral_moments(r.eps, r.q, [x], s.kT)[0]
+            f = fermi((r.eps - x) / s.kT)
+            fp = f * (1.0 - f) / s.kT
+            assert abs(g - o) <= 1e-9 + float(np.sum(fp * tol * np.abs(r.q))), f"cluster {i}: weights at {x}"
+        rows = np.zeros_like(s.S)
+        O.density_rows(s, r.cluster, r.eps, r.C, V, mu_test, s.kT, rows)
+        o0, o1 = row_range(s, i)
+        big = float(np.max(np.abs(rows[o0:o1])))
+        worst_rho = max(worst_rho, float(np.max(np.abs(rho_test[o0:o1] - rows[o0:o1]))) / big)
+        np.testing.assert_allclose(rho_test[o0:o1], rows[o0:o1], rtol=0, atol=row_tol(r, big))
+    return worst_eps, worst_rho
