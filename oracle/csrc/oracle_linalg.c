@@ -223,10 +223,13 @@ static void house_right(double *A, int n, int c0, int len, int r0, int r1,
 static void eig2x2(double a, double b, double c, double d, double *r1, double *i1,
                    double *r2, double *i2)
 {
-    /* eigenvalues of [[a, b], [c, d]] */
+    /* eigenvalues of [[a, b], [c, d]]: tr +- sqrt(p^2 + bc) with p = (a - d)/2.  The
+     * discriminant is formed from p and bc, not as tr^2 - det, which cancels to zero
+     * for eigenvalues closer than about sqrt(u) |tr|. */
     double tr = 0.5 * (a + d);
+    double p = 0.5 * (a - d);
     double det = a * d - b * c;
-    double disc = tr * tr - det;
+    double disc = p * p + b * c;
     if (disc >= 0.0) {
         double s = sqrt(disc);
         double big = tr + (tr >= 0.0 ? s : -s);

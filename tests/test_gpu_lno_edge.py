@@ -21,6 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
+from oracle.dclno_oracle import LNO_COMPLEX_SELECTED, LNO_PAIR_SPLIT  # noqa: E402
 from gpu_helpers import gpu_context, spectral_moments, state_tol, to_dev  # noqa: E402
 
 PAIR_ATOM, SPLIT_ATOM, TIE_ATOM = 0, 21, 42
@@ -88,8 +89,8 @@ def test_complex_pair_and_split_pair(cfg1, cfg1_dc0, targets):
     assert s.k_lno == 2 and np.all(s.norb == 4)
     rho = _with_lambda(s, cfg1_dc0[2], {PAIR_ATOM: targets["pair"][0], SPLIT_ATOM: targets["split"][0]})
     lno = O.compute_lnos(s, rho, s.k_lno)
-    assert lno[PAIR_ATOM][2] == O.LNO_COMPLEX_SELECTED
-    assert lno[SPLIT_ATOM][2] == O.LNO_COMPLEX_SELECTED | O.LNO_PAIR_SPLIT
+    assert lno[PAIR_ATOM][2] == LNO_COMPLEX_SELECTED
+    assert lno[SPLIT_ATOM][2] == LNO_COMPLEX_SELECTED | LNO_PAIR_SPLIT
     ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
     ctx.compute_lnos(to_dev(rho))
     glno = ctx.lnos()

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import tbsystems as T  # noqa: E402
-from gpu_helpers import check_sampled_clusters, gpu_context, oracle_sample, to_dev  # noqa: E402
+from gpu_helpers import check_sampled_clusters, gpu_context, oracle_sample, rho_row_tol, to_dev  # noqa: E402
 from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED  # noqa: E402
 
 SAMPLE = [0, 777, 1727]
@@ -68,12 +68,17 @@ def test_sampled_lnos_match_oracle(run, oracle_res):
 def test_sampled_clusters_match_oracle(run, oracle_res, prec):
     """Both precisions against the FP64 oracle.  Density elements are compared
     relative to the row's largest element: rows reach 1e4 where the nearly
-    dependent basis gives large coefficients (cond S^(i) ~ 3e7)."""
+    dependent basis gives large coefficients (cond S^(i) ~ 3e7).  FP64: within
+    4e-9 of the row maximum (measured 2.8e-9 on 16 sampled clusters).  Mixed: the
+    slice emulation rounds each contraction relative to its operands' row maxima,
+    so its rows are held to the first-order bound of a backward error n u in
+    S^(i) (rho_row_tol, about 2e-6 of the row maximum here; measured 1.4e-7)."""
     s = run["s"]
     _, V, res = oracle_res
     r = run[prec]
+    row_tol = (lambda rr, big: 1e-9 + 4e-9 * big) if prec == "fp64" else rho_row_tol
     worst_eps, worst_rho = check_sampled_clusters(
-        s, V, res, r["spec"], r["rho_test"], MU_TEST, lambda rr, big: 1e-9 + 4e-9 * big, np.linspace(-0.9, 0.1, 11))
+        s, V, res, r["spec"], r["rho_test"], MU_TEST, row_tol, np.linspace(-0.9, 0.1, 11))
     print(f"{prec}: eigenvalues {worst_eps:.3g} of the first-order bound, rho rows {worst_rho:.3g} of the row max")
 
 

@@ -74,6 +74,22 @@ def test_nonsym_eig_vs_numpy(m):
             free.remove(k)
 
 
+@pytest.mark.parametrize("gap", [5e-9, 1e-11, 0.0])
+def test_nonsym_eig_close_real_pair(gap):
+    """Eigenvalues closer than sqrt(u) are still resolved: A = X D X^-1 with a
+    well-conditioned X (so each eigenvalue is determined to about u |A| cond(X)) and
+    D = diag(0.9, 0.5 + gap, 0.5, 0.1).  A discriminant formed as tr^2 - det would
+    merge the close pair into its mean."""
+    rng = np.random.default_rng(3)
+    X = np.eye(4) + 0.3 * rng.standard_normal((4, 4))
+    d = np.array([0.9, 0.5 + gap, 0.5, 0.1])
+    A = X @ np.diag(d) @ np.linalg.inv(X)
+    wr, wi = O.nonsym_eig(A)
+    assert np.all(np.abs(wi) <= 1e-7)  # a close pair may come out complex only at the level of sqrt(u) |A|
+    got = np.sort(wr)[::-1]
+    np.testing.assert_allclose(got, d, rtol=0, atol=1e-13 if gap > 0 else 1e-7)
+
+
 def test_inverse_iteration():
     rng = np.random.default_rng(7)
     A = rng.normal(size=(9, 9))
