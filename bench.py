@@ -32,7 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = "DC-LNO clusters/s at 1 GB300; mixed vs FP64 at ≤1e-6 Ha/atom, % of roofline"
 WORKLOAD = ("DC-LNO step, 1728-atom gapped rock-salt (12^3 SC sites, a=3.0 bohr, jitter 0.05, "
             "9 s-Gaussians/atom, r_core=6, r_lno=10 bohr, 3 LNOs/atom, kT=0.01 Ha), FP64")
-DOMINANT = "k_tridiag"
+# kernels whose time is reported per step (CUDA events around each launch on the context's stream)
+KERNELS = ["k_lambda", "k_lno_eig", "k_lno_blocks", "k_assemble", "k_cholesky", "k_congruence", "k_tridiag",
+           "k_band", "k_chase", "k_ql", "k_merge", "k_apply_q_rows", "k_replay_fwd", "k_mgemm_fwd", "k_weights",
+           "k_mu_partial", "k_mu_update", "k_rho_prep", "k_mgemm_rev", "k_replay_rev", "k_rho_qx", "k_rho_scatter"]
+ROOFLINE_KERNELS = ("k_tridiag", "k_band", "k_chase")  # kernels with a roofline model (roofline_report)
 # oracle sample: one cluster per host core (at least 8, at most 32), evenly spaced atoms
 CPU_SAMPLE_CLUSTERS = max(8, min(32, os.cpu_count() or 1))
 
@@ -413,23 +417,36 @@ def bf16_peak():
         return 1700.0, "fallback (1.7 PFLOP/s sustained bf16, an earlier GB300 measurement)"
 
 
-def roofline_report(kernel, path, n3, k_ms, k_n, dfma, dmma, bf16, bf16_src):
-    """Roofline of one launch of the Householder tridiagonalisation (4 n^3 / 3
-    algorithmic flops per cluster): half symmetric matrix-vector products, which
-    run on the FP64 FMA pipe in both paths, half rank-2k trailing updates, on FP64
-    MMA (FP64 path) or emulated on BF16 tensor cores at 36 slice products per FP64
-    multiply-add (mixed path).  floor = the time of that mix at the measured peaks;
-    frac = floor / measured launch time; peak = algorithmic flops / floor (the
-    kernel's own effective peak, in FP64-equivalent TFLOP/s)."""
-    flops = float(n3.sum() * 4.0 / 3.0)
-    half = flops / 2.0
+def roofline_report(kernel, path, n, k_ms, k_n, dfma, dmma, bf16, bf16_src):
+    """Roofline of one launch of a tridiagonalisation kernel over all clusters
+    (dimensions n), against that kernel's own floor: the time its flop mix takes at
+    the measured peaks.  frac = floor / measured launch time; peak = algorithmic
+    flops / floor (the kernel's own effective peak, FP64-equivalent for emulated work).
+
+    k_tridiag  one-stage Householder, 4 n^3/3: half symmetric matrix-vector products
+               (FP64 FMA in both paths), half rank-2k updates (FP64 MMA, or emulated on
+               BF16 tensor cores at 36 slice products per FP64 multiply-add).
+    k_band     dense -> band of half-width BW = 32, 4 n^3/3 in tile products (FP64 MMA or
+               emulated) plus the panel work (QR, T, W: about 4 n^2 BW FP64 flops).
+    k_chase    band -> tridiagonal by bulge chasing, about 6 n^2 BW FP64 flops."""
+    n = n.astype(np.float64)
+    bw = 32.0
+    if kernel == "k_tridiag":
+        flops = float(np.sum(4.0 * n ** 3 / 3.0))
+        fma_f, mma_f = flops / 2.0, flops / 2.0
+    elif kernel == "k_band":
+        gemm = float(np.sum(4.0 * n ** 3 / 3.0))
+        fma_f, mma_f = float(np.sum(4.0 * n ** 2 * bw)), gemm
+        flops = gemm + fma_f
+    else:  # k_chase
+        flops = float(np.sum(6.0 * n ** 2 * bw))
+        fma_f, mma_f = flops, 0.0
     if path == "fp64":
-        floor_s = half / (dfma * 1e12) + half / (dmma * 1e12)
-        src = (f"measured in-process: FP64 FMA {dfma:.3f} TFLOP/s (symv half) and FP64 MMA {dmma:.3f} TFLOP/s "
-               "(rank-2k half)")
+        floor_s = fma_f / (dfma * 1e12) + mma_f / (dmma * 1e12)
+        src = f"measured in-process: FP64 FMA {dfma:.3f}, FP64 MMA {dmma:.3f} TFLOP/s"
     else:
-        floor_s = half / (dfma * 1e12) + SLICE_PRODUCTS * half / (bf16 * 1e12)
-        src = (f"symv half on measured FP64 FMA {dfma:.3f} TFLOP/s; rank-2k half as {SLICE_PRODUCTS} BF16 slice "
+        floor_s = fma_f / (dfma * 1e12) + SLICE_PRODUCTS * mma_f / (bf16 * 1e12)
+        src = (f"FP64 part on measured FP64 FMA {dfma:.3f} TFLOP/s; tile products as {SLICE_PRODUCTS} BF16 slice "
                f"products per FP64 multiply-add at {bf16:.0f} TFLOP/s BF16, {bf16_src}")
     launch_s = k_ms / max(k_n, 1) / 1e3 if k_n else None
     achieved = flops / launch_s / 1e12 if launch_s else None
@@ -443,17 +460,23 @@ def roofline_report(kernel, path, n3, k_ms, k_n, dfma, dmma, bf16, bf16_src):
             "launch_ms": launch_s * 1e3 if launch_s else None}
 
 
-def step_fmin_report(path, n3, step_ms, dfma, dmma, bf16):
+def dominant(times):
+    """The roofline kernel with the largest time in a {kernel: (ms, launches)} map."""
+    have = [(times[k][0], k) for k in ROOFLINE_KERNELS if times.get(k, (0.0, 0))[1] > 0]
+    return max(have)[1] if have else "k_tridiag"
+
+
+def step_fmin_report(path, n3, step_ms, dfma, dmma, bf16, two_stage=False):
     """The whole step against its algorithmic minimum F_min = sum 8 n^3 / 3 (Cholesky
     n^3/3, symmetric congruence n^3, tridiagonalisation 4 n^3/3): FP64 path at the
-    1:1 FP64 FMA/MMA rate; mixed path with the tridiagonalisation's symv half
-    (2 n^3/3) on FP64 FMA and the rest emulated at 36 BF16 slice products per FP64
-    multiply-add."""
+    1:1 FP64 FMA/MMA rate; mixed path emulated at 36 BF16 slice products per FP64
+    multiply-add, except the one-stage tridiagonalisation's symv half (2 n^3/3),
+    which stays on FP64 FMA (with the two-stage form everything cubic is emulated)."""
     fmin = float(n3.sum() * 8.0 / 3.0)
     if path == "fp64":
         floor_s = fmin / (1e12 / (0.5 / dfma + 0.5 / dmma))
     else:
-        f64 = float(n3.sum() * 2.0 / 3.0)
+        f64 = 0.0 if two_stage else float(n3.sum() * 2.0 / 3.0)
         floor_s = f64 / (dfma * 1e12) + SLICE_PRODUCTS * (fmin - f64) / (bf16 * 1e12)
     return {"fmin_flops": fmin, "achieved_tflops": fmin / (step_ms / 1e3) / 1e12, "floor_ms": floor_s * 1e3,
             "frac": floor_s * 1e3 / step_ms}
@@ -514,7 +537,7 @@ def run_ours(args):
             dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launch_count() - l0
-    k_ms, k_n = ctx.kernel_time(DOMINANT)
+    t64 = {k: ctx.kernel_time(k) for k in KERNELS}
     ctx.set_profiling(False)
     clocks = clk.summary()
     gpu_samples = {}  # per path: spectra and the density rows at the FP64 step's mu (oracle comparison)
@@ -544,7 +567,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms_mx = ev0.elapsed_time(ev1)
-    kmx_ms, kmx_n = ctx.kernel_time(DOMINANT)
+    tmx = {k: ctx.kernel_time(k) for k in KERNELS}
     ctx.set_profiling(False)
     ms_mx = max_over_ranks(ms_mx, world, dev)
     keep_sample("mixed")
@@ -574,15 +597,21 @@ def run_ours(args):
     dfma, dmma = measure_fp64_peaks()
     bf16, bf16_src = bf16_peak()
     n3 = dims.astype(np.float64) ** 3
-    roofline = roofline_report(DOMINANT, "fp64", n3, k_ms, k_n, dfma, dmma, bf16, bf16_src)
+    k64 = dominant(t64)
+    roofline = roofline_report(k64, "fp64", dims, *t64[k64], dfma, dmma, bf16, bf16_src)
     roofline["step_fmin"] = step_fmin_report("fp64", n3, ms / args.steps, dfma, dmma, bf16)
+    roofline["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in t64.items() if v[1]}
+    kmx = dominant(tmx)
     mixed = {"value": replica_throughput(world, ncl, args.steps, ms_mx / 1e3), "unit": "clusters/s",
              "ms_per_step": ms_mx / args.steps,
              "speedup_vs_fp64": ms / ms_mx, "e_band_err_per_atom_vs_fp64": abs(e_mx - e_band) / s.natoms,
              "mu_diff_vs_fp64": abs(mu_mx - mu),
              "dtype": "bf16 slices (8 x 8 bit) emulating f64 contractions; f64 elsewhere",
-             "roofline": roofline_report(DOMINANT, "mixed", n3, kmx_ms, kmx_n, dfma, dmma, bf16, bf16_src)}
-    mixed["roofline"]["step_fmin"] = step_fmin_report("mixed", n3, ms_mx / args.steps, dfma, dmma, bf16)
+             "roofline": roofline_report(kmx, "mixed", dims, *tmx[kmx], dfma, dmma, bf16, bf16_src)}
+    mixed["roofline"]["step_fmin"] = step_fmin_report("mixed", n3, ms_mx / args.steps, dfma, dmma, bf16,
+                                                      two_stage=tmx.get("k_band", (0, 0))[1] > 0)
+    mixed["roofline"]["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in tmx.items() if v[1]}
+    mixed["tridiagonalisation"] = "two-stage (k_band + k_chase)" if tmx.get("k_band", (0, 0))[1] else "one-stage"
 
     scf = None
     if not args.no_scf:

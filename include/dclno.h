@@ -188,6 +188,22 @@ dclno_status dclno_batch_info(dclno_ctx *ctx, int *nbatches_out, size_t *workspa
  * each candidate (-1 = not tried).  The paper has no counterpart.
  */
 dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
+
+/*
+ * Form of the Householder tridiagonalisation in dclno_solve_clusters (Sec. II.C
+ * step (iii); both give the same T up to rounding and the same eigenpairs):
+ *   0  automatic (default): two-stage in the mixed path, one-stage in FP64;
+ *   1  one-stage: blocked Householder with a symmetric matrix-vector product per
+ *      column (each column reads the whole trailing matrix);
+ *   2  two-stage: dense -> band of half-width 32 (blocked Householder whose
+ *      products are all matrix-matrix tile products), band -> tridiagonal by
+ *      Householder bulge chasing.
+ * The two-stage form applies to clusters of dimension >= 128 (smaller ones use the
+ * one-stage form); it keeps a log of about n^2/2 doubles of chase reflectors per
+ * cluster, which the layout of dclno_build_clusters always reserves.  Takes effect
+ * at the next solve.  Errors: DCLNO_ERR_ARG for another mode.
+ */
+dclno_status dclno_set_tridiag(dclno_ctx *ctx, int mode);
 dclno_status dclno_get_tuning(dclno_ctx *ctx, int batch, int *ql_lanes_out, float *candidate_ms);
 
 /*
@@ -271,6 +287,29 @@ dclno_status dclno_density_matrix(dclno_ctx *ctx, double mu, double kT,
  */
 dclno_status dclno_density_matrices(dclno_ctx *ctx, double mu, double kT,
                                     double *rho_out, double *edm_out, double *eband_out);
+
+/*
+ * Density-matrix rows of every central atom from the Green function summed over
+ * the Matsubara poles (the paper's Appendix, Eq. (rho0j), in a non-orthogonal
+ * basis): rho^(i) = S^-1/2 + (2/beta) Re sum_{p>=0} (z_p S^(i) - H^(i))^-1 with
+ * z_p = mu + i (2p+1) pi kT, the same quantity as Eq. (dm) with Eq. (Gi) but without
+ * eigenvectors.  Each cluster is reduced as by dclno_solve_clusters (Cholesky,
+ * congruence, Householder tridiagonalisation T, in `precision`), then the first
+ * n_poles poles cost complex tridiagonal solves with T, and the poles beyond are
+ * summed from the large-|z| expansion of (z - T)^-1 to third order with Hurwitz
+ * zeta sums.  The rows go to the device array rho_out [nval] in the BSR pattern of
+ * S (zero outside the cluster, LNO columns returned to PAOs), as from
+ * dclno_density_matrix.  The expansion holds only when the first omitted pole lies
+ * well above the cluster's spectrum about mu: a cluster whose Gershgorin bound of
+ * |T - mu| exceeds (2 n_poles + 1) pi kT / 3 fails with DCLNO_ERR_ARG (cluster in
+ * the message).  Practical for narrow spectra only (the count grows with the
+ * spectral width over kT).  Needs LNOs (dclno_compute_lnos); overwrites the
+ * workspace of an earlier solve (call dclno_solve_clusters again before
+ * dclno_find_mu or dclno_density_matrix).  Allocates a scratch of
+ * 2 x 32 x 16 bytes per cluster, row and central basis function of a batch.
+ */
+dclno_status dclno_density_matrix_poles(dclno_ctx *ctx, double mu, double kT, int n_poles,
+                                        dclno_precision precision, double *rho_out);
 
 /*
  * One whole DC-LNO step: compute_lnos(rho_in), solve_clusters(precision),

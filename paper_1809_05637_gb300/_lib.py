@@ -23,7 +23,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
-           "dclno_get_lno_counts", "dclno_set_lno_mode"]
+           "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles"]
 
 
 class DclnoError(RuntimeError):
@@ -91,6 +91,8 @@ def load_library():
         "dclno_set_lno_threshold": ([P, I, D], I),
         "dclno_set_lno_mode": ([P, I], I),
         "dclno_get_lno_counts": ([P, P], I),
+        "dclno_set_tridiag": ([P, I], I),
+        "dclno_density_matrix_poles": ([P, D, D, I, I, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -214,6 +216,10 @@ class Context:
         self._check(self.lib.dclno_get_lno_counts(self.h, _ptr(k)))
         return k
 
+    def set_tridiag(self, mode):
+        """Tridiagonalisation form: 0 automatic, 1 one-stage, 2 two-stage (dense -> band -> tridiagonal)."""
+        self._check(self.lib.dclno_set_tridiag(self.h, int(mode)))
+
     def set_autotune(self, on=True):
         """Time the QL launch shape on each batch's first eager solve (default on)."""
         self._check(self.lib.dclno_set_autotune(self.h, int(bool(on))))
@@ -270,6 +276,11 @@ class Context:
         e = ctypes.c_double()
         self._check(self.lib.dclno_density_matrix(self.h, float(mu), float(kT), _ptr(rho_out), _dptr(e)))
         return e.value
+
+    def density_matrix_poles(self, mu, kT, n_poles, rho_out, precision=DCLNO_FP64):
+        """rho rows from the Matsubara pole sum (no eigenvectors); invalidates an earlier solve."""
+        self._check(self.lib.dclno_density_matrix_poles(self.h, float(mu), float(kT), int(n_poles), int(precision),
+                                                        _ptr(rho_out)))
 
     def density_matrices(self, mu, kT, rho_out, edm_out):
         """rho and the energy density matrix e (Eq. (edm)) rows; returns the band energy."""

@@ -64,6 +64,9 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_hist);
     dfree(c->d_tune);
     dfree(c->d_kat);
+    if (c->d_pole) cudaFree(c->d_pole);
+    c->d_pole = nullptr;
+    c->pole_bytes = 0;
     c->tune_doubles = 0;
     c->ql_lanes.clear();
     c->ql_tune_ms.clear();
@@ -447,9 +450,14 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     // W (32 ld), P ([n][2 mc]), rotation logs (2 rot_cap per segment), for a torn problem the merge
     // matrix and its transpose (n x ld each); 256-byte aligned.  Sweep headers: it_cap ints per segment.
     auto nseg = [](const ClusterDesc& d) { return d.split ? 2LL : 1LL; };
+    // the two-stage reduction's chase reflectors (kept until the density rows are written);
+    // it also borrows the merge-matrix area as scratch, so only torn clusters qualify
+    auto q2_doubles = [](const ClusterDesc& d) {
+        return (d.split && d.n >= DCLNO_TWO_STAGE_MIN) ? (long long)DCLNO_BW * band_refl_count(d.n) : 0LL;
+    };
     auto ws_doubles = [&](const ClusterDesc& d) {
         const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap * nseg(d) +
-                            (d.split ? 2LL * d.n * d.ld : 0LL);
+                            (d.split ? 2LL * d.n * d.ld : 0LL) + ((q2_doubles(d) + 3) & ~3LL);
         return (m + 31) & ~31LL;
     };
     auto ws_bytes = [&](const ClusterDesc& d) { return 8 * ws_doubles(d) + 4LL * d.it_cap * nseg(d); };
@@ -514,6 +522,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
             d.cc_off = d.aux_off + 35LL * d.ld;
             d.rot_off = d.cc_off + 2LL * d.mc * d.ld;
             d.m_off = d.rot_off + 2LL * d.rot_cap * nseg(d);
+            d.q2_off = q2_doubles(d) ? d.m_off + (d.split ? 2LL * d.n * d.ld : 0LL) : -1;
             mat += ws_doubles(d);
             d.it_off = its;
             its += (long long)d.it_cap * nseg(d);
@@ -736,6 +745,7 @@ static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
 
 // every batch: assemble + solve (eps and q of all clusters)
 static dclno_status solve_all(dclno_ctx* c, dclno_precision prec) {
+    c->solved_two = c->tridiag_mode == 2 || (c->tridiag_mode == 0 && prec == DCLNO_MIXED);
     dclno_status st = launch_lno_blocks(c);
     for (int bi = 0; st == DCLNO_OK && bi < (int)c->batches.size(); ++bi) st = solve_batch(c, bi, prec);
     if (st == DCLNO_OK) c->solved_prec = prec;
@@ -819,10 +829,67 @@ extern "C" dclno_status dclno_density_matrices(dclno_ctx* c, double mu, double k
     return read_eband(c, eband_out);
 }
 
+// statuses of a batch after a launch sequence (host synchronisation)
+static dclno_status check_batch_status(dclno_ctx* c, const Batch& b, const char* who) {
+    const int nid = b.id_hi - b.id_lo;
+    std::vector<int> st(nid);
+    DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status + b.id_lo, sizeof(int) * nid, cudaMemcpyDeviceToHost,
+                                  c->stream));
+    DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nid; ++k) {
+        const int i = b.id_lo + k;
+        if (st[k] == ST_OK) continue;
+        const std::string id = std::string(who) + ": cluster " + std::to_string(i);
+        if (st[k] == ST_NOT_SPD) return set_err(c, DCLNO_ERR_NOT_SPD, id + ": overlap not positive definite");
+        if (st[k] == ST_FEW_POLES)
+            return set_err(c, DCLNO_ERR_ARG, id + ": too few poles (the first omitted pole is below three times the "
+                                                  "spectral radius of the cluster about mu)");
+        return set_err(c, DCLNO_ERR_NOT_CONVERGED, id + ": status " + std::to_string(st[k]));
+    }
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_density_matrix_poles(dclno_ctx* c, double mu, double kT, int n_poles,
+                                                   dclno_precision prec, double* rho_out) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (!c->built) return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix_poles: build clusters first");
+    if (!c->lnos_ready) return set_err(c, DCLNO_ERR_NO_LNOS, "dclno_density_matrix_poles: compute LNOs first");
+    if (!(kT > 0.0) || n_poles < 1 || !rho_out || !(mu == mu))
+        return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix_poles: need kT > 0, n_poles >= 1, rho_out");
+    if (prec != DCLNO_FP64 && prec != DCLNO_MIXED)
+        return set_err(c, DCLNO_ERR_ARG, "dclno_density_matrix_poles: unknown precision");
+    // the reduction overwrites the workspace of any earlier solve
+    c->solved = false;
+    c->resident = -1;
+    c->solved_two = c->tridiag_mode == 2 || (c->tridiag_mode == 0 && prec == DCLNO_MIXED);
+    c->solved_prec = prec;
+    dclno_status st = launch_lno_blocks(c);
+    for (int bi = 0; st == DCLNO_OK && bi < (int)c->batches.size(); ++bi) {
+        const Batch& b = c->batches[bi];
+        st = launch_assemble(c, b);
+        if (st == DCLNO_OK)
+            st = (prec == DCLNO_MIXED) ? launch_solve_mixed(c, b, true) : launch_solve_fp64(c, b, true);
+        if (st == DCLNO_OK) st = launch_poles(c, b, mu, kT, n_poles);
+        if (st == DCLNO_OK) st = check_batch_status(c, b, "dclno_density_matrix_poles");
+        if (st == DCLNO_OK) st = launch_density(c, b, mu, kT, rho_out, nullptr, true);
+    }
+    if (st == DCLNO_OK) DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    return st;
+}
+
 extern "C" dclno_status dclno_set_workspace_limit(dclno_ctx* c, size_t bytes) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
     c->ws_limit = bytes;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (mode < 0 || mode > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_tridiag: mode must be 0, 1 or 2");
+    c->tridiag_mode = mode;
     return DCLNO_OK;
 }
 

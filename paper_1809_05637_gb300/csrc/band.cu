@@ -1,0 +1,425 @@
+// Two-stage Householder tridiagonalisation of the congruence-transformed cluster
+// matrix A = L^-1 H^(i) L^-T (Sec. II.C step (iii)), the alternative to the one-stage
+// k_tridiag for clusters of dimension >= DCLNO_TWO_STAGE_MIN.
+//
+//   k_band   A = Q1 B Q1^T, B symmetric with half-bandwidth BW: panels of BW columns,
+//            each a Householder QR of the block below the band (BW reflectors in
+//            compact WY form I - V T V^T), then the two-sided update of the trailing
+//            matrix A22 <- A22 - V W^T - W V^T with W = Y T - 1/2 V (T^T V^T Y T),
+//            Y = A22 V.  Y, V^T [V | Y] and the rank-2 BW update are tile GEMMs (FP64
+//            MMA, or FP64 emulated on BF16 tensor cores in the mixed path), so the
+//            matrix-vector products of the one-stage reduction become matrix-matrix
+//            products that read A22 once per panel instead of once per column.
+//   k_chase  B = Q2 T Q2^T, T tridiagonal: Householder bulge chasing.  Sweep j
+//            annihilates column j below its subdiagonal with a reflector on rows
+//            [j+1, j+1+BW); its application from the right fills the block below the
+//            window (the bulge), whose first column the next reflector, BW rows
+//            further down, annihilates, and so on to the end of the matrix.  What
+//            remains of each bulge lies in the columns that later sweeps annihilate,
+//            so the matrix never grows beyond half-bandwidth 2 BW - 1.
+//
+// Storage (per cluster): the band and the bulges in A's lower triangle (zero below the
+// band after k_band); the panel reflectors Q1 row-contiguous in A's otherwise unused
+// upper triangle (reflector of column c in row c from column c + BW on, unit entry
+// stored) with tau in the aux tau vector (0 where column c has none); the chase
+// reflectors Q2 in the cluster's log at q2_off, one slot of BW doubles per reflector
+// in generation order: [tau, v_1 .. v_{len-1}] (v_0 = 1).  The merge-matrix area, not
+// used until after the tridiagonal eigensolve, is k_band's scratch.
+#include "dclno_internal.cuh"
+#include "emu_gemm.cuh"
+
+#define BW DCLNO_BW
+#define TL (BW + 1)  // row stride of the BW x BW shared-memory blocks
+
+// shared memory of k_band: GEMM staging (also the mirror's transpose tiles), T, M,
+// reduction scratch
+__host__ __device__ inline size_t band_gemm_doubles(bool emu) {
+    const size_t g = emu ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
+    const size_t mirror = 8 * 32 * 33;  // eight warps' 32 x 33 transpose tiles
+    return g > mirror ? g : mirror;
+}
+__host__ __device__ inline size_t band_smem_bytes(bool emu) {
+    return (band_gemm_doubles(emu) + 2 * BW * TL + 64) * sizeof(double);
+}
+
+// upper triangle of the trailing block [r0, n)^2 <- its lower triangle (32 x 32 tiles
+// through shared memory, one tile per warp at a time)
+__device__ static void mirror_lower(double* A, int ld, int r0, int n, double* tiles) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double* T = tiles + (size_t)warp * 32 * 33;
+    const int nt = (n - r0 + 31) / 32;
+    for (int t = warp; t < nt * (nt + 1) / 2; t += nw) {
+        // tile (bi, bj) of the lower triangle, bj <= bi; copied transposed to (bj, bi)
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        const int rb = r0 + 32 * bi, cb = r0 + 32 * bj;
+        for (int r = 0; r < 32; ++r) {
+            const int gr = rb + r, gc = cb + lane;
+            T[r * 33 + lane] = (gr < n && gc < n && gc <= gr) ? A[(size_t)gr * ld + gc] : 0.0;
+        }
+        __syncwarp();
+        // element (gr, gc), gc < gr, goes to (gc, gr): row cb + c of the upper triangle
+        for (int c = 0; c < 32; ++c) {
+            const int gr = rb + lane, gc = cb + c;
+            if (gr < n && gc < n && gc < gr) A[(size_t)gc * ld + gr] = T[lane * 33 + c];
+        }
+        __syncwarp();
+    }
+}
+
+template <bool EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_band(const ClusterDesc* __restrict__ cls,
+                                                                                 const int* __restrict__ order,
+                                                                                 double* __restrict__ arena,
+                                                                                 const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!two_stage_cluster(d)) return;
+    const int n = d.n, ld = d.ld;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    double* A = arena + d.mat_off;
+    double* tauv = arena + d.aux_off + 2 * ld;
+    double* W = arena + d.aux_off + 3 * ld;   // m x BW (stride BW)
+    double* Vx = arena + d.m_off;             // m x BW (stride BW): the panel's reflectors, explicit
+    double* NVt = Vx + (size_t)BW * ld;       // BW x m (stride ld): -V^T
+    double* Yt = NVt + (size_t)BW * ld;       // BW x m (stride ld): Y^T = V^T A22
+    double* GZ = Yt + (size_t)BW * ld;        // [-V^T V | V^T Y], BW x 2BW (row stride gz)
+    const int gz = 2 * BW + 1;
+    double* G = sm;
+    double* Ts = sm + band_gemm_doubles(EMU);  // T (upper triangular)
+    double* Ms = Ts + BW * TL;                 // T^T (V^T Y) T
+    double* red = Ms + BW * TL;
+
+    for (int t = tid; t < n; t += blockDim.x) tauv[t] = 0.0;
+    __syncthreads();
+    for (int c0 = 0; c0 + BW < n; c0 += BW) {
+        const int r0 = c0 + BW, m = n - r0;
+        const int nbr = min(BW, m);  // reflectors of this panel (one per column with rows below the band)
+        // (1) Householder QR of the panel block A[r0:n, c0:c0+BW]; reflector j acts on rows r0+j ..
+        for (int j = 0; j < nbr; ++j) {
+            const int c = c0 + j, rs = r0 + j;
+            const double alpha = A[(size_t)rs * ld + c];
+            double sig = 0.0;
+            for (int r = rs + 1 + tid; r < n; r += blockDim.x) {
+                const double a = A[(size_t)r * ld + c];
+                sig = fma(a, a, sig);
+            }
+            sig = block_sum(sig, red);
+            double tau = 0.0, beta = alpha, scale = 0.0;
+            if (sig > 0.0) {
+                const double nrm = sqrt(alpha * alpha + sig);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            for (int r = rs + 1 + tid; r < n; r += blockDim.x) A[(size_t)r * ld + c] *= scale;
+            __syncthreads();
+            if (tid == 0) {
+                A[(size_t)rs * ld + c] = beta;
+                tauv[c] = tau;
+            }
+            if (tau != 0.0) {
+                // the remaining panel columns: x <- x - tau (v . x) v over rows rs .. n-1
+                for (int cc = c + 1 + warp; cc < c0 + BW; cc += nw) {
+                    double w = (lane == 0) ? A[(size_t)rs * ld + cc] : 0.0;
+                    for (int r = rs + 1 + lane; r < n; r += 32) w = fma(A[(size_t)r * ld + c], A[(size_t)r * ld + cc], w);
+                    w = tau * warp_sum(w);
+                    if (lane == 0) A[(size_t)rs * ld + cc] -= w;
+                    for (int r = rs + 1 + lane; r < n; r += 32)
+                        A[(size_t)r * ld + cc] = fma(-w, A[(size_t)r * ld + c], A[(size_t)r * ld + cc]);
+                }
+            }
+            __syncthreads();
+        }
+        // (2) explicit V (unit diagonal, zero above) and -V^T; the reflectors' row-contiguous
+        // copies for the back-transforms in the upper triangle (row c from column c + BW);
+        // the lower triangle below the band is cleared for the chase
+        for (int e = tid; e < m * BW; e += blockDim.x) {
+            const int t = e / BW, j = e % BW;
+            const double v = (j >= nbr || t < j) ? 0.0 : (t == j ? 1.0 : A[(size_t)(r0 + t) * ld + c0 + j]);
+            Vx[e] = v;
+            NVt[(size_t)j * ld + t] = -v;
+            if (j < nbr && t >= j) A[(size_t)(c0 + j) * ld + r0 + t] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < m * BW; e += blockDim.x) {
+            const int t = e / BW, j = e % BW;
+            if (j < nbr && t > j) A[(size_t)(r0 + t) * ld + c0 + j] = 0.0;
+        }
+        // (3) the trailing block in full (upper triangle from the lower) for Y = A22 V
+        mirror_lower(A, ld, r0, n, G);
+        __syncthreads();
+        // (4) Y^T = V^T A22: C -= (-V^T) A22^T with A22 symmetric
+        double* A22 = A + (size_t)r0 * ld + r0;
+        for (int e = tid; e < BW * m; e += blockDim.x) Yt[(size_t)(e / m) * ld + e % m] = 0.0;
+        __syncthreads();
+        tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G);
+        // (5) [-V^T V | V^T Y] = -(-V^T) [-V^T ; Y^T]^T ... as C -= A B^T with B = the 2BW rows
+        // of NVt and Yt (contiguous, stride ld): C = -(V^T V) on the left, +V^T Y on the right
+        for (int e = tid; e < BW * gz; e += blockDim.x) GZ[e] = 0.0;
+        __syncthreads();
+        tile_update_longk<EMU>(GZ, gz, NVt, ld, NVt, ld, BW, 2 * BW, m, G);
+        // (6) T (upper triangular): T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j]
+        if (warp == 0) {
+            for (int j = 0; j < BW; ++j) {
+                const double tj = (j < nbr) ? tauv[c0 + j] : 0.0;
+                double s = 0.0;
+                if (lane < j)
+                    for (int l = lane; l < j; ++l) s = fma(Ts[lane * TL + l], -GZ[l * gz + j], s);
+                __syncwarp();
+                if (lane < j) Ts[lane * TL + j] = -tj * s;
+                if (lane == j) Ts[j * TL + j] = tj;
+                if (lane > j) Ts[lane * TL + j] = 0.0;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // (7) M = T^T (V^T Y) T  (BW x BW, symmetric): first P = (V^T Y) T into Ms, then T^T P
+        for (int e = tid; e < BW * BW; e += blockDim.x) {
+            const int a = e / BW, b = e % BW;
+            double s = 0.0;
+            for (int l = 0; l <= b; ++l) s = fma(GZ[a * gz + BW + l], Ts[l * TL + b], s);
+            Ms[a * TL + b] = s;
+        }
+        __syncthreads();
+        {
+            double mv[BW / 8];
+            for (int q = 0; q < BW * BW / DCLNO_SOLVE_THREADS; ++q) {
+                const int e = tid + q * DCLNO_SOLVE_THREADS, a = e / BW, b = e % BW;
+                double s = 0.0;
+                for (int l = 0; l <= a; ++l) s = fma(Ts[l * TL + a], Ms[l * TL + b], s);
+                mv[q] = s;
+            }
+            __syncthreads();
+            for (int q = 0; q < BW * BW / DCLNO_SOLVE_THREADS; ++q) {
+                const int e = tid + q * DCLNO_SOLVE_THREADS;
+                Ms[(e / BW) * TL + e % BW] = mv[q];
+            }
+        }
+        __syncthreads();
+        // (8) W = Y T - 1/2 V M (m x BW), one row t per thread, in two passes; the row's
+        // operands are staged in the (now idle) GEMM area, one column per thread
+        {
+            double* Zs = G;  // BW x blockDim
+            const int nt = blockDim.x;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int t0 = 0; t0 < m; t0 += nt) {
+                    const int t = t0 + tid;
+                    if (t < m) {
+                        for (int a = 0; a < BW; ++a)
+                            Zs[a * nt + tid] = pass == 0 ? Yt[(size_t)a * ld + t] : Vx[(size_t)t * BW + a];
+                        for (int b = 0; b < BW; ++b) {
+                            double s = pass == 0 ? 0.0 : W[(size_t)t * BW + b];
+                            if (pass == 0)
+                                for (int a = 0; a <= b; ++a) s = fma(Ts[a * TL + b], Zs[a * nt + tid], s);
+                            else
+                                for (int a = 0; a < BW; ++a) s = fma(-0.5 * Ms[a * TL + b], Zs[a * nt + tid], s);
+                            W[(size_t)t * BW + b] = s;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (9) A22 <- A22 - V W^T - W V^T (lower triangle)
+        tile_update<true, EMU>(A22, ld, Vx, BW, W, BW, m, m, BW, 0, G);
+        tile_update<true, EMU>(A22, ld, W, BW, Vx, BW, m, m, BW, 0, G);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulge chasing, one warp per cluster.  Window blocks are staged in shared memory:
+// D (the symmetric diagonal block of the current reflector) and O (the block below
+// the window, which the reflector fills from the right; it is carried to the next
+// step, whose reflector annihilates its first column and is applied to the rest of it
+// from the left).
+// ---------------------------------------------------------------------------
+struct Refl {
+    double v, tau, beta;  // this lane's entry of v (v_0 = 1), tau, new leading entry
+};
+
+// reflector H = I - tau v v^T with H x = beta e_0 for x = (lane < len ? x : 0)
+__device__ __forceinline__ Refl warp_householder(double x, int len) {
+    const int lane = threadIdx.x & 31;
+    const double alpha = __shfl_sync(0xffffffffu, x, 0);
+    const double sig = warp_sum((lane >= 1 && lane < len) ? x * x : 0.0);
+    Refl h;
+    h.tau = 0.0;
+    h.beta = alpha;
+    h.v = (lane == 0) ? 1.0 : 0.0;
+    if (sig > 0.0) {
+        const double nrm = sqrt(alpha * alpha + sig);
+        h.beta = (alpha >= 0.0) ? -nrm : nrm;
+        h.tau = (h.beta - alpha) / h.beta;
+        if (lane >= 1 && lane < len) h.v = x / (alpha - h.beta);
+    }
+    return h;
+}
+
+// D <- H D H for the symmetric window [p, p + len) (lower triangle in A)
+__device__ static void chase_two_sided(double* A, int ld, int p, int len, const Refl& h, double* Ds) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int i = 0; i < len; ++i)
+        if (lane <= i) {
+            const double a = A[(size_t)(p + i) * ld + p + lane];
+            Ds[i * TL + lane] = a;
+            Ds[lane * TL + i] = a;
+        }
+    __syncwarp();
+    double y0 = 0.0, y1 = 0.0;
+    for (int c = 0; c < len; c += 2) {
+        const double v0 = __shfl_sync(0xffffffffu, h.v, c);
+        const double v1 = __shfl_sync(0xffffffffu, h.v, c + 1);
+        if (lane < len) {
+            y0 = fma(Ds[lane * TL + c], v0, y0);
+            if (c + 1 < len) y1 = fma(Ds[lane * TL + c + 1], v1, y1);
+        }
+    }
+    const double y = h.tau * (y0 + y1);
+    const double dot = warp_sum(lane < len ? h.v * y : 0.0);
+    const double w = y - 0.5 * h.tau * dot * h.v;
+    for (int i = 0; i < len; ++i) {
+        const double vi = __shfl_sync(0xffffffffu, h.v, i), wi = __shfl_sync(0xffffffffu, w, i);
+        if (lane <= i) A[(size_t)(p + i) * ld + p + lane] = Ds[i * TL + lane] - vi * w - wi * h.v;
+    }
+    __syncwarp();
+}
+
+// Os (rows [p + len, p + len + nr) x cols [p, p + len)) loaded and multiplied by H from the right
+__device__ static void chase_right(const double* A, int ld, int p, int len, int nr, const Refl& h, double* Os) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int r = 0; r < nr; ++r) Os[r * TL + lane] = (lane < len) ? A[(size_t)(p + len + r) * ld + p + lane] : 0.0;
+    __syncwarp();
+    double s0 = 0.0, s1 = 0.0;
+    for (int c = 0; c < len; c += 2) {
+        const double v0 = __shfl_sync(0xffffffffu, h.v, c);
+        const double v1 = __shfl_sync(0xffffffffu, h.v, c + 1);
+        if (lane < nr) {
+            s0 = fma(Os[lane * TL + c], v0, s0);
+            if (c + 1 < len) s1 = fma(Os[lane * TL + c + 1], v1, s1);
+        }
+    }
+    const double s = h.tau * (s0 + s1);
+    for (int r = 0; r < nr; ++r) {
+        const double sr = __shfl_sync(0xffffffffu, s, r);
+        if (lane < len) Os[r * TL + lane] = fma(-sr, h.v, Os[r * TL + lane]);
+    }
+    __syncwarp();
+}
+
+__device__ static void chase_store(double* A, int ld, int row0, int col0, int nr, int nc, const double* Os) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < nr; ++r)
+        if (lane < nc) A[(size_t)(row0 + r) * ld + col0 + lane] = Os[r * TL + lane];
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                                              double* __restrict__ arena, const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    double* Ds = sm;
+    double* Os = sm + BW * TL;
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!two_stage_cluster(d)) return;
+    const int n = d.n, ld = d.ld, lane = threadIdx.x;
+    double* A = arena + d.mat_off;
+    double* slot = arena + d.q2_off;
+    for (int j = 0; j + 2 < n; ++j) {
+        const int nsteps = (int)chase_steps(n, j);
+        int p = j + 1, len = min(BW, n - p);
+        // step 0: column j below its subdiagonal
+        Refl h = warp_householder(lane < len ? A[(size_t)(p + lane) * ld + j] : 0.0, len);
+        if (lane < len) A[(size_t)(p + lane) * ld + j] = (lane == 0) ? h.beta : 0.0;
+        if (lane == 0) slot[0] = h.tau;
+        else if (lane < len) slot[lane] = h.v;
+        slot += BW;
+        chase_two_sided(A, ld, p, len, h, Ds);
+        int nr = max(0, min(BW, n - p - len));
+        chase_right(A, ld, p, len, nr, h, Os);
+        for (int k = 1; k < nsteps; ++k) {
+            // the carried block O holds rows [p + BW, ...) x cols [p, p + BW) (len == BW here)
+            const int pp = p;
+            p = pp + BW;
+            len = min(BW, n - p);  // == nr
+            h = warp_householder(lane < len ? Os[lane * TL] : 0.0, len);
+            if (lane < len) Os[lane * TL] = (lane == 0) ? h.beta : 0.0;
+            if (lane == 0) slot[0] = h.tau;
+            else if (lane < len) slot[lane] = h.v;
+            slot += BW;
+            __syncwarp();
+            // from the left on the carried block's other columns (lane = column)
+            {
+                double s0 = 0.0, s1 = 0.0;
+                for (int i = 0; i < len; i += 2) {
+                    const double v0 = __shfl_sync(0xffffffffu, h.v, i);
+                    const double v1 = __shfl_sync(0xffffffffu, h.v, i + 1);
+                    if (lane >= 1) {
+                        s0 = fma(v0, Os[i * TL + lane], s0);
+                        if (i + 1 < len) s1 = fma(v1, Os[(i + 1) * TL + lane], s1);
+                    }
+                }
+                const double s = h.tau * (s0 + s1);
+                for (int i = 0; i < len; ++i) {
+                    const double vi = __shfl_sync(0xffffffffu, h.v, i);
+                    if (lane >= 1) Os[i * TL + lane] = fma(-s, vi, Os[i * TL + lane]);
+                }
+                __syncwarp();
+            }
+            chase_store(A, ld, p, pp, len, BW, Os);
+            chase_two_sided(A, ld, p, len, h, Ds);
+            nr = max(0, min(BW, n - p - len));
+            chase_right(A, ld, p, len, nr, h, Os);
+        }
+        chase_store(A, ld, p + len, p, nr, len, Os);
+    }
+    // the tridiagonal matrix: d, e into the aux vectors, then Cuppen's tear as in k_tridiag
+    double* dv = arena + d.aux_off;
+    double* ev = dv + ld;
+    for (int t = lane; t < n; t += 32) {
+        dv[t] = A[(size_t)t * ld + t];
+        ev[t] = (t + 1 < n) ? A[(size_t)(t + 1) * ld + t] : 0.0;
+    }
+    __syncwarp();
+    if (d.split && lane == 0) {
+        double* W = dv + 3 * ld;
+        const int k = d.split;
+        const double beta = ev[k - 1];
+        W[n] = beta;
+        ev[k - 1] = 0.0;
+        dv[k - 1] -= fabs(beta);
+        dv[k] -= fabs(beta);
+    }
+}
+
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool emu) {
+    const int N = b.oend - b.obeg;
+    if (N == 0) return DCLNO_OK;
+    const int* order = c->d_order + b.obeg;
+    const size_t smb = band_smem_bytes(emu);
+    if (smb > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "band reduction: shared memory");
+    {
+        ProfScope ps__(c, "k_band");
+        if (emu) {
+            DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+            k_band<true><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+        } else {
+            DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+            k_band<false><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+        }
+    }
+    DCLNO_LAUNCHED(c);
+    {
+        ProfScope ps__(c, "k_chase");
+        const size_t sm2 = 2 * BW * TL * sizeof(double);
+        k_chase<<<N, 32, sm2, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+    }
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}

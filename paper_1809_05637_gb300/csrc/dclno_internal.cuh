@@ -38,7 +38,25 @@ struct ClusterDesc {
     int split;          // tear point k of the tridiagonal matrix (segments [0,k), [k,n)); 0 = no tear
     long long pair_off; // offset of the cluster's member-pair block table (nmem x nmem ints)
     long long m_off;    // arena offset of the merge matrix M (n x ld) and its transpose (n x ld); split only
+    long long q2_off;   // arena offset of the bulge-chasing reflector log of the two-stage reduction
+                        // (band_refl_count(n) slots of DCLNO_BW doubles), -1 if the cluster is too small
 };
+
+// Two-stage tridiagonalisation: A -> band of half-width DCLNO_BW (blocked Householder,
+// k_band) -> tridiagonal (Householder bulge chasing, k_chase).  Sweep j of the chase
+// (j = 0 .. n-3) uses reflectors k = 0, 1, ... acting on rows [p, p + min(BW, n - p))
+// with p = j + 1 + k BW while p + 1 < n.
+#define DCLNO_BW 32
+#define DCLNO_TWO_STAGE_MIN 128  // clusters of at least this dimension (and torn) may use it
+__host__ __device__ inline long long chase_steps(int n, int j) {
+    const int r = n - 2 - j;
+    return r > 0 ? (r + DCLNO_BW - 1) / DCLNO_BW : 0;
+}
+__host__ __device__ inline long long band_refl_count(int n) {
+    long long s = 0;
+    for (int j = 0; j + 2 < n; ++j) s += chase_steps(n, j);
+    return s;
+}
 
 // segment s (0, 1) of a cluster's tridiagonal problem: first index and length
 __host__ __device__ inline int seg_start(const ClusterDesc& d, int s) { return s ? d.split : 0; }
@@ -76,6 +94,7 @@ enum : int {
     ST_NOT_CONVERGED = 2,
     ST_LOG_FULL = 3,
     ST_BAD_LNO = 4,
+    ST_FEW_POLES = 5,  // the Matsubara pole sum was asked for too few poles for this cluster
 };
 
 // A memory-admitted batch: a contiguous range of cluster ids whose workspace is
@@ -131,6 +150,11 @@ struct dclno_ctx {
     std::vector<Batch> batches;       // memory-admitted batches (one when everything fits)
     int resident = -1;                // batch whose solved workspace is in the arena
     dclno_precision solved_prec = DCLNO_FP64;
+    // tridiagonalisation: 0 = automatic (two-stage in the mixed path, one-stage in FP64),
+    // 1 = one-stage, 2 = two-stage (for the clusters that qualify); solved_two = the form
+    // the last solve used (the density pass applies the same Q)
+    int tridiag_mode = 0;
+    bool solved_two = false;
     size_t ws_limit = 0;              // workspace limit in bytes (0 = free device memory)
     // launch-shape autotuner: QL lanes per warp chosen per batch by timing (0 = not yet)
     bool autotune = true;
@@ -138,6 +162,8 @@ struct dclno_ctx {
     std::vector<float> ql_tune_ms;    // per batch: the timed candidates (lanes 4, 8, 12, 16, 24, 32)
     double* d_tune = nullptr;         // saved d, e of a batch while candidates are timed
     size_t tune_doubles = 0;
+    void* d_pole = nullptr;           // scratch of the Matsubara pole sum (pivots, solutions per pole)
+    size_t pole_bytes = 0;
     std::vector<MemberDesc> mem;
     long long total_dim = 0;
     ClusterDesc* d_cl = nullptr;
@@ -247,15 +273,20 @@ dclno_status relayout_clusters(dclno_ctx* c);
 dclno_status launch_lno_blocks(dclno_ctx* c);
 dclno_status launch_assemble(dclno_ctx* c, const Batch& b);
 dclno_status launch_pair_index(dclno_ctx* c);
-dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b);
-dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b);
+// reduce_only: Cholesky, congruence, tridiagonalisation and the central strips P = [R1 Q; R2 Q]
+// only (the Matsubara pole route), without the tridiagonal eigensolve and the weights
+dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only = false);
+dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only = false);
+dclno_status launch_poles(dclno_ctx* c, const Batch& b, double mu, double kT, int npoles);
 dclno_status launch_merge(dclno_ctx* c, const Batch& b);
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool emu);
 // Y <- X Y for the torn clusters of a batch: dir 0 = central strips P <- M^T P (after the
 // forward replay), dir 1 = density columns G <- M G (before the reverse replay)
 dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
+// poles: the density columns G are already formed (k_poles); only L^-T Q G and the scatter
 dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out,
-                            double* e_out = nullptr);
+                            double* e_out = nullptr, bool poles = false);
 dclno_status launch_status_or(dclno_ctx* c);
 dclno_status launch_scf_tail(dclno_ctx* c, double* rho, const double* rho_out, double alpha);
 
@@ -376,6 +407,70 @@ __host__ __device__ __forceinline__ void sweep_rev(double* __restrict__ X, size_
     X[(size_t)(ib + cnt) * stride] = wi;
 }
 #define DCLNO_REPLAY_DEPTH 1  // the replays run many warps per SM and are bound by the FP64 pipe
+
+// A cluster reduced by the two-stage tridiagonalisation (band.cu) when that mode is on.
+__device__ __forceinline__ bool two_stage_cluster(const ClusterDesc& d) {
+    return d.q2_off >= 0 && d.split && d.n >= DCLNO_TWO_STAGE_MIN;
+}
+
+// Chase reflector H = I - tau v v^T of the two-stage reduction, log slot
+// [tau, v_1 .. v_{len-1}] (v_0 = 1), acting on entries [p, p + len) of the R
+// consecutive rows of X (row stride ldx) that this warp owns: x <- x - tau (x . v) v.
+template <int R>
+__device__ __forceinline__ void warp_reflect_short(double* X, int ldx, int p, int len,
+                                                   const double* __restrict__ slot) {
+    const int lane = threadIdx.x & 31;
+    const double tau = slot[0];
+    if (tau == 0.0) return;  // the same for every lane
+    const double v = (lane == 0) ? 1.0 : (lane < len ? slot[lane] : 0.0);
+    double u[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) u[j] = (lane < len) ? X[(size_t)j * ldx + p + lane] * v : 0.0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) u[j] = tau * warp_sum(u[j]);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        if (lane < len) X[(size_t)j * ldx + p + lane] = fma(-u[j], v, X[(size_t)j * ldx + p + lane]);
+}
+
+// The two-stage factor Q = Q1 Q2 (A = Q T Q^T) on the R rows of X owned by this warp:
+// Q1 = the panel reflectors (reflector c in row c of A's upper triangle from column
+// c + BW on, tau[c], 0 where there is none), Q2 = the chase log q2 in generation order.
+// dir 0: X <- X Q (the central strips, reflectors in their order); dir 1: each row x of
+// X <- Q x (the density columns stored as rows, reflectors in reverse order: each
+// reflector is symmetric).
+template <int R>
+__device__ __forceinline__ void warp_apply_two_stage(double* X, int n, const double* __restrict__ A, int ld,
+                                                     const double* __restrict__ tau, const double* __restrict__ q2,
+                                                     int dir) {
+    if (dir == 0) {
+        for (int c = 0; c + DCLNO_BW < n; ++c) {
+            const double tc = tau[c];
+            if (tc != 0.0) warp_reflect<R>(X, n, c + DCLNO_BW - 1, n, A + (size_t)c * ld, tc);
+        }
+        const double* slot = q2;
+        for (int j = 0; j + 2 < n; ++j) {
+            const int ns = (int)chase_steps(n, j);
+            for (int k = 0; k < ns; ++k, slot += DCLNO_BW) {
+                const int p = j + 1 + k * DCLNO_BW;
+                warp_reflect_short<R>(X, n, p, min(DCLNO_BW, n - p), slot);
+            }
+        }
+        return;
+    }
+    const double* slot = q2 + (band_refl_count(n) - 1) * DCLNO_BW;
+    for (int j = n - 3; j >= 0; --j) {
+        const int ns = (int)chase_steps(n, j);
+        for (int k = ns - 1; k >= 0; --k, slot -= DCLNO_BW) {
+            const int p = j + 1 + k * DCLNO_BW;
+            warp_reflect_short<R>(X, n, p, min(DCLNO_BW, n - p), slot);
+        }
+    }
+    for (int c = n - 1 - DCLNO_BW; c >= 0; --c) {
+        const double tc = tau[c];
+        if (tc != 0.0) warp_reflect<R>(X, n, c + DCLNO_BW - 1, n, A + (size_t)c * ld, tc);
+    }
+}
 
 // One FP64 tensor-core MMA: D(8x8) += A(8x4, row) * B(4x8, col).
 // Fragments (per lane l): a = A[l/4][l%4], b = B[l%4][l/4],

@@ -14,6 +14,8 @@
 
 #include <cuda_bf16.h>
 
+#include "dclno_internal.cuh"
+
 #define EG_M 64
 #define EG_N 64
 #define EG_K 32
@@ -173,3 +175,45 @@ __device__ void cta_gemm_nt_sub_emu(double* __restrict__ C, int ldc, const doubl
         __syncthreads();
     }
 }
+
+// The cubic steps' tile update: FP64 mma.sync tiles (FP64 path) or FP64 emulated
+// on BF16 tensor cores (mixed path; K <= EG_K per call).
+template <bool LOWER, bool EMU>
+__device__ __forceinline__ void tile_update(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
+                                            int M, int N, int K, int diag, double* smem) {
+    if (EMU)
+        cta_gemm_nt_sub_emu<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, reinterpret_cast<unsigned char*>(smem));
+    else
+        cta_gemm_nt_sub<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, smem);
+}
+
+// C -= A B^T for any K: FP64 tiles take K whole, the emulated tiles in chunks of EG_K
+// (each chunk sliced against its own row exponents and added to C in FP64).
+template <bool EMU>
+__device__ __forceinline__ void tile_update_longk(double* C, int ldc, const double* A, int lda, const double* B,
+                                                  int ldb, int M, int N, int K, double* smem) {
+    if (!EMU) {
+        cta_gemm_nt_sub<false>(C, ldc, A, lda, B, ldb, M, N, K, 0, smem);
+        return;
+    }
+    for (int k0 = 0; k0 < K; k0 += EG_K)
+        cta_gemm_nt_sub_emu<false>(C, ldc, A + k0, lda, B + k0, ldb, M, N, min(EG_K, K - k0), 0,
+                                   reinterpret_cast<unsigned char*>(smem));
+}
+
+// CTA-wide sum (every thread gets the result); red holds one double per warp.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+// CTAs per SM the cubic kernels are compiled for: the FP64 tiles gain from a third
+// CTA (latency hiding), the emulated ones lose by it (their slicing needs registers);
+// measured on the 1728-atom step.
+#define DCLNO_CTAS_PER_SM(EMU) ((EMU) ? 2 : 3)

@@ -301,11 +301,16 @@ __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, co
 // reflectors from the last one), then L^T X_new = X by back substitution.
 template <int R>
 __device__ static void rho_qx_warp(double* X, int n, const double* __restrict__ A, const double* __restrict__ L,
-                                   int ld, const double* __restrict__ tau, const double* __restrict__ invd) {
+                                   int ld, const double* __restrict__ tau, const double* __restrict__ invd,
+                                   const double* __restrict__ q2) {
     const int lane = threadIdx.x & 31;
-    for (int k = n - 3; k >= 0; --k) {
-        const double tk = tau[k];
-        if (tk != 0.0) warp_reflect<R>(X, n, k, n, A + (size_t)k * ld, tk);
+    if (q2) {
+        warp_apply_two_stage<R>(X, n, A, ld, tau, q2, 1);  // Q = Q1 Q2 of the two-stage reduction
+    } else {
+        for (int k = n - 3; k >= 0; --k) {
+            const double tk = tau[k];
+            if (tk != 0.0) warp_reflect<R>(X, n, k, n, A + (size_t)k * ld, tk);
+        }
     }
     // x_t = g_t / L[t][t], then g_s -= L[t][s] x_t for s < t
     for (int t = n - 1; t >= 0; --t) {
@@ -334,9 +339,11 @@ __device__ static void rho_qx_warp(double* X, int n, const double* __restrict__ 
 // reflectors and the triangular solve (rho_qx_warp), with no block barriers.
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDesc* __restrict__ cls,
                                                                 const int* __restrict__ order,
-                                                                double* __restrict__ arena, int with_e, int rch) {
+                                                                double* __restrict__ arena, int with_e, int rch,
+                                                                int two_stage) {
     extern __shared__ double sm[];
     const ClusterDesc d = cls[order[blockIdx.x]];
+    const double* q2 = (two_stage && two_stage_cluster(d)) ? arena + d.q2_off : nullptr;
     const int n = d.n, ld = d.ld, mcw = with_e ? 2 * d.mc : d.mc;  // columns of G
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* A = arena + d.mat_off;
@@ -357,10 +364,10 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_rho_qx(const ClusterDes
             const int rpw = (cols + nw - 1) / nw, r0 = warp * rpw, my = min(rpw, cols - r0);
             double* Xw = Xs + (size_t)max(r0, 0) * n;
             switch (my) {
-                case 1: rho_qx_warp<1>(Xw, n, A, L, ld, tau, invd); break;
-                case 2: rho_qx_warp<2>(Xw, n, A, L, ld, tau, invd); break;
-                case 3: rho_qx_warp<3>(Xw, n, A, L, ld, tau, invd); break;
-                case 4: rho_qx_warp<4>(Xw, n, A, L, ld, tau, invd); break;
+                case 1: rho_qx_warp<1>(Xw, n, A, L, ld, tau, invd, q2); break;
+                case 2: rho_qx_warp<2>(Xw, n, A, L, ld, tau, invd, q2); break;
+                case 3: rho_qx_warp<3>(Xw, n, A, L, ld, tau, invd, q2); break;
+                case 4: rho_qx_warp<4>(Xw, n, A, L, ld, tau, invd, q2); break;
                 default: break;
             }
         }
@@ -423,32 +430,31 @@ __global__ void k_rho_scatter(int id_lo, const ClusterDesc* __restrict__ cls, co
     }
 }
 
-dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out, double* e_out) {
+dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out, double* e_out,
+                            bool poles) {
     const int with_e = e_out ? 1 : 0;
     const int N = b.oend - b.obeg;  // clusters of the batch
     if (N == 0) return DCLNO_OK;
     const int maxn = b.maxn;
     long long maxrow = 0;
     for (int i = b.id_lo; i < b.id_hi; ++i) maxrow = std::max(maxrow, c->row_ptr[i + 1] - c->row_ptr[i]);
-    {
-        ProfScope ps__(c, "k_rho_prep");
-        k_rho_prep<<<N, 256, 0, c->stream>>>(b.id_lo, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
-                                             c->deferred ? c->d_scalars + 2 : nullptr, kT, with_e, c->d_eband);
-    }
-    DCLNO_LAUNCHED(c);
-    {
+    if (!poles) {  // G = F C_c^T from the spectrum, then Z G (merge matrix, logged rotations)
+        {
+            ProfScope ps__(c, "k_rho_prep");
+            k_rho_prep<<<N, 256, 0, c->stream>>>(b.id_lo, c->d_cl, c->d_arena, c->d_eps, c->d_q, mu,
+                                                 c->deferred ? c->d_scalars + 2 : nullptr, kT, with_e, c->d_eband);
+        }
+        DCLNO_LAUNCHED(c);
         const dclno_status st = launch_mgemm(c, b, 1, with_e, c->solved_prec == DCLNO_MIXED);
         if (st != DCLNO_OK) return st;
-    }
-    {
         ProfScope ps__(c, "k_replay_rev");
         const int wmax = with_e ? 2 * b.mcmax : b.mcmax;
         const int per_warp = std::max(1, 32 / wmax);
         const int warps = (2 * N + per_warp - 1) / per_warp;
         k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(2 * N, per_warp, wmax, with_e, c->d_cl,
                                                                       c->d_order + b.obeg, c->d_arena, c->d_iters);
+        DCLNO_LAUNCHED(c);
     }
-    DCLNO_LAUNCHED(c);
     // columns per shared-memory chunk of k_rho_qx: at most DCLNO_RPW per warp, within 200 KB
     const int wcols = with_e ? 2 * b.mcmax : b.mcmax;
     const int rch = (int)std::min<long long>(std::min(wcols, DCLNO_RPW * (DCLNO_SOLVE_THREADS / 32)),
@@ -458,7 +464,8 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_rho_qx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
         ProfScope ps__(c, "k_rho_qx");
-        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, with_e, rch);
+        k_rho_qx<<<N, DCLNO_SOLVE_THREADS, sm, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, with_e, rch,
+                                                            c->solved_two ? 1 : 0);
     }
     DCLNO_LAUNCHED(c);
     const int wpb = 8;

@@ -24,21 +24,6 @@
 
 #define NB DCLNO_NB
 #define DK_LD 33
-// CTAs per SM the cubic kernels are compiled for: the FP64 tiles gain from a third
-// CTA (latency hiding), the emulated ones lose by it (their slicing needs registers);
-// measured on the 1728-atom step.
-#define DCLNO_CTAS_PER_SM(EMU) ((EMU) ? 2 : 3)
-
-// The cubic steps' tile update: FP64 mma.sync tiles (FP64 path) or FP64 emulated
-// on BF16 tensor cores (mixed path).
-template <bool LOWER, bool EMU>
-__device__ __forceinline__ void tile_update(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                                            int M, int N, int K, int diag, double* smem) {
-    if (EMU)
-        cta_gemm_nt_sub_emu<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, reinterpret_cast<unsigned char*>(smem));
-    else
-        cta_gemm_nt_sub<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, smem);
-}
 
 // x L_kk^T = h for rows [r0, r1) of M (columns kb .. kb+nb-1), L_kk in smem (lower),
 // reciprocals of its diagonal in invd.
@@ -199,26 +184,17 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
 // On exit: d (diagonal), e (sub-diagonal), tau; reflector k is (1, A[k+2:, k]) acting
 // on rows k+1.. (A[k+1][k] holds the unit element).
 // ---------------------------------------------------------------------------
-__device__ static double block_sum(double v, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w];
-    return s;
-}
-
 template <bool EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_tridiag(const ClusterDesc* __restrict__ cls,
                                                                  const int* __restrict__ order,
                                                                  double* __restrict__ arena,
-                                                                 const int* __restrict__ status) {
+                                                                 const int* __restrict__ status,
+                                                                 int skip_two_stage) {
     extern __shared__ double sm[];
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
+    if (skip_two_stage && two_stage_cluster(d)) return;  // reduced by k_band + k_chase instead
     const int n = d.n, ld = d.ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double* A = arena + d.mat_off;
@@ -625,9 +601,15 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
 // in shared memory (row-major, stride n) and each warp applies every reflector to the
 // rows it owns (q_rows_warp), so there is no block barrier per reflector.
 // ---------------------------------------------------------------------------
-// X <- X H_0 H_1 ... H_{n-3} on R rows owned by one warp
+// X <- X H_0 H_1 ... H_{n-3} on R rows owned by one warp (one-stage reduction), or
+// X <- X Q1 Q2 (two-stage reduction, q2 = the chase log)
 template <int R>
-__device__ static void q_rows_warp(double* X, int n, const double* __restrict__ A, int ld, const double* __restrict__ tau) {
+__device__ static void q_rows_warp(double* X, int n, const double* __restrict__ A, int ld, const double* __restrict__ tau,
+                                   const double* __restrict__ q2) {
+    if (q2) {
+        warp_apply_two_stage<R>(X, n, A, ld, tau, q2, 0);
+        return;
+    }
     for (int k = 0; k + 2 < n; ++k) {
         const double tk = tau[k];
         if (tk != 0.0) warp_reflect<R>(X, n, k, n, A + (size_t)k * ld, tk);
@@ -637,12 +619,14 @@ __device__ static void q_rows_warp(double* X, int n, const double* __restrict__ 
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const ClusterDesc* __restrict__ cls,
                                                                       const int* __restrict__ order,
                                                                       double* __restrict__ arena,
-                                                                      const int* __restrict__ status, int rch) {
+                                                                      const int* __restrict__ status, int rch,
+                                                                      int two_stage) {
     extern __shared__ double sm[];
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld, mc = d.mc, w2 = 2 * mc, c0 = n - mc;
+    const double* q2 = (two_stage && two_stage_cluster(d)) ? arena + d.q2_off : nullptr;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
@@ -674,10 +658,10 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const Clus
             const int rpw = (rows + nw - 1) / nw, r0 = warp * rpw, my = min(rpw, rows - r0);
             double* Xw = Xs + (size_t)max(r0, 0) * n;
             switch (my) {
-                case 1: q_rows_warp<1>(Xw, n, A, ld, tau); break;
-                case 2: q_rows_warp<2>(Xw, n, A, ld, tau); break;
-                case 3: q_rows_warp<3>(Xw, n, A, ld, tau); break;
-                case 4: q_rows_warp<4>(Xw, n, A, ld, tau); break;
+                case 1: q_rows_warp<1>(Xw, n, A, ld, tau, q2); break;
+                case 2: q_rows_warp<2>(Xw, n, A, ld, tau, q2); break;
+                case 3: q_rows_warp<3>(Xw, n, A, ld, tau, q2); break;
+                case 4: q_rows_warp<4>(Xw, n, A, ld, tau, q2); break;
                 default: break;
             }
         }
@@ -919,7 +903,7 @@ static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int 
 }
 
 template <bool EMU>
-static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
+static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only) {
     const int N = b.oend - b.obeg;  // clusters of the batch
     if (N == 0) return DCLNO_OK;
     const int maxn = b.maxn;
@@ -949,11 +933,23 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
         k_congruence<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
     }
     DCLNO_LAUNCHED(c);
+    const int two = c->solved_two ? 1 : 0;
     {
         ProfScope ps__(c, "k_tridiag");
-        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, two);
     }
     DCLNO_LAUNCHED(c);
+    if (two) {
+        const dclno_status st = launch_two_stage(c, b, EMU);
+        if (st != DCLNO_OK) return st;
+    }
+    if (reduce_only) {
+        ProfScope ps__(c, "k_apply_q_rows");
+        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, rch,
+                                                                     two);
+        DCLNO_LAUNCHED(c);
+        return DCLNO_OK;  // statuses are read by the caller after the pole sum
+    }
     {
         int segmax = 1;
         for (int i = b.id_lo; i < b.id_hi; ++i) segmax = std::max(segmax, std::max(seg_len(c->cl[i], 0), seg_len(c->cl[i], 1)));
@@ -976,7 +972,8 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     }
     {
         ProfScope ps__(c, "k_apply_q_rows");
-        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, rch);
+        k_apply_q_rows<<<N, DCLNO_SOLVE_THREADS, sm_q, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, rch,
+                                                                     two);
     }
     DCLNO_LAUNCHED(c);
     {
@@ -1018,5 +1015,9 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b) {
     return DCLNO_OK;
 }
 
-dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b) { return launch_solve<false>(c, b); }
-dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b) { return launch_solve<true>(c, b); }
+dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only) {
+    return launch_solve<false>(c, b, reduce_only);
+}
+dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only) {
+    return launch_solve<true>(c, b, reduce_only);
+}
