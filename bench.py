@@ -429,7 +429,9 @@ def roofline_report(kernel, path, n, k_ms, k_n, dfma, dmma, bf16, bf16_src):
     k_band     dense -> band of half-width BW = 32, 4 n^3/3 in tile products (FP64 MMA or
                emulated) plus the panel work (QR, T, W: about 4 n^2 BW FP64 flops).
     k_chase    band -> tridiagonal by bulge chasing, about 6 n^2 BW FP64 flops."""
-    n = n.astype(np.float64)
+    import numpy as np
+
+    n = np.asarray(n, dtype=np.float64)
     bw = 32.0
     if kernel == "k_tridiag":
         flops = float(np.sum(4.0 * n ** 3 / 3.0))
