@@ -192,7 +192,8 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
 /*
  * Form of the Householder tridiagonalisation in dclno_solve_clusters (Sec. II.C
  * step (iii); both give the same T up to rounding and the same eigenpairs):
- *   0  automatic (default): two-stage in the mixed path, one-stage in FP64;
+ *   0  automatic (default): the form measured faster on this GPU for the
+ *      precision of the solve (at present the one-stage form in both);
  *   1  one-stage: blocked Householder with a symmetric matrix-vector product per
  *      column (each column reads the whole trailing matrix);
  *   2  two-stage: dense -> band of half-width 32 (blocked Householder whose
@@ -204,6 +205,19 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
  * at the next solve.  Errors: DCLNO_ERR_ARG for another mode.
  */
 dclno_status dclno_set_tridiag(dclno_ctx *ctx, int mode);
+
+/*
+ * Tensor-core engine of the mixed path's emulated FP64 tile products (the same
+ * arithmetic either way: eight 8-bit slices per FP64 row, exact FP32 level sums,
+ * exact 64-bit level combination):
+ *   1  mma.sync.m16n8k16 BF16 from register fragments;
+ *   2  tcgen05.mma with the level accumulators in tensor memory (default): one
+ *      thread issues the products of a level while the CTA's warps combine the
+ *      previous level; each CTA of the cubic kernels holds 128 tensor-memory columns.
+ * A tensor-core wait that runs out fails the solve with DCLNO_ERR_TIMEOUT (cluster
+ * in the message).  Takes effect at the next solve; DCLNO_ERR_ARG for another value.
+ */
+dclno_status dclno_set_mixed_engine(dclno_ctx *ctx, int engine);
 dclno_status dclno_get_tuning(dclno_ctx *ctx, int batch, int *ql_lanes_out, float *candidate_ms);
 
 /*

@@ -23,7 +23,8 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_kernel_time", "dclno_measure_fp64_peaks", "dclno_find_mu_noalloc", "dclno_scf_run",
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
-           "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles"]
+           "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles",
+           "dclno_set_mixed_engine"]
 
 
 class DclnoError(RuntimeError):
@@ -93,6 +94,7 @@ def load_library():
         "dclno_get_lno_counts": ([P, P], I),
         "dclno_set_tridiag": ([P, I], I),
         "dclno_density_matrix_poles": ([P, D, D, I, I, P], I),
+        "dclno_set_mixed_engine": ([P, I], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -219,6 +221,10 @@ class Context:
     def set_tridiag(self, mode):
         """Tridiagonalisation form: 0 automatic, 1 one-stage, 2 two-stage (dense -> band -> tridiagonal)."""
         self._check(self.lib.dclno_set_tridiag(self.h, int(mode)))
+
+    def set_mixed_engine(self, engine):
+        """Emulated tile products of the mixed path: 1 = mma.sync, 2 = tcgen05 with tensor memory."""
+        self._check(self.lib.dclno_set_mixed_engine(self.h, int(engine)))
 
     def set_autotune(self, on=True):
         """Time the QL launch shape on each batch's first eager solve (default on)."""

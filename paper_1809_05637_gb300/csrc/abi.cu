@@ -743,9 +743,17 @@ static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
     return st;
 }
 
+// The tridiagonalisation form of a solve: mode 1 one-stage, 2 two-stage; the automatic
+// mode (0) takes the form measured faster on the 1,728-atom step in each precision
+// (one-stage in both at present: see the kernel times in the design notes).
+static bool resolve_two_stage(const dclno_ctx* c, dclno_precision prec) {
+    (void)prec;
+    return c->tridiag_mode == 2;
+}
+
 // every batch: assemble + solve (eps and q of all clusters)
 static dclno_status solve_all(dclno_ctx* c, dclno_precision prec) {
-    c->solved_two = c->tridiag_mode == 2 || (c->tridiag_mode == 0 && prec == DCLNO_MIXED);
+    c->solved_two = resolve_two_stage(c, prec);
     dclno_status st = launch_lno_blocks(c);
     for (int bi = 0; st == DCLNO_OK && bi < (int)c->batches.size(); ++bi) st = solve_batch(c, bi, prec);
     if (st == DCLNO_OK) c->solved_prec = prec;
@@ -841,6 +849,7 @@ static dclno_status check_batch_status(dclno_ctx* c, const Batch& b, const char*
         if (st[k] == ST_OK) continue;
         const std::string id = std::string(who) + ": cluster " + std::to_string(i);
         if (st[k] == ST_NOT_SPD) return set_err(c, DCLNO_ERR_NOT_SPD, id + ": overlap not positive definite");
+        if (st[k] == ST_TIMEOUT) return set_err(c, DCLNO_ERR_TIMEOUT, id + ": a tensor-core wait ran out");
         if (st[k] == ST_FEW_POLES)
             return set_err(c, DCLNO_ERR_ARG, id + ": too few poles (the first omitted pole is below three times the "
                                                   "spectral radius of the cluster about mu)");
@@ -862,7 +871,7 @@ extern "C" dclno_status dclno_density_matrix_poles(dclno_ctx* c, double mu, doub
     // the reduction overwrites the workspace of any earlier solve
     c->solved = false;
     c->resident = -1;
-    c->solved_two = c->tridiag_mode == 2 || (c->tridiag_mode == 0 && prec == DCLNO_MIXED);
+    c->solved_two = resolve_two_stage(c, prec);
     c->solved_prec = prec;
     dclno_status st = launch_lno_blocks(c);
     for (int bi = 0; st == DCLNO_OK && bi < (int)c->batches.size(); ++bi) {
@@ -890,6 +899,14 @@ extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
     c->err.clear();
     if (mode < 0 || mode > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_tridiag: mode must be 0, 1 or 2");
     c->tridiag_mode = mode;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_mixed_engine(dclno_ctx* c, int engine) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (engine != 1 && engine != 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_mixed_engine: engine must be 1 or 2");
+    c->mixed_engine = engine;
     return DCLNO_OK;
 }
 
@@ -1074,6 +1091,7 @@ extern "C" dclno_status dclno_scf_run(dclno_ctx* c, double* rho, int nsteps, dou
     c->lnos_ready = true;
     if (err[0] == 16) return set_err(c, DCLNO_ERR_NO_BRACKET, "dclno_scf_run: N_e outside the bracket of N(mu)");
     if (err[0] == ST_NOT_SPD) return set_err(c, DCLNO_ERR_NOT_SPD, "dclno_scf_run: a cluster overlap is not positive definite");
+    if (err[0] == ST_TIMEOUT) return set_err(c, DCLNO_ERR_TIMEOUT, "dclno_scf_run: a tensor-core wait ran out");
     if (err[0] != 0) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "dclno_scf_run: an eigensolver failed (status " + std::to_string(err[0]) + ")");
     return DCLNO_OK;
 }

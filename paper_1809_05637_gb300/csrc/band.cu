@@ -31,16 +31,14 @@
 #define BW DCLNO_BW
 #define TL (BW + 1)  // row stride of the BW x BW shared-memory blocks
 
-// shared memory of k_band: GEMM staging (also the mirror's transpose tiles), T, M,
-// reduction scratch
-__host__ __device__ inline size_t band_gemm_doubles(bool emu) {
-    const size_t g = emu ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
+// shared memory of k_band: GEMM staging (also the mirror's transpose tiles and step 8's
+// operand columns), reduction scratch
+__host__ __device__ inline size_t band_gemm_doubles(int emu) {
+    const size_t g = (ENGINE_SMEM_BYTES(emu) + 7) / 8;
     const size_t mirror = 8 * 32 * 33;  // eight warps' 32 x 33 transpose tiles
     return g > mirror ? g : mirror;
 }
-__host__ __device__ inline size_t band_smem_bytes(bool emu) {
-    return (band_gemm_doubles(emu) + 2 * BW * TL + 64) * sizeof(double);
-}
+__host__ __device__ inline size_t band_smem_bytes(int emu) { return (band_gemm_doubles(emu) + 64) * sizeof(double); }
 
 // upper triangle of the trailing block [r0, n)^2 <- its lower triangle (32 x 32 tiles
 // through shared memory, one tile per warp at a time)
@@ -68,12 +66,13 @@ __device__ static void mirror_lower(double* A, int ld, int r0, int n, double* ti
     }
 }
 
-template <bool EMU>
+template <int EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_band(const ClusterDesc* __restrict__ cls,
                                                                                  const int* __restrict__ order,
                                                                                  double* __restrict__ arena,
-                                                                                 const int* __restrict__ status) {
+                                                                                 int* __restrict__ status) {
     extern __shared__ double sm[];
+    __shared__ TcState tcs;
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
@@ -88,12 +87,13 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
     double* Yt = NVt + (size_t)BW * ld;       // BW x m (stride ld): Y^T = V^T A22
     double* GZ = Yt + (size_t)BW * ld;        // [-V^T V | V^T Y], BW x 2BW (row stride gz)
     const int gz = 2 * BW + 1;
+    double* Ts = GZ + BW * gz;                // T (upper triangular), BW x TL
+    double* Ms = Ts + BW * TL;                // T^T (V^T Y) T, BW x TL
     double* G = sm;
-    double* Ts = sm + band_gemm_doubles(EMU);  // T (upper triangular)
-    double* Ms = Ts + BW * TL;                 // T^T (V^T Y) T
-    double* red = Ms + BW * TL;
+    double* red = sm + band_gemm_doubles(EMU);
 
     for (int t = tid; t < n; t += blockDim.x) tauv[t] = 0.0;
+    ENGINE_BEGIN(EMU, &tcs);
     __syncthreads();
     for (int c0 = 0; c0 + BW < n; c0 += BW) {
         const int r0 = c0 + BW, m = n - r0;
@@ -156,12 +156,12 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         double* A22 = A + (size_t)r0 * ld + r0;
         for (int e = tid; e < BW * m; e += blockDim.x) Yt[(size_t)(e / m) * ld + e % m] = 0.0;
         __syncthreads();
-        tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G);
+        tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G, &tcs);
         // (5) [-V^T V | V^T Y] = -(-V^T) [-V^T ; Y^T]^T ... as C -= A B^T with B = the 2BW rows
         // of NVt and Yt (contiguous, stride ld): C = -(V^T V) on the left, +V^T Y on the right
         for (int e = tid; e < BW * gz; e += blockDim.x) GZ[e] = 0.0;
         __syncthreads();
-        tile_update_longk<EMU>(GZ, gz, NVt, ld, NVt, ld, BW, 2 * BW, m, G);
+        tile_update_longk<EMU>(GZ, gz, NVt, ld, NVt, ld, BW, 2 * BW, m, G, &tcs);
         // (6) T (upper triangular): T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j]
         if (warp == 0) {
             for (int j = 0; j < BW; ++j) {
@@ -225,9 +225,11 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         }
         __syncthreads();
         // (9) A22 <- A22 - V W^T - W V^T (lower triangle)
-        tile_update<true, EMU>(A22, ld, Vx, BW, W, BW, m, m, BW, 0, G);
-        tile_update<true, EMU>(A22, ld, W, BW, Vx, BW, m, m, BW, 0, G);
+        tile_update<true, EMU>(A22, ld, Vx, BW, W, BW, m, m, BW, 0, G, &tcs);
+        tile_update<true, EMU>(A22, ld, W, BW, Vx, BW, m, m, BW, 0, G, &tcs);
     }
+    ENGINE_END(EMU, &tcs);
+    if (EMU == 2 && tcs.failed && tid == 0) status[ci] = ST_TIMEOUT;
 }
 
 // ---------------------------------------------------------------------------
@@ -398,23 +400,27 @@ __global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cl
     }
 }
 
-dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool emu) {
+template <int EMU>
+static dclno_status launch_band_t(dclno_ctx* c, int N, const int* order) {
+    const size_t smb = band_smem_bytes(EMU);
+    if (smb > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "band reduction: shared memory");
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    k_band<EMU><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, int emu) {
     const int N = b.oend - b.obeg;
     if (N == 0) return DCLNO_OK;
     const int* order = c->d_order + b.obeg;
-    const size_t smb = band_smem_bytes(emu);
-    if (smb > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "band reduction: shared memory");
     {
         ProfScope ps__(c, "k_band");
-        if (emu) {
-            DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-            k_band<true><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-        } else {
-            DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-            k_band<false><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-        }
+        const dclno_status st = emu == 2 ? launch_band_t<2>(c, N, order)
+                                : emu == 1 ? launch_band_t<1>(c, N, order)
+                                           : launch_band_t<0>(c, N, order);
+        if (st != DCLNO_OK) return st;
     }
-    DCLNO_LAUNCHED(c);
     {
         ProfScope ps__(c, "k_chase");
         const size_t sm2 = 2 * BW * TL * sizeof(double);

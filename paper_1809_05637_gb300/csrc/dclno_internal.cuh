@@ -95,6 +95,7 @@ enum : int {
     ST_LOG_FULL = 3,
     ST_BAD_LNO = 4,
     ST_FEW_POLES = 5,  // the Matsubara pole sum was asked for too few poles for this cluster
+    ST_TIMEOUT = 6,    // a bounded wait on the tensor cores ran out
 };
 
 // A memory-admitted batch: a contiguous range of cluster ids whose workspace is
@@ -155,6 +156,8 @@ struct dclno_ctx {
     // the last solve used (the density pass applies the same Q)
     int tridiag_mode = 0;
     bool solved_two = false;
+    // engine of the mixed path's emulated tile products: 1 = mma.sync, 2 = tcgen05 (default)
+    int mixed_engine = 2;
     size_t ws_limit = 0;              // workspace limit in bytes (0 = free device memory)
     // launch-shape autotuner: QL lanes per warp chosen per batch by timing (0 = not yet)
     bool autotune = true;
@@ -279,10 +282,10 @@ dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only = 
 dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only = false);
 dclno_status launch_poles(dclno_ctx* c, const Batch& b, double mu, double kT, int npoles);
 dclno_status launch_merge(dclno_ctx* c, const Batch& b);
-dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool emu);
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, int emu);
 // Y <- X Y for the torn clusters of a batch: dir 0 = central strips P <- M^T P (after the
 // forward replay), dir 1 = density columns G <- M G (before the reverse replay)
-dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu);
+dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, int emu);
 dclno_status launch_find_mu(dclno_ctx* c, double ne, double kT, double* mu, double* nmu);
 // poles: the density columns G are already formed (k_poles); only L^-T Q G and the scatter
 dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, double* rho_out,
@@ -433,6 +436,49 @@ __device__ __forceinline__ void warp_reflect_short(double* X, int ldx, int p, in
         if (lane < len) X[(size_t)j * ldx + p + lane] = fma(-u[j], v, X[(size_t)j * ldx + p + lane]);
 }
 
+// The chase reflectors of sweep j (disjoint windows [p_k, p_k + len_k), p_k = j + 1 + k BW)
+// on the R rows of X owned by this warp, KW windows at a time: the KW x R dot products
+// are reduced by interleaved butterflies, so their shuffle and FP64-add latencies overlap
+// (a reflector alone is a chain of five dependent shuffle-adds).  Windows of one sweep
+// commute, so the same code serves both directions.
+#define DCLNO_CHASE_KW 4
+template <int R>
+__device__ __forceinline__ void warp_chase_sweep(double* X, int n, int j, const double* __restrict__ slot0) {
+    const int lane = threadIdx.x & 31;
+    const int ns = (int)chase_steps(n, j);
+    for (int k0 = 0; k0 < ns; k0 += DCLNO_CHASE_KW) {
+        double v[DCLNO_CHASE_KW], tau[DCLNO_CHASE_KW], u[DCLNO_CHASE_KW][R];
+        int p[DCLNO_CHASE_KW];
+        bool on[DCLNO_CHASE_KW];
+#pragma unroll
+        for (int w = 0; w < DCLNO_CHASE_KW; ++w) {
+            const int k = k0 + w;
+            p[w] = j + 1 + k * DCLNO_BW;
+            const int len = k < ns ? min(DCLNO_BW, n - p[w]) : 0;
+            const double* sl = slot0 + (size_t)k * DCLNO_BW;
+            tau[w] = k < ns ? sl[0] : 0.0;
+            on[w] = lane < len;
+            v[w] = !on[w] ? 0.0 : (lane == 0 ? 1.0 : sl[lane]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[w][r] = on[w] ? X[(size_t)r * n + p[w] + lane] * v[w] : 0.0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int w = 0; w < DCLNO_CHASE_KW; ++w)
+#pragma unroll
+                for (int r = 0; r < R; ++r) u[w][r] += __shfl_xor_sync(0xffffffffu, u[w][r], o);
+#pragma unroll
+        for (int w = 0; w < DCLNO_CHASE_KW; ++w)
+            if (on[w])
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double* x = X + (size_t)r * n + p[w] + lane;
+                    *x = fma(-tau[w] * u[w][r], v[w], *x);
+                }
+    }
+}
+
 // The two-stage factor Q = Q1 Q2 (A = Q T Q^T) on the R rows of X owned by this warp:
 // Q1 = the panel reflectors (reflector c in row c of A's upper triangle from column
 // c + BW on, tau[c], 0 where there is none), Q2 = the chase log q2 in generation order.
@@ -450,21 +496,15 @@ __device__ __forceinline__ void warp_apply_two_stage(double* X, int n, const dou
         }
         const double* slot = q2;
         for (int j = 0; j + 2 < n; ++j) {
-            const int ns = (int)chase_steps(n, j);
-            for (int k = 0; k < ns; ++k, slot += DCLNO_BW) {
-                const int p = j + 1 + k * DCLNO_BW;
-                warp_reflect_short<R>(X, n, p, min(DCLNO_BW, n - p), slot);
-            }
+            warp_chase_sweep<R>(X, n, j, slot);
+            slot += chase_steps(n, j) * DCLNO_BW;
         }
         return;
     }
-    const double* slot = q2 + (band_refl_count(n) - 1) * DCLNO_BW;
+    const double* slot = q2 + band_refl_count(n) * DCLNO_BW;
     for (int j = n - 3; j >= 0; --j) {
-        const int ns = (int)chase_steps(n, j);
-        for (int k = ns - 1; k >= 0; --k, slot -= DCLNO_BW) {
-            const int p = j + 1 + k * DCLNO_BW;
-            warp_reflect_short<R>(X, n, p, min(DCLNO_BW, n - p), slot);
-        }
+        slot -= chase_steps(n, j) * DCLNO_BW;
+        warp_chase_sweep<R>(X, n, j, slot);
     }
     for (int c = n - 1 - DCLNO_BW; c >= 0; --c) {
         const double tc = tau[c];

@@ -176,30 +176,49 @@ __device__ void cta_gemm_nt_sub_emu(double* __restrict__ C, int ldc, const doubl
     }
 }
 
-// The cubic steps' tile update: FP64 mma.sync tiles (FP64 path) or FP64 emulated
-// on BF16 tensor cores (mixed path; K <= EG_K per call).
-template <bool LOWER, bool EMU>
+#include "emu_tc.cuh"
+
+// The cubic steps' tile update, by engine: EMU = 0 FP64 mma.sync tiles (FP64 path);
+// EMU = 1 FP64 emulated by BF16 slices on mma.sync (register fragments); EMU = 2 the
+// same emulation on tcgen05.mma with tensor-memory accumulators (tc: the CTA's state,
+// set up by tc_begin).  The emulated engines take K <= 32 per call.
+template <bool LOWER, int EMU>
 __device__ __forceinline__ void tile_update(double* C, int ldc, const double* A, int lda, const double* B, int ldb,
-                                            int M, int N, int K, int diag, double* smem) {
-    if (EMU)
+                                            int M, int N, int K, int diag, double* smem, TcState* tc) {
+    if constexpr (EMU == 2)
+        cta_gemm_nt_sub_tc<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, reinterpret_cast<unsigned char*>(smem), tc);
+    else if constexpr (EMU == 1)
         cta_gemm_nt_sub_emu<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, reinterpret_cast<unsigned char*>(smem));
     else
         cta_gemm_nt_sub<LOWER>(C, ldc, A, lda, B, ldb, M, N, K, diag, smem);
 }
 
-// C -= A B^T for any K: FP64 tiles take K whole, the emulated tiles in chunks of EG_K
+// C -= A B^T for any K: FP64 tiles take K whole, the emulated engines chunks of 32
 // (each chunk sliced against its own row exponents and added to C in FP64).
-template <bool EMU>
+template <int EMU>
 __device__ __forceinline__ void tile_update_longk(double* C, int ldc, const double* A, int lda, const double* B,
-                                                  int ldb, int M, int N, int K, double* smem) {
-    if (!EMU) {
+                                                  int ldb, int M, int N, int K, double* smem, TcState* tc) {
+    if constexpr (EMU == 0) {
         cta_gemm_nt_sub<false>(C, ldc, A, lda, B, ldb, M, N, K, 0, smem);
-        return;
+    } else {
+        for (int k0 = 0; k0 < K; k0 += EG_K)
+            tile_update<false, EMU>(C, ldc, A + k0, lda, B + k0, ldb, M, N, min(EG_K, K - k0), 0, smem, tc);
     }
-    for (int k0 = 0; k0 < K; k0 += EG_K)
-        cta_gemm_nt_sub_emu<false>(C, ldc, A + k0, lda, B + k0, ldb, M, N, min(EG_K, K - k0), 0,
-                                   reinterpret_cast<unsigned char*>(smem));
 }
+
+// shared memory of one engine's staging (bytes)
+#define ENGINE_SMEM_BYTES(EMU) ((EMU) == 2 ? TC_SMEM_BYTES : (EMU) == 1 ? EG_SMEM_BYTES : GT_SMEM_DOUBLES * 8)
+
+// Tensor memory and barriers of an EMU == 2 kernel's CTA: tc_begin after the early
+// exits, tc_end before every later exit (it waits out a timed-out engine's MMAs).
+#define ENGINE_BEGIN(EMU, st) \
+    do {                      \
+        if ((EMU) == 2) tc_begin(st); \
+    } while (0)
+#define ENGINE_END(EMU, st) \
+    do {                    \
+        if ((EMU) == 2) tc_end(st); \
+    } while (0)
 
 // CTA-wide sum (every thread gets the result); red holds one double per warp.
 __device__ __forceinline__ double block_sum(double v, double* red) {

@@ -63,7 +63,7 @@ __device__ static void load_diag_block(const double* L, int ld, int kb, int nb, 
 // ---------------------------------------------------------------------------
 // Cholesky of S^(i) in place (lower); sets ST_NOT_SPD on a non-positive pivot.
 // ---------------------------------------------------------------------------
-template <bool EMU>
+template <int EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_cholesky(const ClusterDesc* __restrict__ cls,
                                                                   const int* __restrict__ order,
                                                                   double* __restrict__ arena,
@@ -73,12 +73,14 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
     double* invd = sm + NB * DK_LD;    // NB
     double* G = invd + NB;             // GEMM tiles
     __shared__ int fail;
+    __shared__ TcState tcs;
     const int ci = order[blockIdx.x];
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld;
     double* L = arena + d.mat_off + (size_t)n * ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) fail = 0;
+    ENGINE_BEGIN(EMU, &tcs);
     for (int kb = 0; kb < n; kb += NB) {
         const int nb = min(NB, n - kb);
         for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         }
         __syncthreads();
         if (fail) {
+            ENGINE_END(EMU, &tcs);
             if (threadIdx.x == 0) status[ci] = ST_NOT_SPD;
             return;
         }
@@ -122,38 +125,43 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         const int m2 = n - kb - nb;
         if (m2 > 0) {
             double* P = L + (size_t)(kb + nb) * ld + kb;
-            tile_update<true, EMU>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G);
+            tile_update<true, EMU>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G, &tcs);
         }
     }
-    if (threadIdx.x == 0) status[ci] = ST_OK;
+    ENGINE_END(EMU, &tcs);
+    if (threadIdx.x == 0) status[ci] = (EMU == 2 && tcs.failed) ? ST_TIMEOUT : ST_OK;
 }
 
 // ---------------------------------------------------------------------------
 // A = L^-1 H L^-T, lower triangle valid on exit (in place of H^(i)).
 // Y = H L^-T (all rows), transpose, then A = Y^T L^-T restricted to the lower part.
 // ---------------------------------------------------------------------------
-template <bool EMU>
+template <int EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_congruence(const ClusterDesc* __restrict__ cls,
                                                                     const int* __restrict__ order,
                                                                     double* __restrict__ arena,
-                                                                    const int* __restrict__ status) {
+                                                                    int* __restrict__ status) {
     extern __shared__ double sm[];
     double* Dk = sm;
     double* invd = sm + NB * DK_LD;
     double* G = invd + NB;
+    __shared__ TcState tcs;
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld;
     double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
+    ENGINE_BEGIN(EMU, &tcs);
     for (int kb = 0; kb < n; kb += NB) {
         const int nb = min(NB, n - kb);
         load_diag_block(L, ld, kb, nb, Dk, invd);
         panel_solve_rows(A, ld, kb, nb, 0, n, Dk, invd);
         __syncthreads();
         const int n2 = n - kb - nb;
-        if (n2 > 0) tile_update<false, EMU>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G);
+        if (n2 > 0)
+            tile_update<false, EMU>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G,
+                                    &tcs);
     }
     // in-place transpose
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -174,9 +182,11 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         if (m2 > 0) {
             double* C = A + (size_t)(kb + nb) * ld + kb + nb;
             tile_update<true, EMU>(C, ld, A + (size_t)(kb + nb) * ld + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, m2, m2,
-                                  nb, 0, G);
+                                  nb, 0, G, &tcs);
         }
     }
+    ENGINE_END(EMU, &tcs);
+    if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,17 +194,19 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
 // On exit: d (diagonal), e (sub-diagonal), tau; reflector k is (1, A[k+2:, k]) acting
 // on rows k+1.. (A[k+1][k] holds the unit element).
 // ---------------------------------------------------------------------------
-template <bool EMU>
+template <int EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_tridiag(const ClusterDesc* __restrict__ cls,
                                                                  const int* __restrict__ order,
                                                                  double* __restrict__ arena,
-                                                                 const int* __restrict__ status,
+                                                                 int* __restrict__ status,
                                                                  int skip_two_stage) {
     extern __shared__ double sm[];
+    __shared__ TcState tcs;
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     if (skip_two_stage && two_stage_cluster(d)) return;  // reduced by k_band + k_chase instead
+    ENGINE_BEGIN(EMU, &tcs);
     const int n = d.n, ld = d.ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double* A = arena + d.mat_off;
@@ -338,10 +350,12 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
             double* C = A + (size_t)(c0 + nb) * ld + c0 + nb;
             const double* Vp = A + (size_t)(c0 + nb) * ld + c0;
             const double* Wp = W + (size_t)(c0 + nb) * NB;
-            tile_update<true, EMU>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G);
-            tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G);
+            tile_update<true, EMU>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G, &tcs);
+            tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G, &tcs);
         }
     }
+    ENGINE_END(EMU, &tcs);
+    if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
     // Cuppen's tear: T = diag(T1, T2) + |beta| v v^T with beta = e[k-1], v = e_{k-1} + sign(beta) e_k;
     // T1 and T2 (d[k-1], d[k] lowered by |beta|) are solved as separate QL segments and merged
     // afterwards (k_merge).  beta is kept in W[n].
@@ -750,12 +764,13 @@ __device__ static void tall_gemm_fp64(double* __restrict__ C, const double* __re
 // Y is first copied to scratch (W for dir 0, the M^T area for dir 1).  FP64 path:
 // tall_gemm_fp64.  Mixed path: C -= X B^T on the emulated tile GEMM with B = -Y^T
 // staged in the scratch and C = Y cleared.
-template <bool EMU>
+template <int EMU>
 __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterDesc* __restrict__ cls,
                                                                const int* __restrict__ order,
                                                                double* __restrict__ arena,
-                                                               const int* __restrict__ status, int dir, int with_e) {
+                                                               int* __restrict__ status, int dir, int with_e) {
     extern __shared__ double sm[];
+    __shared__ TcState tcs;
     const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
@@ -767,12 +782,12 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
     double* Y = (dir == 0) ? arena + d.cc_off : arena + d.aux_off + 3 * ld;
     double* Bt = (dir == 0) ? arena + d.aux_off + 3 * ld : MT;
     const double* X = (dir == 0) ? MT : M;
-    if (!EMU) {
+    if constexpr (EMU == 0) {
         for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Bt[e] = Y[e];
         __syncthreads();
         tall_gemm_fp64(Y, X, ld, Bt, n, w);
         return;
-    }
+    } else {
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) {
         const int t = (int)(e / w), a = (int)(e % w);
         Bt[(size_t)a * ld + t] = -Y[e];
@@ -780,29 +795,33 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
     __syncthreads();
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Y[e] = 0.0;
     __syncthreads();
-    for (int k0 = 0; k0 < n; k0 += EG_K)
-        tile_update<false, true>(Y, w, X + k0, ld, Bt + k0, ld, n, w, min(EG_K, n - k0), 0, sm);
+    ENGINE_BEGIN(EMU, &tcs);
+    tile_update_longk<EMU>(Y, w, X, ld, Bt, ld, n, w, n, sm, &tcs);
+    ENGINE_END(EMU, &tcs);
+    if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
+    }
 }
 
-dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, bool emu) {
+template <int EMU>
+static dclno_status launch_mgemm_t(dclno_ctx* c, const Batch& b, int N, int dir, int with_e) {
+    const size_t smb = EMU ? (size_t)ENGINE_SMEM_BYTES(EMU) : 0;
+    DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    k_mgemm<EMU><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, c->d_status,
+                                                             dir, with_e);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, int emu) {
     const int N = b.oend - b.obeg;
     if (N == 0) return DCLNO_OK;
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
-    const size_t smb = emu ? (size_t)EG_SMEM_BYTES : 0;
     ProfScope ps__(c, dir == 0 ? "k_mgemm_fwd" : "k_mgemm_rev");
-    if (emu) {
-        DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-        k_mgemm<true><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena,
-                                                                  c->d_status, dir, with_e);
-    } else {
-        DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-        k_mgemm<false><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena,
-                                                                   c->d_status, dir, with_e);
-    }
-    DCLNO_LAUNCHED(c);
-    return DCLNO_OK;
+    if (emu == 2) return launch_mgemm_t<2>(c, b, N, dir, with_e);
+    if (emu == 1) return launch_mgemm_t<1>(c, b, N, dir, with_e);
+    return launch_mgemm_t<0>(c, b, N, dir, with_e);
 }
 
 // eigenvalues and weights: eps_mu = d_mu, q_mu = sum_a P[mu][a] P[mu][mc + a]
@@ -902,14 +921,14 @@ static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int 
     return DCLNO_OK;
 }
 
-template <bool EMU>
+template <int EMU>
 static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only) {
     const int N = b.oend - b.obeg;  // clusters of the batch
     if (N == 0) return DCLNO_OK;
     const int maxn = b.maxn;
     const int* order = c->d_order + b.obeg;
     const int nw = DCLNO_SOLVE_THREADS / 32;
-    const size_t gemm_doubles = EMU ? (EG_SMEM_BYTES + 7) / 8 : (size_t)GT_SMEM_DOUBLES;
+    const size_t gemm_doubles = (ENGINE_SMEM_BYTES(EMU) + 7) / 8;
     size_t sm_chol = (size_t)(NB * DK_LD + NB + gemm_doubles) * sizeof(double);
     size_t sm_tri = std::max(gemm_doubles, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
     // strip rows per shared-memory chunk of k_apply_q_rows: at most DCLNO_RPW per warp, within 200 KB
@@ -1010,14 +1029,16 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL did not converge for cluster " + std::to_string(i));
         if (st[k] == ST_LOG_FULL)
             return set_err(c, DCLNO_ERR_NOT_CONVERGED, "QL rotation log full for cluster " + std::to_string(i));
+        if (st[k] == ST_TIMEOUT)
+            return set_err(c, DCLNO_ERR_TIMEOUT, "tensor-core wait ran out for cluster " + std::to_string(i));
         if (st[k] != ST_OK) return set_err(c, DCLNO_ERR_NOT_CONVERGED, "solver failed for cluster " + std::to_string(i));
     }
     return DCLNO_OK;
 }
 
 dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only) {
-    return launch_solve<false>(c, b, reduce_only);
+    return launch_solve<0>(c, b, reduce_only);
 }
 dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only) {
-    return launch_solve<true>(c, b, reduce_only);
+    return c->mixed_engine == 1 ? launch_solve<1>(c, b, reduce_only) : launch_solve<2>(c, b, reduce_only);
 }
