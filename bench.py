@@ -58,6 +58,11 @@ def parse():
                         "amorphous32000: the 32,000-atom random packing, generated row range by row range "
                         "into device memory and solved through memory-admitted batches")
     p.add_argument("--atoms", type=int, default=32000, help="atoms of the amorphous workload (same density)")
+    p.add_argument("--tridiag", type=int, choices=[0, 1, 2], default=0,
+                   help="tridiagonalisation form of both paths: 0 the library's automatic choice, 1 one-stage, "
+                        "2 two-stage (dense -> band -> tridiagonal)")
+    p.add_argument("--mixed-engine", type=int, choices=[1, 2], default=2,
+                   help="tensor-core engine of the mixed path: 1 mma.sync, 2 tcgen05 with tensor memory")
     return p.parse_args()
 
 
@@ -513,6 +518,8 @@ def run_ours(args):
     ctx = Context(stream=stream.cuda_stream)
     ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
                        s.r_core, s.r_lno, s.k_lno)
+    ctx.set_tridiag(args.tridiag)
+    ctx.set_mixed_engine(args.mixed_engine)
     dims = ctx.cluster_info()[0]
     ncl = int(s.natoms)
 
@@ -640,7 +647,8 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD if args.workload == "rocksalt1728" else args.workload,
                            "precision": "fp64", "clusters": ncl,
                            "cluster_dim_min": int(dims.min()), "cluster_dim_max": int(dims.max()),
-                           "parallelism": f"replicas x{world}",
+                           "parallelism": f"replicas x{world}", "tridiag_option": args.tridiag,
+                           "mixed_engine": args.mixed_engine,
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "mu": mu, "n_electrons": n_mu, "e_band": e_band}

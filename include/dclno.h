@@ -192,8 +192,8 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
 /*
  * Form of the Householder tridiagonalisation in dclno_solve_clusters (Sec. II.C
  * step (iii); both give the same T up to rounding and the same eigenpairs):
- *   0  automatic (default): the form measured faster on this GPU for the
- *      precision of the solve (at present the one-stage form in both);
+ *   0  automatic (default): the form measured faster on GB300 for the precision
+ *      of the solve (one-stage in FP64, two-stage in the mixed path);
  *   1  one-stage: blocked Householder with a symmetric matrix-vector product per
  *      column (each column reads the whole trailing matrix);
  *   2  two-stage: dense -> band of half-width 32 (blocked Householder whose

@@ -156,12 +156,18 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         double* A22 = A + (size_t)r0 * ld + r0;
         for (int e = tid; e < BW * m; e += blockDim.x) Yt[(size_t)(e / m) * ld + e % m] = 0.0;
         __syncthreads();
-        tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G, &tcs);
+        if constexpr (EMU == 2)  // Y = A22 V, one FP64 epilogue per element, written as Y^T
+            cta_gemm_tc_longk<true>(Yt, ld, A22, ld, NVt, ld, m, BW, m, reinterpret_cast<unsigned char*>(G), &tcs);
+        else
+            tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G, &tcs);
         // (5) [-V^T V | V^T Y] = -(-V^T) [-V^T ; Y^T]^T ... as C -= A B^T with B = the 2BW rows
         // of NVt and Yt (contiguous, stride ld): C = -(V^T V) on the left, +V^T Y on the right
         for (int e = tid; e < BW * gz; e += blockDim.x) GZ[e] = 0.0;
         __syncthreads();
-        tile_update_longk<EMU>(GZ, gz, NVt, ld, NVt, ld, BW, 2 * BW, m, G, &tcs);
+        if constexpr (EMU == 2)  // its transpose [-V^T V ; Y^T V] = -[-V^T ; Y^T] (-V^T)^T, written transposed
+            cta_gemm_tc_longk<true>(GZ, gz, NVt, ld, NVt, ld, 2 * BW, BW, m, reinterpret_cast<unsigned char*>(G), &tcs);
+        else
+            tile_update_longk<EMU>(GZ, gz, NVt, ld, NVt, ld, BW, 2 * BW, m, G, &tcs);
         // (6) T (upper triangular): T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j]
         if (warp == 0) {
             for (int j = 0; j < BW; ++j) {

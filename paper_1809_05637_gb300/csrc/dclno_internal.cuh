@@ -436,46 +436,83 @@ __device__ __forceinline__ void warp_reflect_short(double* X, int ldx, int p, in
         if (lane < len) X[(size_t)j * ldx + p + lane] = fma(-u[j], v, X[(size_t)j * ldx + p + lane]);
 }
 
+// Sum over the 32 lanes of 16 values per lane at once ("transposing" reduction): each
+// step halves the values a lane keeps, sending the other half to its partner, so the
+// 16 sums cost 8 + 4 + 2 + 1 + 1 = 16 FP64 adds per lane instead of 16 x 5 for separate
+// butterflies (on this GPU a warp-wide FP64 instruction occupies the SM's FP64 pipe for
+// about 19 cycles).  On return lane L holds the sum of value (L >> 1) & 15.
+__device__ __forceinline__ double warp_sum16(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16, cnt = 8; s >= 2; s >>= 1, cnt >>= 1) {
+        const bool hi = (lane & s) != 0;  // this lane keeps the upper half of its values
+#pragma unroll
+        for (int i = 0; i < cnt; ++i) {
+            const double send = hi ? v[i] : v[i + cnt];
+            const double keep = hi ? v[i + cnt] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// The same for 8 values per lane (4 + 2 + 1 transposing adds, then 2 butterfly adds):
+// on return lane L holds the sum of value (L >> 2) & 7.
+__device__ __forceinline__ double warp_sum8(double (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16, cnt = 4; s >= 4; s >>= 1, cnt >>= 1) {
+        const bool hi = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < cnt; ++i) {
+            const double send = hi ? v[i] : v[i + cnt];
+            const double keep = hi ? v[i + cnt] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    const double a = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+    return a + __shfl_xor_sync(0xffffffffu, a, 1);
+}
+
 // The chase reflectors of sweep j (disjoint windows [p_k, p_k + len_k), p_k = j + 1 + k BW)
-// on the R rows of X owned by this warp, KW windows at a time: the KW x R dot products
-// are reduced by interleaved butterflies, so their shuffle and FP64-add latencies overlap
-// (a reflector alone is a chain of five dependent shuffle-adds).  Windows of one sweep
-// commute, so the same code serves both directions.
-#define DCLNO_CHASE_KW 4
+// on the R rows of X owned by this warp: KW = 16 / R windows at a time, their KW x R dot
+// products reduced together by warp_sum16.  Windows of one sweep commute, so the same
+// code serves both directions.
 template <int R>
 __device__ __forceinline__ void warp_chase_sweep(double* X, int n, int j, const double* __restrict__ slot0) {
+    constexpr int KW = 16 / R;
     const int lane = threadIdx.x & 31;
     const int ns = (int)chase_steps(n, j);
-    for (int k0 = 0; k0 < ns; k0 += DCLNO_CHASE_KW) {
-        double v[DCLNO_CHASE_KW], tau[DCLNO_CHASE_KW], u[DCLNO_CHASE_KW][R];
-        int p[DCLNO_CHASE_KW];
-        bool on[DCLNO_CHASE_KW];
+    for (int k0 = 0; k0 < ns; k0 += KW) {
+        double v[KW], val[16];
+        int p[KW];
+        bool on[KW];
 #pragma unroll
-        for (int w = 0; w < DCLNO_CHASE_KW; ++w) {
+        for (int i = 0; i < 16; ++i) val[i] = 0.0;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
             const int k = k0 + w;
             p[w] = j + 1 + k * DCLNO_BW;
             const int len = k < ns ? min(DCLNO_BW, n - p[w]) : 0;
             const double* sl = slot0 + (size_t)k * DCLNO_BW;
-            tau[w] = k < ns ? sl[0] : 0.0;
             on[w] = lane < len;
+            const double tau = k < ns ? sl[0] : 0.0;
             v[w] = !on[w] ? 0.0 : (lane == 0 ? 1.0 : sl[lane]);
+            const double vt = tau * v[w];  // the dot products come out scaled by tau
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[w][r] = on[w] ? X[(size_t)r * n + p[w] + lane] * v[w] : 0.0;
+            for (int r = 0; r < R; ++r) val[w * R + r] = on[w] ? X[(size_t)r * n + p[w] + lane] * vt : 0.0;
         }
+        const double mine = warp_sum16(val);  // lane L: pair (L >> 1) & 15 = w R + r
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+        for (int w = 0; w < KW; ++w)
 #pragma unroll
-            for (int w = 0; w < DCLNO_CHASE_KW; ++w)
-#pragma unroll
-                for (int r = 0; r < R; ++r) u[w][r] += __shfl_xor_sync(0xffffffffu, u[w][r], o);
-#pragma unroll
-        for (int w = 0; w < DCLNO_CHASE_KW; ++w)
-            if (on[w])
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < R; ++r) {
+                const double u = __shfl_sync(0xffffffffu, mine, 2 * (w * R + r));
+                if (on[w]) {
                     double* x = X + (size_t)r * n + p[w] + lane;
-                    *x = fma(-tau[w] * u[w][r], v[w], *x);
+                    *x = fma(-u, v[w], *x);
                 }
+            }
     }
 }
 

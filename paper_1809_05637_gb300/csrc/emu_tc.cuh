@@ -263,3 +263,198 @@ __device__ void cta_gemm_nt_sub_tc(double* __restrict__ C, int ldc, const double
     }
     __syncthreads();
 }
+
+// ---------------------------------------------------------------------------
+// Long-K products with one FP64 epilogue: C[M x N] -= A[M x K] B[N x K]^T for any K,
+// N <= 32 per tile column (tiles of 128 x 32).  Row exponents are taken over all of K
+// (a first pass over the tile's rows), every K-chunk of 32 is sliced against them, and
+// the integer totals of all chunks are kept in registers (|total| < 2^54 per chunk, so
+// up to 500 chunks fit 64 bits); each output then costs two FP64 instructions in all,
+// instead of two per chunk.  TRANS writes element (r, c) to C[c * ldc + r].
+// smem: TC_SMEM_BYTES; tensor memory: columns [0, 64) of the CTA's allocation.
+// ---------------------------------------------------------------------------
+#define TCL_N 32
+#define TCL_B_SLICE_BYTES (TCL_N * TC_K * 2)  // 2048
+
+// largest exponent of rows [r0, r0 + rows) of X over k < K (warp per row)
+__device__ __forceinline__ void tcl_row_expo(const double* __restrict__ X, int ld, int r0, int rows, int nrows, int K,
+                                             int* expo) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        const int gr = r0 + r;
+        int e = -100000;
+        if (gr < nrows)
+            for (int k = lane; k < K; k += 32) {
+                const int eb = (int)((__double_as_longlong(X[(size_t)gr * ld + k]) >> 52) & 0x7ff);
+                if (eb != 0) e = max(e, eb - 1023);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (lane == 0) expo[r] = e;
+    }
+}
+
+// slices of rows [r0, r0 + ROWS) x k [k0, k0 + 32) against the fixed row exponents expo[]
+template <int ROWS>
+__device__ __forceinline__ void tcl_slice_chunk(const double* __restrict__ X, int ld, int r0, int nrows, int k0, int K,
+                                                const int* expo, unsigned char* sl, int slice_bytes) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int kofs = (lane >> 3) * TC_LBO + (lane & 7) * 2;
+    constexpr int PER = (ROWS + 7) / 8;  // rows per warp (eight warps): loads issued together
+    double x[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int r = warp + i * nw, gr = r0 + r, gk = k0 + lane;
+        x[i] = (r < ROWS && gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int r = warp + i * nw;
+        if (r >= ROWS) break;
+        const long long b = __double_as_longlong(x[i]);
+        const int ebits = (int)((b >> 52) & 0x7ff);
+        unsigned long long al = 0ull;
+        if (ebits != 0) {
+            const unsigned long long man = ((unsigned long long)b & 0xfffffffffffffull) | 0x10000000000000ull;
+            const int sh = expo[r] - (ebits - 1023);
+            al = sh >= 64 ? 0ull : ((man << 11) >> sh);
+        }
+        const bool neg = b < 0;
+        unsigned char* dst = sl + (r >> 3) * TC_SBO + (r & 7) * 16 + kofs;
+#pragma unroll
+        for (int t = 0; t < TC_SL; ++t) {
+            const int v = (int)((al >> (56 - 8 * t)) & 0xffull);
+            *reinterpret_cast<__nv_bfloat16*>(dst + t * slice_bytes) = __float2bfloat16_rn((float)(neg ? -v : v));
+        }
+    }
+}
+
+__device__ __forceinline__ void tcl_issue_level(TcState* st, const unsigned char* As, const unsigned char* Bs, int L,
+                                                int buf) {
+    const uint32_t d = st->tmem + (uint32_t)(buf * TCL_N);
+    const uint32_t id = tc_idesc(TC_M, TCL_N);
+    const uint32_t a0 = tc_smem_u32(As), b0 = tc_smem_u32(Bs);
+    int first = 1;
+    for (int t = 0; t <= L; ++t) {
+        const int u = L - t;
+#pragma unroll
+        for (int ks = 0; ks < TC_K / 16; ++ks) {
+            const uint64_t ad = tc_desc(a0 + t * TC_A_SLICE_BYTES + ks * 2 * TC_LBO);
+            const uint64_t bd = tc_desc(b0 + u * TCL_B_SLICE_BYTES + ks * 2 * TC_LBO);
+            asm volatile(
+                "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(id), "r"(first ? 0 : 1));
+            first = 0;
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        tc_smem_u32(&st->mbar[buf])));
+    st->issued[buf] += 1;
+}
+
+template <bool TRANS>
+__device__ void cta_gemm_tc_longk(double* __restrict__ C, int ldc, const double* __restrict__ A, int lda,
+                                  const double* __restrict__ B, int ldb, int M, int N, int K, unsigned char* smem,
+                                  TcState* st) {
+    unsigned char* As = smem;
+    unsigned char* Bs = As + TC_SL * TC_A_SLICE_BYTES;
+    int* ea = reinterpret_cast<int*>(Bs + TC_SL * TCL_B_SLICE_BYTES);
+    int* eb = ea + TC_M;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int q = warp & 3, h = warp >> 2;  // rows 32 q .., columns 16 h ..
+    const int tilesM = (M + TC_M - 1) / TC_M, tilesN = (N + TCL_N - 1) / TCL_N;
+    for (int tix = 0; tix < tilesM * tilesN; ++tix) {
+        if (st->failed) break;
+        const int ti = tix / tilesN, tj = tix % tilesN;
+        const int r0 = ti * TC_M, c0 = tj * TCL_N;
+        tcl_row_expo(A, lda, r0, TC_M, M, K, ea);
+        tcl_row_expo(B, ldb, c0, TCL_N, N, K, eb);
+        __syncthreads();
+        long long tot[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tot[j] = 0;
+        bool ok = true;
+        for (int k0 = 0; k0 < K && ok; k0 += TC_K) {
+            tcl_slice_chunk<TC_M>(A, lda, r0, M, k0, K, ea, As, TC_A_SLICE_BYTES);
+            tcl_slice_chunk<TCL_N>(B, ldb, c0, N, k0, K, eb, Bs, TCL_B_SLICE_BYTES);
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                tcl_issue_level(st, As, Bs, 0, 0);
+                tcl_issue_level(st, As, Bs, 1, 1);
+            }
+            for (int L = 0; L < TC_SL; ++L) {
+                const int buf = L & 1;
+                ok = ok && tc_wait(&st->mbar[buf], st->uses[buf]);
+                if (!ok) st->failed = 1;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (ok) {
+                    uint32_t r[16];
+                    const uint32_t ta = st->tmem + (uint32_t)(buf * TCL_N + 16 * h) + ((uint32_t)(32 * q) << 16);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                        " [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long a = (long long)__float2int_rn(__uint_as_float(r[j]));
+                        tot[j] += (L <= 4) ? (a << (32 - 8 * L)) : (a >> (8 * L - 32));
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+                if (tid == 0) {
+                    ok = ok && !st->failed;
+                    st->uses[buf] += 1;
+                    if (ok && L + 2 < TC_SL) {
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        tcl_issue_level(st, As, Bs, L + 2, buf);
+                    }
+                }
+                __syncthreads();
+                ok = !st->failed;
+            }
+        }
+        if (!ok) break;
+        // one epilogue: (tot >> 3) 2^(ea + eb - 43), staged through shared memory (the A
+        // slices) for row-contiguous (or, with TRANS, column-contiguous) updates of C
+        double* Vs = reinterpret_cast<double*>(As);  // TC_M x TCL_N, columns XOR-swizzled by the row
+        {
+            const int rl = 32 * q + lane;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int cl = 16 * h + j;
+                Vs[rl * TCL_N + (cl ^ (rl & 15))] = (double)(tot[j] >> 3);
+            }
+        }
+        __syncthreads();
+        if (!TRANS) {
+            for (int rr = warp; rr < TC_M; rr += nw) {
+                const int r = r0 + rr, cl = lane, cc = c0 + cl;
+                if (r >= M || cc >= N) continue;
+                const int es = ea[rr] + eb[cl] - 43 + 1023;
+                if (es < 1 || es > 2046) continue;
+                double* pc = C + (size_t)r * ldc + cc;
+                *pc = fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), *pc);
+            }
+        } else {
+            for (int idx = tid; idx < TC_M * TCL_N; idx += blockDim.x) {
+                const int cl = idx / TC_M, rr = idx % TC_M;
+                const int r = r0 + rr, cc = c0 + cl;
+                if (r >= M || cc >= N) continue;
+                const int es = ea[rr] + eb[cl] - 43 + 1023;
+                if (es < 1 || es > 2046) continue;
+                double* pc = C + (size_t)cc * ldc + r;
+                *pc = fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), *pc);
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+}
