@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
+    p.add_argument("--no-amorphous", action="store_true",
+                   help="skip the one-step measurement of the 32,000-atom amorphous workload (run on one GPU only)")
     p.add_argument("--workload", choices=["rocksalt1728", "rocksalt512", "small64", "amorphous32000"],
                    default="rocksalt1728",
                    help="rocksalt512: the same rock-salt recipe on 8^3 sites (the same cluster dimensions, one "
@@ -61,8 +63,10 @@ def parse():
     p.add_argument("--tridiag", type=int, choices=[0, 1, 2], default=0,
                    help="tridiagonalisation form of both paths: 0 the library's automatic choice, 1 one-stage, "
                         "2 two-stage (dense -> band -> tridiagonal)")
-    p.add_argument("--mixed-engine", type=int, choices=[1, 2], default=2,
-                   help="tensor-core engine of the mixed path: 1 mma.sync, 2 tcgen05 with tensor memory")
+    p.add_argument("--mixed-engine", type=int, choices=[0, 1, 2], default=0,
+                   help="tensor-core engine of the mixed path's Cholesky, congruence and one-stage "
+                        "tridiagonalisation: 0 tuned per size bucket, 1 mma.sync, 2 tcgen05 with tensor memory "
+                        "(the band reduction's long-K products always run on tcgen05)")
     return p.parse_args()
 
 
@@ -275,6 +279,10 @@ def measure_scf(world):
         dims = ctx.cluster_info()[0]
         out["cluster_dim_min"], out["cluster_dim_max"] = int(dims.min()), int(dims.max())
         for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
+            # eager steps first: the schedule tuner decides outside graph capture
+            tmp = torch.zeros_like(rho0)
+            for _ in range(TUNE_STEPS):
+                ctx.step(rho0, tmp, s.n_electrons, s.kT, precision=prec)
             rho = rho0.clone()
             ctx.scf_run(rho, 1, 0.3, s.n_electrons, s.kT, prec, use_graph=True)  # warm-up
             rho = rho0.clone()
@@ -287,6 +295,7 @@ def measure_scf(world):
             ms = max_over_ranks(e0.elapsed_time(e1), world)
             out[name] = {"value": replica_throughput(world, s.natoms, SCF_STEPS, ms / 1e3), "unit": "clusters/s",
                          "ms_per_step": ms / SCF_STEPS, "mu_last": float(mu[-1]), "e_band_last": float(eb[-1])}
+        out["schedules"] = schedule_summary(ctx.tuning_report())
         ctx.close()
     out["e_band_diff_per_atom_mixed_vs_fp64"] = abs(out["mixed"]["e_band_last"] - out["fp64"]["e_band_last"]) / s.natoms
     return out
@@ -300,12 +309,13 @@ AMORPHOUS = ("DC-LNO step, {n}-atom amorphous two-species packing (random sequen
              "4 LNOs/atom, kT=0.01 Ha, memory-admitted batches")
 
 
-def run_streamed(args):
+def measure_amorphous(n_atoms):
     """One LNO step of the amorphous workload in FP64 and in mixed precision: S, H
-    and the input density are generated row range by row range straight into
-    device memory (the host never holds them), the context admits the cluster
-    workspace in batches; invariants on the device and sampled clusters against
-    the oracle (host blocks computed only for the rows those clusters touch)."""
+    and the input density are generated row range by row range (host threads) straight
+    into device memory (the host never holds them), the context admits the cluster
+    workspace in batches; invariants on the device and, for both paths, sampled
+    clusters against the oracle (host blocks computed only for the rows those clusters
+    touch)."""
     import numpy as np
     import torch
 
@@ -316,21 +326,17 @@ def run_streamed(args):
         return sum(float(torch.dot(a[k:k + chunk], b[k:k + chunk])) for k in range(0, a.numel(), chunk))
 
     t0 = time.perf_counter()
-    s = T.make_system_streamed(5, n_atoms=args.atoms)
+    s = T.make_system_streamed(5, n_atoms=n_atoms)
     t_struct = time.perf_counter() - t0
     nval = len(s.S)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     H = torch.empty(nval, dtype=torch.float64, device=dev)
     S = torch.empty_like(H)
     R = torch.empty_like(H)
-    for i0 in range(0, s.natoms, 512):
-        i1 = min(s.natoms, i0 + 512)
-        o0, sv, hv = T.row_values(s, i0, i1)
+    for i0, i1, o0, sv, hv, rv in T.row_chunks(s, 128, density_seed=11):
         S[o0:o0 + len(sv)].copy_(torch.from_numpy(sv))
         H[o0:o0 + len(hv)].copy_(torch.from_numpy(hv))
-        buf = np.empty(len(sv))
-        T.synthetic_density_rows(s, i0, i1, buf, seed=11, base=o0)
-        R[o0:o0 + len(buf)].copy_(torch.from_numpy(buf))
+        R[o0:o0 + len(rv)].copy_(torch.from_numpy(rv))
     torch.cuda.synchronize()
     t_fill = time.perf_counter() - t0 - t_struct
     out = torch.zeros_like(H)
@@ -338,13 +344,15 @@ def run_streamed(args):
     ctx = Context(stream=stream.cuda_stream)
     ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
                        s.r_core, s.r_lno, s.k_lno)
+    t_build = time.perf_counter() - t0 - t_struct - t_fill
     nb, ws = ctx.batch_info()
     dims = ctx.cluster_info()[0]
-    print(f"structure {t_struct:.0f} s, device fill {t_fill:.0f} s, {nb} batches of <= {ws / 1e9:.1f} GB",
-          file=sys.stderr, flush=True)
+    print(f"amorphous {s.natoms}: structure {t_struct:.0f} s, device fill {t_fill:.0f} s, clusters {t_build:.0f} s, "
+          f"{nb} batches of <= {ws / 1e9:.1f} GB", file=sys.stderr, flush=True)
     res = {}
     for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
-        ctx.step(R, out, s.n_electrons, s.kT, precision=prec)  # warm-up (tunes the QL launch shape)
+        # warm-up: tunes the QL launch shape and (batches share tuner slots) the schedules
+        ctx.step(R, out, s.n_electrons, s.kT, precision=prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -356,13 +364,10 @@ def run_streamed(args):
                      "n_electrons": n, "e_band": eb,
                      "trace_rho_s_minus_n": abs(2.0 * ddot(out, S) - n) / s.n_electrons,
                      "trace_rho_h_minus_eband": abs(2.0 * ddot(out, H) - eb) / abs(eb)}
-    # sampled clusters against the oracle (FP64 path, fixed mu)
+    # sampled clusters against the oracle (both paths, rows at the FP64 step's mu)
     import oracle as O
 
     mu_fix = res["fp64"]["mu"]
-    ctx.step(R, out, s.n_electrons, s.kT, precision=DCLNO_FP64)
-    ctx.density_matrix(mu_fix, s.kT, out)
-    spec = ctx.spectrum()
     sample = [0, s.natoms // 2]
     cls = {i: O.cluster_members(s, i, s.r_core, s.r_lno, s.k_lno) for i in sample}
     rows_needed = set()
@@ -379,28 +384,40 @@ def run_streamed(args):
     V = {j: v[0] for j, v in lno.items()}
     ores = O.dclno_solve(s, V, s.r_core, s.r_lno, s.k_lno, atoms=sample, threads=len(sample))
     out_rows = np.zeros(nval)
-    deps, deps_b, drho = 0.0, 0.0, 0.0
     for i, r in ores.items():
-        d = np.abs(np.sort(spec[i][0]) - r.eps)
-        # first-order bound of a backward error n u in H^(i), S^(i) (c^T S c = 1)
-        bound = 1e-10 + 2.0 * len(r.eps) * 2.0 ** -53 * (r.h_norm + np.abs(r.eps) * r.s_norm) * np.einsum(
-            "am,am->m", r.C, r.C)
-        deps = max(deps, float(np.max(d)))
-        deps_b = max(deps_b, float(np.max(d / bound)))
         O.density_rows(s, r.cluster, r.eps, r.C, V, mu_fix, s.kT, out_rows)
-        o0, o1 = int(s.blk_off[s.row_ptr[i]]), int(s.blk_off[s.row_ptr[i + 1]])
-        g = out[o0:o1].cpu().numpy()
-        drho = max(drho, float(np.max(np.abs(g - out_rows[o0:o1])) / np.max(np.abs(out_rows[o0:o1]))))
+    for name, prec in (("fp64", DCLNO_FP64), ("mixed", DCLNO_MIXED)):
+        ctx.step(R, out, s.n_electrons, s.kT, precision=prec)
+        ctx.density_matrix(mu_fix, s.kT, out)
+        spec = ctx.spectrum()
+        deps, deps_b, drho = 0.0, 0.0, 0.0
+        for i, r in ores.items():
+            d = np.abs(np.sort(spec[i][0]) - r.eps)
+            # first-order bound of a backward error n u in H^(i), S^(i) (c^T S c = 1)
+            bound = 1e-10 + 2.0 * len(r.eps) * 2.0 ** -53 * (r.h_norm + np.abs(r.eps) * r.s_norm) * np.einsum(
+                "am,am->m", r.C, r.C)
+            deps = max(deps, float(np.max(d)))
+            deps_b = max(deps_b, float(np.max(d / bound)))
+            o0, o1 = int(s.blk_off[s.row_ptr[i]]), int(s.blk_off[s.row_ptr[i + 1]])
+            g = out[o0:o1].cpu().numpy()
+            drho = max(drho, float(np.max(np.abs(g - out_rows[o0:o1])) / np.max(np.abs(out_rows[o0:o1]))))
+        res[name]["oracle_sample"] = {"clusters": sample, "max_abs_eps_diff_ha": deps,
+                                      "max_eps_diff_over_first_order_bound": deps_b,
+                                      "max_rho_row_diff_rel_to_row_max": drho, "mu": mu_fix}
+    schedules = schedule_summary(ctx.tuning_report())
     ctx.close()
-    line = {"workload": AMORPHOUS.format(n=s.natoms), "clusters": s.natoms, "cluster_dim_min": int(dims.min()),
+    del H, S, R, out
+    torch.cuda.empty_cache()
+    return {"workload": AMORPHOUS.format(n=s.natoms), "clusters": s.natoms, "cluster_dim_min": int(dims.min()),
             "cluster_dim_max": int(dims.max()), "stored_blocks": int(len(s.col)), "matrix_gb": nval * 8 / 1e9,
             "batches": nb, "workspace_gb": ws / 1e9, "host_structure_s": t_struct, "fill_s": t_fill,
-            "fp64": res["fp64"], "mixed": res["mixed"],
+            "clusters_build_s": t_build, "fp64": res["fp64"], "mixed": res["mixed"],
             "e_band_diff_per_atom_mixed_vs_fp64": abs(res["mixed"]["e_band"] - res["fp64"]["e_band"]) / s.natoms,
-            "oracle_sample": {"clusters": sample, "max_abs_eps_diff": deps,
-                              "max_eps_diff_over_first_order_bound": deps_b, "max_rho_row_diff_rel_to_row_max": drho,
-                              "mu": mu_fix}}
-    print(json.dumps(line))
+            "schedules": schedules}
+
+
+def run_streamed(args):
+    print(json.dumps(measure_amorphous(args.atoms)))
     return 0
 
 
@@ -467,6 +484,20 @@ def roofline_report(kernel, path, n, k_ms, k_n, dfma, dmma, bf16, bf16_src):
             "launch_ms": launch_s * 1e3 if launch_s else None}
 
 
+TUNE_STEPS = 4  # eager solves the schedule tuner needs to decide (its largest candidate set)
+
+
+def schedule_summary(report):
+    """Per precision and kernel: (rounded cluster dimension, engine, persistent grid) of
+    every size bucket, from the library's tuning report."""
+    out = {}
+    for b in report.get("batches", []):
+        for bk in b["buckets"]:
+            for name, v in bk["schedules"].items():
+                out.setdefault(name, []).append([bk["n_rounded"], v["engine"], v["persistent"], v["decided"]])
+    return out
+
+
 def dominant(times):
     """The roofline kernel with the largest time in a {kernel: (ms, launches)} map."""
     have = [(times[k][0], k) for k in ROOFLINE_KERNELS if times.get(k, (0.0, 0))[1] > 0]
@@ -516,9 +547,9 @@ def run_ours(args):
     rho_out = torch.zeros_like(rho_in)
     stream = torch.cuda.current_stream(dev)
     ctx = Context(stream=stream.cuda_stream)
+    ctx.set_tridiag(args.tridiag)  # before the build: the two-stage form lays out its reflector log there
     ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
                        s.r_core, s.r_lno, s.k_lno)
-    ctx.set_tridiag(args.tridiag)
     ctx.set_mixed_engine(args.mixed_engine)
     dims = ctx.cluster_info()[0]
     ncl = int(s.natoms)
@@ -526,7 +557,10 @@ def run_ours(args):
     def step(prec=DCLNO_FP64):
         return ctx.step(rho_in, rho_out, s.n_electrons, s.kT, precision=prec)
 
-    for _ in range(max(args.warmup, 3)):
+    # warm-up: at least TUNE_STEPS eager steps, so that the schedule tuner (which times one
+    # candidate per size bucket and kernel per eager solve) has decided before the timing
+    warmup = max(args.warmup, 3, TUNE_STEPS)
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     ctx.set_profiling(True)
@@ -562,7 +596,8 @@ def run_ours(args):
 
     # the mixed-precision form of the same step (BF16 tensor-core emulation of the FP64
     # contractions), timed the same way; accuracy against the FP64 step above
-    step(DCLNO_MIXED)
+    for _ in range(warmup):
+        step(DCLNO_MIXED)
     torch.cuda.synchronize()
     ctx.set_profiling(True)
     if world > 1:
@@ -621,11 +656,20 @@ def run_ours(args):
                                                       two_stage=tmx.get("k_band", (0, 0))[1] > 0)
     mixed["roofline"]["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in tmx.items() if v[1]}
     mixed["tridiagonalisation"] = "two-stage (k_band + k_chase)" if tmx.get("k_band", (0, 0))[1] else "one-stage"
+    schedules = schedule_summary(ctx.tuning_report())
 
     scf = None
     if not args.no_scf:
         ctx.close()
         scf = measure_scf(world)
+
+    # the 32,000-atom amorphous workload (memory-admitted batches), one GPU only
+    amorphous = None
+    if world == 1 and args.workload == "rocksalt1728" and not args.no_amorphous:
+        ctx.close()
+        del H, S, rho_in, rho_out
+        torch.cuda.empty_cache()
+        amorphous = measure_amorphous(args.atoms)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -642,7 +686,7 @@ def run_ours(args):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
-                "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "warmup": warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD if args.workload == "rocksalt1728" else args.workload,
                            "precision": "fp64", "clusters": ncl,
@@ -651,7 +695,9 @@ def run_ours(args):
                            "mixed_engine": args.mixed_engine,
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-                "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "mu": mu, "n_electrons": n_mu, "e_band": e_band}
+                "schedules": schedules,
+                "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "amorphous32000": amorphous, "mu": mu,
+                "n_electrons": n_mu, "e_band": e_band}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -192,8 +192,8 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
 /*
  * Form of the Householder tridiagonalisation in dclno_solve_clusters (Sec. II.C
  * step (iii); both give the same T up to rounding and the same eigenpairs):
- *   0  automatic (default): the form measured faster on GB300 for the precision
- *      of the solve (one-stage in FP64, two-stage in the mixed path);
+ *   0  automatic (default): the form measured faster on GB300, at present the
+ *      one-stage form in both precisions;
  *   1  one-stage: blocked Householder with a symmetric matrix-vector product per
  *      column (each column reads the whole trailing matrix);
  *   2  two-stage: dense -> band of half-width 32 (blocked Householder whose
@@ -201,23 +201,72 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
  *      Householder bulge chasing.
  * The two-stage form applies to clusters of dimension >= 128 (smaller ones use the
  * one-stage form); it keeps a log of about n^2/2 doubles of chase reflectors per
- * cluster, which the layout of dclno_build_clusters always reserves.  Takes effect
- * at the next solve.  Errors: DCLNO_ERR_ARG for another mode.
+ * cluster, which dclno_build_clusters reserves only when the mode is 2 at that time:
+ * select mode 2 before building.  Modes 0 and 1 can be selected at any time, and mode
+ * 2 again on a context built in mode 2; each takes effect at the next solve.
+ * Errors: DCLNO_ERR_ARG for another mode, or for mode 2 on clusters built without
+ * the log.
  */
 dclno_status dclno_set_tridiag(dclno_ctx *ctx, int mode);
 
 /*
  * Tensor-core engine of the mixed path's emulated FP64 tile products (the same
- * arithmetic either way: eight 8-bit slices per FP64 row, exact FP32 level sums,
- * exact 64-bit level combination):
+ * arithmetic and the same bits either way: eight 8-bit slices per FP64 row, exact
+ * FP32 level sums, exact 64-bit level combination) for the products with K <= 32
+ * (Cholesky, congruence, one-stage tridiagonalisation):
+ *   0  chosen per kernel and size bucket by the schedule tuner (default);
  *   1  mma.sync.m16n8k16 BF16 from register fragments;
- *   2  tcgen05.mma with the level accumulators in tensor memory (default): one
- *      thread issues the products of a level while the CTA's warps combine the
- *      previous level; each CTA of the cubic kernels holds 128 tensor-memory columns.
- * A tensor-core wait that runs out fails the solve with DCLNO_ERR_TIMEOUT (cluster
- * in the message).  Takes effect at the next solve; DCLNO_ERR_ARG for another value.
+ *   2  tcgen05.mma with the level accumulators in tensor memory: one thread issues
+ *      the products of a level while the CTA's warps combine the previous level.
+ * The long-K products (Y = A22 V of the band reduction, the merge-matrix products)
+ * always run on tcgen05 with one FP64 epilogue per output.  Each CTA using tcgen05
+ * holds 128 tensor-memory columns.  A tensor-core wait that runs out fails the solve
+ * with DCLNO_ERR_TIMEOUT (cluster in the message).  Takes effect at the next solve
+ * and clears the tuned schedules; DCLNO_ERR_ARG for another value.
  */
 dclno_status dclno_set_mixed_engine(dclno_ctx *ctx, int engine);
+
+/*
+ * Scheduling of the cubic kernels (Cholesky, congruence, tridiagonalisation, band
+ * reduction, bulge chasing).  A batch's clusters, in decreasing-dimension order, form
+ * size buckets (dimension rounded up to 64; a bucket below the minimum count of
+ * dclno_set_bucket_min merged into its neighbour).  For each bucket and kernel the grid
+ * is either one CTA per cluster or persistent (as many CTAs as fit the GPU, each taking
+ * clusters from an atomic work counter; no CTA waits on another), and in the mixed
+ * path the engine of dclno_set_mixed_engine; consecutive buckets with the same
+ * schedule run as one launch.  None of these choices changes a bit of the results.
+ * mode 0 (default): the tuner picks: every eager solve of a batch (not one captured
+ * into a CUDA graph) times each bucket's kernels under the next untried candidate
+ * (timings per cluster, shared by batches with the same rounded dimension), then keeps
+ * the fastest, or the untuned default when it is within 2% (at most four solves per
+ * precision); 1: one CTA per cluster; 2: persistent.  DCLNO_ERR_ARG for another mode.
+ */
+dclno_status dclno_set_schedule(dclno_ctx *ctx, int mode);
+
+/*
+ * Minimum clusters per size bucket (default 0: twice the GPU's SM count).  Every launch
+ * ends in a tail while its last clusters finish, so a bucket of a few clusters costs
+ * about the time of one cluster while the rest of the GPU idles; smaller buckets are
+ * merged into a neighbour.  1 keeps every 64-wide bucket.  Rebuilds the buckets of the
+ * current clusters and clears the tuned schedules; DCLNO_ERR_ARG for a negative count.
+ */
+dclno_status dclno_set_bucket_min(dclno_ctx *ctx, int count);
+
+/*
+ * Text cache of tuned schedules (one line per GPU name, precision, kernel and rounded
+ * dimension), read now if the file exists and rewritten whenever the tuner decides a
+ * schedule; a later context given the same path starts with those schedules.  NULL
+ * switches the cache off.  An unreadable file is treated as empty.
+ */
+dclno_status dclno_set_tuning_cache(dclno_ctx *ctx, const char *path);
+
+/*
+ * JSON summary of the size buckets and their schedules (engine, grid form, whether
+ * decided, taken from the cache, and the timed milliseconds of each candidate),
+ * written to buf (host, len bytes, NUL-terminated, truncated if short); *needed
+ * (nullable) receives the full length including the NUL.
+ */
+dclno_status dclno_tuning_report(dclno_ctx *ctx, char *buf, size_t len, size_t *needed);
 dclno_status dclno_get_tuning(dclno_ctx *ctx, int batch, int *ql_lanes_out, float *candidate_ms);
 
 /*

@@ -24,7 +24,8 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_density_matrices", "dclno_set_workspace_limit", "dclno_batch_info",
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
            "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles",
-           "dclno_set_mixed_engine"]
+           "dclno_set_mixed_engine", "dclno_set_schedule", "dclno_set_tuning_cache", "dclno_tuning_report",
+           "dclno_set_bucket_min"]
 
 
 class DclnoError(RuntimeError):
@@ -95,6 +96,10 @@ def load_library():
         "dclno_set_tridiag": ([P, I], I),
         "dclno_density_matrix_poles": ([P, D, D, I, I, P], I),
         "dclno_set_mixed_engine": ([P, I], I),
+        "dclno_set_schedule": ([P, I], I),
+        "dclno_set_bucket_min": ([P, I], I),
+        "dclno_set_tuning_cache": ([P, ctypes.c_char_p], I),
+        "dclno_tuning_report": ([P, ctypes.c_char_p, ctypes.c_size_t, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -223,8 +228,30 @@ class Context:
         self._check(self.lib.dclno_set_tridiag(self.h, int(mode)))
 
     def set_mixed_engine(self, engine):
-        """Emulated tile products of the mixed path: 1 = mma.sync, 2 = tcgen05 with tensor memory."""
+        """Engine of the mixed path's K <= 32 tile products: 0 tuned, 1 mma.sync, 2 tcgen05."""
         self._check(self.lib.dclno_set_mixed_engine(self.h, int(engine)))
+
+    def set_schedule(self, mode):
+        """Grid form of the cubic kernels: 0 tuned, 1 one CTA per cluster, 2 persistent."""
+        self._check(self.lib.dclno_set_schedule(self.h, int(mode)))
+
+    def set_bucket_min(self, count):
+        """Minimum clusters per size bucket (0: twice the SM count; 1: every 64-wide bucket)."""
+        self._check(self.lib.dclno_set_bucket_min(self.h, int(count)))
+
+    def set_tuning_cache(self, path):
+        """Text cache of tuned schedules (None: off)."""
+        self._check(self.lib.dclno_set_tuning_cache(self.h, None if path is None else str(path).encode()))
+
+    def tuning_report(self):
+        """Size buckets and their schedules, as a dict."""
+        import json
+
+        need = ctypes.c_size_t()
+        self._check(self.lib.dclno_tuning_report(self.h, None, 0, ctypes.cast(ctypes.byref(need), ctypes.c_void_p)))
+        buf = ctypes.create_string_buffer(need.value)
+        self._check(self.lib.dclno_tuning_report(self.h, buf, need.value, None))
+        return json.loads(buf.value.decode())
 
     def set_autotune(self, on=True):
         """Time the QL launch shape on each batch's first eager solve (default on)."""

@@ -64,6 +64,8 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_hist);
     dfree(c->d_tune);
     dfree(c->d_kat);
+    dfree(c->d_queue);
+    sched_reset(c);
     if (c->d_pole) cudaFree(c->d_pole);
     c->d_pole = nullptr;
     c->pole_bytes = 0;
@@ -82,10 +84,15 @@ extern "C" dclno_status dclno_create(dclno_ctx** out, void* cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, c->device);
     if (e != cudaSuccess || c->nsm < 1) {
         delete c;
         return DCLNO_ERR_CUDA;
     }
+    c->gpu_name = prop.name;
+    for (char& ch : c->gpu_name)
+        if (ch == ' ' || ch == '|') ch = '_';
     *out = c;
     return DCLNO_OK;
 }
@@ -450,10 +457,13 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     // W (32 ld), P ([n][2 mc]), rotation logs (2 rot_cap per segment), for a torn problem the merge
     // matrix and its transpose (n x ld each); 256-byte aligned.  Sweep headers: it_cap ints per segment.
     auto nseg = [](const ClusterDesc& d) { return d.split ? 2LL : 1LL; };
-    // the two-stage reduction's chase reflectors (kept until the density rows are written);
-    // it also borrows the merge-matrix area as scratch, so only torn clusters qualify
-    auto q2_doubles = [](const ClusterDesc& d) {
-        return (d.split && d.n >= DCLNO_TWO_STAGE_MIN) ? (long long)DCLNO_BW * band_refl_count(d.n) : 0LL;
+    // the two-stage reduction's chase reflectors (kept until the density rows are written),
+    // laid out only when the context is in two-stage mode; it also borrows the merge-matrix
+    // area as scratch, so only torn clusters qualify
+    c->layout_two = c->tridiag_mode == 2;
+    const bool two = c->layout_two;
+    auto q2_doubles = [two](const ClusterDesc& d) {
+        return (two && d.split && d.n >= DCLNO_TWO_STAGE_MIN) ? (long long)DCLNO_BW * band_refl_count(d.n) : 0LL;
     };
     auto ws_doubles = [&](const ClusterDesc& d) {
         const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap * nseg(d) +
@@ -540,6 +550,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
                          [&](int x, int y) { return c->cl[x].n > c->cl[y].n; });
         b.mbeg = c->cl[b.id_lo].mbeg;
         b.mend = b.id_hi < N ? c->cl[b.id_hi].mbeg : (long long)c->mem.size();
+        build_buckets(c, b);
     }
     c->arena_doubles = (size_t)arena_max;
     c->resident = -1;
@@ -606,6 +617,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
         (e = cudaMalloc(&c->d_eband, sizeof(double) * N)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_scalars, sizeof(double) * 64)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_mu_work, sizeof(double) * 4096 * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_queue, sizeof(int) * 64)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_pairblk, sizeof(int) * std::max<long long>(c->pair_total, 1))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_tblk, sizeof(double) * std::max<long long>(c->tblk_total, 1))) != cudaSuccess) {
         free_clusters(c);
@@ -747,8 +759,11 @@ static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
 // mode (0) takes the form measured faster on the 1,728-atom step in each precision:
 // one-stage in FP64 (2.61 against 3.33 s per step), two-stage in the mixed path
 // (1.58 against 1.75 s).
+// mode 0 is the one-stage form in both precisions: measured faster on GB300 on every
+// workload here (the 1,728-atom step and the bcc slab, FP64 and mixed)
 static bool resolve_two_stage(const dclno_ctx* c, dclno_precision prec) {
-    return c->tridiag_mode == 2 || (c->tridiag_mode == 0 && prec == DCLNO_MIXED);
+    (void)prec;
+    return c->tridiag_mode == 2 && c->layout_two;
 }
 
 // every batch: assemble + solve (eps and q of all clusters)
@@ -898,6 +913,10 @@ extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
     if (mode < 0 || mode > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_tridiag: mode must be 0, 1 or 2");
+    if (mode == 2 && c->built && !c->layout_two)
+        return set_err(c, DCLNO_ERR_ARG,
+                       "dclno_set_tridiag: the two-stage form keeps its chase reflectors in the cluster workspace, "
+                       "laid out by dclno_build_clusters: select mode 2 before building the clusters");
     c->tridiag_mode = mode;
     return DCLNO_OK;
 }
@@ -905,8 +924,9 @@ extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
 extern "C" dclno_status dclno_set_mixed_engine(dclno_ctx* c, int engine) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
-    if (engine != 1 && engine != 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_mixed_engine: engine must be 1 or 2");
+    if (engine < 0 || engine > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_mixed_engine: engine must be 0, 1 or 2");
     c->mixed_engine = engine;
+    sched_reset(c);
     return DCLNO_OK;
 }
 

@@ -67,13 +67,10 @@ __device__ static void mirror_lower(double* A, int ld, int r0, int n, double* ti
 }
 
 template <int EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_band(const ClusterDesc* __restrict__ cls,
-                                                                                 const int* __restrict__ order,
-                                                                                 double* __restrict__ arena,
-                                                                                 int* __restrict__ status) {
+__device__ __forceinline__ void band_one(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                         int* __restrict__ status, TcState* tcsp) {
     extern __shared__ double sm[];
-    __shared__ TcState tcs;
-    const int ci = order[blockIdx.x];
+    TcState& tcs = *tcsp;
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     if (!two_stage_cluster(d)) return;
@@ -93,7 +90,6 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
     double* red = sm + band_gemm_doubles(EMU);
 
     for (int t = tid; t < n; t += blockDim.x) tauv[t] = 0.0;
-    ENGINE_BEGIN(EMU, &tcs);
     __syncthreads();
     for (int c0 = 0; c0 + BW < n; c0 += BW) {
         const int r0 = c0 + BW, m = n - r0;
@@ -234,8 +230,14 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         tile_update<true, EMU>(A22, ld, Vx, BW, W, BW, m, m, BW, 0, G, &tcs);
         tile_update<true, EMU>(A22, ld, W, BW, Vx, BW, m, m, BW, 0, G, &tcs);
     }
-    ENGINE_END(EMU, &tcs);
     if (EMU == 2 && tcs.failed && tid == 0) status[ci] = ST_TIMEOUT;
+}
+
+template <int EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_band(
+    const ClusterDesc* __restrict__ cls, const int* __restrict__ order, double* __restrict__ arena,
+    int* __restrict__ status, int nitems, int* __restrict__ queue) {
+    CUBIC_KERNEL_LOOP(EMU, band_one<EMU>(cls, order[it], arena, status, &tcs))
 }
 
 // ---------------------------------------------------------------------------
@@ -327,12 +329,11 @@ __device__ static void chase_store(double* A, int ld, int row0, int col0, int nr
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
-                                              double* __restrict__ arena, const int* __restrict__ status) {
+__device__ __forceinline__ void chase_one(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                          const int* __restrict__ status) {
     extern __shared__ double sm[];
     double* Ds = sm;
     double* Os = sm + BW * TL;
-    const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     if (!two_stage_cluster(d)) return;
@@ -406,32 +407,77 @@ __global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cl
     }
 }
 
+// one warp per cluster: a CTA per cluster, or a persistent grid on the work counter
+__global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+                                              double* __restrict__ arena, const int* __restrict__ status, int nitems,
+                                              int* __restrict__ queue) {
+    for (int it = blockIdx.x;;) {
+        if (queue) {
+            __syncwarp();
+            int v = 0;
+            if (threadIdx.x == 0) v = atomicAdd(queue, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= nitems) break;
+        chase_one(cls, order[it], arena, status);
+        if (!queue) break;
+    }
+}
+
 template <int EMU>
-static dclno_status launch_band_t(dclno_ctx* c, int N, const int* order) {
+static dclno_status launch_band_t(dclno_ctx* c, const int* order, int nitems, int persistent) {
     const size_t smb = band_smem_bytes(EMU);
     if (smb > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "band reduction: shared memory");
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_band<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-    k_band<EMU><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
+    const int grid = sched_grid(c, (const void*)k_band<EMU>, DCLNO_SOLVE_THREADS, smb, nitems, persistent != 0);
+    int* q = persistent ? c->d_queue : nullptr;
+    if (q) DCLNO_CUDA(c, cudaMemsetAsync(q, 0, sizeof(int), c->stream));
+    k_band<EMU><<<grid, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems, q);
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
 
-dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, int emu) {
-    const int N = b.oend - b.obeg;
-    if (N == 0) return DCLNO_OK;
-    const int* order = c->d_order + b.obeg;
-    {
-        ProfScope ps__(c, "k_band");
-        const dclno_status st = emu == 2 ? launch_band_t<2>(c, N, order)
-                                : emu == 1 ? launch_band_t<1>(c, N, order)
-                                           : launch_band_t<0>(c, N, order);
-        if (st != DCLNO_OK) return st;
-    }
-    {
-        ProfScope ps__(c, "k_chase");
-        const size_t sm2 = 2 * BW * TL * sizeof(double);
-        k_chase<<<N, 32, sm2, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-    }
+static dclno_status launch_chase_s(dclno_ctx* c, const int* order, int nitems, int persistent) {
+    const size_t sm2 = 2 * BW * TL * sizeof(double);
+    const int grid = sched_grid(c, (const void*)k_chase, 32, sm2, nitems, persistent != 0);
+    int* q = persistent ? c->d_queue : nullptr;
+    if (q) DCLNO_CUDA(c, cudaMemsetAsync(q, 0, sizeof(int), c->stream));
+    k_chase<<<grid, 32, sm2, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems, q);
     DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+// k_band then k_chase, per size bucket with the bucket's schedules (buckets without a
+// two-stage cluster are skipped)
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool mixed, bool tune) {
+    static const char* names[2] = {"k_band", "k_chase"};
+    for (int kernel = TK_BAND; kernel <= TK_CHASE; ++kernel) {
+        ProfScope ps__(c, names[kernel - TK_BAND]);
+        std::vector<char> use(b.buckets.size(), 0);
+        for (int k = 0; k < (int)b.buckets.size(); ++k) {
+            const Bucket& bk = b.buckets[k];
+            for (int o = bk.obeg; o < bk.oend && !use[k]; ++o) {
+                const ClusterDesc& d = c->cl[c->order[o]];
+                use[k] = d.q2_off >= 0 && d.split && d.n >= DCLNO_TWO_STAGE_MIN;
+            }
+        }
+        for (const SchedRun& r : sched_runs(c, b, kernel, mixed, tune, use)) {
+            const Sched s = r.s;
+            cudaEvent_t e0 = nullptr;
+            if (r.cand >= 0) {
+                const dclno_status st = sched_time_begin(c, &e0);
+                if (st != DCLNO_OK) return st;
+            }
+            const int* ord = c->d_order + r.obeg;
+            const int ni = r.oend - r.obeg;
+            dclno_status st;
+            if (kernel == TK_CHASE) st = launch_chase_s(c, ord, ni, s.persistent);
+            else if (s.engine == 2) st = launch_band_t<2>(c, ord, ni, s.persistent);
+            else if (s.engine == 1) st = launch_band_t<1>(c, ord, ni, s.persistent);
+            else st = launch_band_t<0>(c, ord, ni, s.persistent);
+            if (st == DCLNO_OK && r.cand >= 0) st = sched_time_end(c, b, r.k0, kernel, mixed, r.cand, e0);
+            if (st != DCLNO_OK) return st;
+        }
+    }
     return DCLNO_OK;
 }

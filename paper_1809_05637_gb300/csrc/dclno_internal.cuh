@@ -102,6 +102,49 @@ enum : int {
 // resident at once.  Arena offsets (mat_off, aux_off, cc_off, rot_off) and sweep
 // header offsets (it_off) of its clusters are relative to the batch; eig_off and
 // pair_off are global.
+// A size bucket: a contiguous range of a batch's clusters in the scheduling order
+// (decreasing n) whose dimensions round up to the same multiple of 64, buckets of
+// fewer than two CTAs per SM merged into a neighbour (a launch ends in a tail of
+// idle SMs: a bucket of a few clusters would cost the time of a whole cluster while
+// the rest of the GPU waits).  Each bucket has its own schedule; consecutive
+// buckets whose schedules agree run as one launch.
+struct Bucket {
+    int obeg = 0, oend = 0;  // positions in dclno_ctx::order
+    int nround = 0;          // dimension rounded up to 64
+    int maxn = 0;
+};
+
+// cubic kernels with a tuned schedule
+enum { TK_CHOL = 0, TK_CONG, TK_TRI, TK_BAND, TK_CHASE, TK_COUNT };
+// Schedule of one kernel on one bucket: engine of the emulated products (0 FP64 tiles,
+// 1 mma.sync, 2 tcgen05) and grid form (0 one CTA per cluster, 1 persistent CTAs on an
+// atomic work counter).  Every choice gives the same bits.
+struct Sched {
+    int engine = 0;
+    int persistent = 0;
+};
+// One launch of a tuned kernel: consecutive buckets [k0, k1) sharing schedule s, or
+// a single bucket timed for the tuner (cand >= 0).
+struct SchedRun {
+    int k0 = 0, k1 = 0;
+    int obeg = 0, oend = 0, maxn = 0;
+    Sched s;
+    int cand = -1;
+};
+struct TuneSlot {
+    int next = 0;             // next candidate to time
+    int chosen = -1;          // index into the candidates once decided
+    bool from_cache = false;
+    int default_index = -1;   // the untuned schedule among the candidates
+    std::vector<float> ms;    // timed milliseconds per cluster, per candidate (-1 = not timed)
+};
+struct TunePending {
+    std::string slot;
+    int cand;
+    cudaEvent_t e0, e1;
+    int clusters;
+};
+
 struct Batch {
     int id_lo = 0, id_hi = 0;       // clusters [id_lo, id_hi)
     int obeg = 0, oend = 0;         // the same clusters in `order` (by decreasing n)
@@ -109,6 +152,7 @@ struct Batch {
     int maxn = 0, mcmax = 1;
     long long arena_doubles = 0, iters = 0;
     int index = 0;                  // position in dclno_ctx::batches
+    std::vector<Bucket> buckets;
 };
 
 // ---------------------------------------------------------------------------
@@ -155,9 +199,20 @@ struct dclno_ctx {
     // 1 = one-stage, 2 = two-stage (for the clusters that qualify); solved_two = the form
     // the last solve used (the density pass applies the same Q)
     int tridiag_mode = 0;
+    bool layout_two = false;  // the workspace holds chase-reflector logs (built in mode 2)
     bool solved_two = false;
-    // engine of the mixed path's emulated tile products: 1 = mma.sync, 2 = tcgen05 (default)
-    int mixed_engine = 2;
+    // engine of the mixed path's K <= 32 tile products (Cholesky, congruence, one-stage
+    // tridiagonalisation): 0 = chosen per kernel and bucket by the tuner, 1 = mma.sync,
+    // 2 = tcgen05; the long-K products (band reduction, merge matrix) always use tcgen05
+    int mixed_engine = 0;
+    // schedules of the cubic kernels: 0 tuned, 1 one CTA per cluster, 2 persistent
+    int sched_force = 0;
+    int bucket_min = 0;  // minimum clusters per size bucket (0: twice the SM count)
+    std::map<std::string, TuneSlot> tune_slots;  // key: batch / bucket / kernel / precision
+    std::map<std::string, Sched> tune_cache;     // key: gpu | precision | kernel | rounded n
+    std::string tune_cache_path, gpu_name;
+    std::vector<TunePending> tune_pending;
+    int* d_queue = nullptr;                      // work counter of persistent launches
     size_t ws_limit = 0;              // workspace limit in bytes (0 = free device memory)
     // launch-shape autotuner: QL lanes per warp chosen per batch by timing (0 = not yet)
     bool autotune = true;
@@ -282,7 +337,21 @@ dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only = 
 dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only = false);
 dclno_status launch_poles(dclno_ctx* c, const Batch& b, double mu, double kT, int npoles);
 dclno_status launch_merge(dclno_ctx* c, const Batch& b);
-dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, int emu);
+dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool mixed, bool tune);
+
+// scheduler (sched.cu)
+void build_buckets(dclno_ctx* c, Batch& b);
+// the schedule of `kernel` on bucket k of batch b; *cand >= 0 when this launch is timed
+// for the tuner (then bracket it with sched_time_begin / sched_time_end)
+Sched sched_pick(dclno_ctx* c, const Batch& b, int k, int kernel, bool mixed, bool tune, int* cand);
+// the launches of `kernel` over the buckets with use[k] != 0
+std::vector<SchedRun> sched_runs(dclno_ctx* c, const Batch& b, int kernel, bool mixed, bool tune,
+                                 const std::vector<char>& use);
+dclno_status sched_time_begin(dclno_ctx* c, cudaEvent_t* e0);
+dclno_status sched_time_end(dclno_ctx* c, const Batch& b, int k, int kernel, bool mixed, int cand, cudaEvent_t e0);
+void sched_collect(dclno_ctx* c);  // after the stream is synchronised: fold timings into the slots
+void sched_reset(dclno_ctx* c);
+int sched_grid(dclno_ctx* c, const void* fn, int threads, size_t smem, int nitems, bool persistent);
 // Y <- X Y for the torn clusters of a batch: dir 0 = central strips P <- M^T P (after the
 // forward replay), dir 1 = density columns G <- M G (before the reverse replay)
 dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, int emu);

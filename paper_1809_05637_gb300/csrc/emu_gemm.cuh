@@ -236,3 +236,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // CTA (latency hiding), the emulated ones lose by it (their slicing needs registers);
 // measured on the 1728-atom step.
 #define DCLNO_CTAS_PER_SM(EMU) ((EMU) ? 2 : 3)
+
+// Work distribution of the cubic kernels.  With queue == nullptr the grid has one CTA
+// per cluster (CTA b takes cluster order[b]); otherwise the grid is persistent and every
+// CTA takes the next cluster from the atomic counter *queue until nitems are taken (no CTA
+// waits on another).  A CTA's tensor memory (EMU == 2) is set up once for all its clusters.
+#define CUBIC_KERNEL_LOOP(EMU, call)                                   \
+    __shared__ TcState tcs;                                            \
+    __shared__ int s_item;                                             \
+    ENGINE_BEGIN(EMU, &tcs);                                           \
+    for (int it = blockIdx.x;;) {                                      \
+        if (queue) {                                                   \
+            __syncthreads();                                           \
+            if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);        \
+            __syncthreads();                                           \
+            it = s_item;                                               \
+        }                                                              \
+        if (it >= nitems) break;                                       \
+        call;                                                          \
+        if (!queue) break;                                             \
+    }                                                                  \
+    ENGINE_END(EMU, &tcs);

@@ -445,7 +445,7 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
                                                  c->deferred ? c->d_scalars + 2 : nullptr, kT, with_e, c->d_eband);
         }
         DCLNO_LAUNCHED(c);
-        const dclno_status st = launch_mgemm(c, b, 1, with_e, c->solved_prec == DCLNO_MIXED ? c->mixed_engine : 0);
+        const dclno_status st = launch_mgemm(c, b, 1, with_e, c->solved_prec == DCLNO_MIXED ? 2 : 0);
         if (st != DCLNO_OK) return st;
         ProfScope ps__(c, "k_replay_rev");
         const int wmax = with_e ? 2 * b.mcmax : b.mcmax;

@@ -64,23 +64,19 @@ __device__ static void load_diag_block(const double* L, int ld, int kb, int nb, 
 // Cholesky of S^(i) in place (lower); sets ST_NOT_SPD on a non-positive pivot.
 // ---------------------------------------------------------------------------
 template <int EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_cholesky(const ClusterDesc* __restrict__ cls,
-                                                                  const int* __restrict__ order,
-                                                                  double* __restrict__ arena,
-                                                                  int* __restrict__ status) {
+__device__ __forceinline__ void cholesky_one(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                             int* __restrict__ status, TcState* tcs) {
     extern __shared__ double sm[];
     double* Dk = sm;                   // NB x DK_LD
     double* invd = sm + NB * DK_LD;    // NB
     double* G = invd + NB;             // GEMM tiles
     __shared__ int fail;
-    __shared__ TcState tcs;
-    const int ci = order[blockIdx.x];
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld;
     double* L = arena + d.mat_off + (size_t)n * ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) fail = 0;
-    ENGINE_BEGIN(EMU, &tcs);
+    __syncthreads();
     for (int kb = 0; kb < n; kb += NB) {
         const int nb = min(NB, n - kb);
         for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -112,7 +108,6 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         }
         __syncthreads();
         if (fail) {
-            ENGINE_END(EMU, &tcs);
             if (threadIdx.x == 0) status[ci] = ST_NOT_SPD;
             return;
         }
@@ -125,11 +120,18 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         const int m2 = n - kb - nb;
         if (m2 > 0) {
             double* P = L + (size_t)(kb + nb) * ld + kb;
-            tile_update<true, EMU>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G, &tcs);
+            tile_update<true, EMU>(P + nb, ld, P, ld, P, ld, m2, m2, nb, 0, G, tcs);
         }
     }
-    ENGINE_END(EMU, &tcs);
-    if (threadIdx.x == 0) status[ci] = (EMU == 2 && tcs.failed) ? ST_TIMEOUT : ST_OK;
+    if (threadIdx.x == 0) status[ci] = (EMU == 2 && tcs->failed) ? ST_TIMEOUT : ST_OK;
+}
+
+
+template <int EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_cholesky(
+    const ClusterDesc* __restrict__ cls, const int* __restrict__ order, double* __restrict__ arena,
+    int* __restrict__ status, int nitems, int* __restrict__ queue) {
+    CUBIC_KERNEL_LOOP(EMU, cholesky_one<EMU>(cls, order[it], arena, status, &tcs))
 }
 
 // ---------------------------------------------------------------------------
@@ -137,22 +139,17 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
 // Y = H L^-T (all rows), transpose, then A = Y^T L^-T restricted to the lower part.
 // ---------------------------------------------------------------------------
 template <int EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_congruence(const ClusterDesc* __restrict__ cls,
-                                                                    const int* __restrict__ order,
-                                                                    double* __restrict__ arena,
-                                                                    int* __restrict__ status) {
+__device__ __forceinline__ void congruence_one(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                               int* __restrict__ status, TcState* tcs) {
     extern __shared__ double sm[];
     double* Dk = sm;
     double* invd = sm + NB * DK_LD;
     double* G = invd + NB;
-    __shared__ TcState tcs;
-    const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     const int n = d.n, ld = d.ld;
     double* A = arena + d.mat_off;
     const double* L = A + (size_t)n * ld;
-    ENGINE_BEGIN(EMU, &tcs);
     for (int kb = 0; kb < n; kb += NB) {
         const int nb = min(NB, n - kb);
         load_diag_block(L, ld, kb, nb, Dk, invd);
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         const int n2 = n - kb - nb;
         if (n2 > 0)
             tile_update<false, EMU>(A + kb + nb, ld, A + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, n, n2, nb, 0, G,
-                                    &tcs);
+                                    tcs);
     }
     // in-place transpose
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -182,11 +179,17 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         if (m2 > 0) {
             double* C = A + (size_t)(kb + nb) * ld + kb + nb;
             tile_update<true, EMU>(C, ld, A + (size_t)(kb + nb) * ld + kb, ld, L + (size_t)(kb + nb) * ld + kb, ld, m2, m2,
-                                  nb, 0, G, &tcs);
+                                  nb, 0, G, tcs);
         }
     }
-    ENGINE_END(EMU, &tcs);
-    if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
+    if (EMU == 2 && tcs->failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
+}
+
+template <int EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_congruence(
+    const ClusterDesc* __restrict__ cls, const int* __restrict__ order, double* __restrict__ arena,
+    int* __restrict__ status, int nitems, int* __restrict__ queue) {
+    CUBIC_KERNEL_LOOP(EMU, congruence_one<EMU>(cls, order[it], arena, status, &tcs))
 }
 
 // ---------------------------------------------------------------------------
@@ -195,18 +198,12 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
 // on rows k+1.. (A[k+1][k] holds the unit element).
 // ---------------------------------------------------------------------------
 template <int EMU>
-__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_tridiag(const ClusterDesc* __restrict__ cls,
-                                                                 const int* __restrict__ order,
-                                                                 double* __restrict__ arena,
-                                                                 int* __restrict__ status,
-                                                                 int skip_two_stage) {
+__device__ __forceinline__ void tridiag_one(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                            int* __restrict__ status, int skip_two_stage, TcState* tcs) {
     extern __shared__ double sm[];
-    __shared__ TcState tcs;
-    const int ci = order[blockIdx.x];
     if (status[ci] != ST_OK) return;
     const ClusterDesc d = cls[ci];
     if (skip_two_stage && two_stage_cluster(d)) return;  // reduced by k_band + k_chase instead
-    ENGINE_BEGIN(EMU, &tcs);
     const int n = d.n, ld = d.ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double* A = arena + d.mat_off;
@@ -350,12 +347,11 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
             double* C = A + (size_t)(c0 + nb) * ld + c0 + nb;
             const double* Vp = A + (size_t)(c0 + nb) * ld + c0;
             const double* Wp = W + (size_t)(c0 + nb) * NB;
-            tile_update<true, EMU>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G, &tcs);
-            tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G, &tcs);
+            tile_update<true, EMU>(C, ld, Vp, ld, Wp, NB, m2, m2, nb, 0, G, tcs);
+            tile_update<true, EMU>(C, ld, Wp, NB, Vp, ld, m2, m2, nb, 0, G, tcs);
         }
     }
-    ENGINE_END(EMU, &tcs);
-    if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
+    if (EMU == 2 && tcs->failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
     // Cuppen's tear: T = diag(T1, T2) + |beta| v v^T with beta = e[k-1], v = e_{k-1} + sign(beta) e_k;
     // T1 and T2 (d[k-1], d[k] lowered by |beta|) are solved as separate QL segments and merged
     // afterwards (k_merge).  beta is kept in W[n].
@@ -368,6 +364,13 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k
         dv[k - 1] -= fabs(beta);
         dv[k] -= fabs(beta);
     }
+}
+
+template <int EMU>
+__global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, DCLNO_CTAS_PER_SM(EMU)) k_tridiag(
+    const ClusterDesc* __restrict__ cls, const int* __restrict__ order, double* __restrict__ arena,
+    int* __restrict__ status, int skip_two_stage, int nitems, int* __restrict__ queue) {
+    CUBIC_KERNEL_LOOP(EMU, tridiag_one<EMU>(cls, order[it], arena, status, skip_two_stage, &tcs))
 }
 
 // ---------------------------------------------------------------------------
@@ -924,45 +927,85 @@ static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int 
     return DCLNO_OK;
 }
 
+// one cubic kernel over the clusters order[0 .. nitems) with a schedule
 template <int EMU>
-static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only) {
+static dclno_status launch_cubic_t(dclno_ctx* c, int kernel, const int* order, int nitems, size_t smem, int persistent,
+                                   int two) {
+    const void* fn = kernel == TK_CHOL ? (const void*)k_cholesky<EMU>
+                     : kernel == TK_CONG ? (const void*)k_congruence<EMU>
+                                         : (const void*)k_tridiag<EMU>;
+    DCLNO_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = sched_grid(c, fn, DCLNO_SOLVE_THREADS, smem, nitems, persistent != 0);
+    int* q = persistent ? c->d_queue : nullptr;
+    if (q) DCLNO_CUDA(c, cudaMemsetAsync(q, 0, sizeof(int), c->stream));
+    if (kernel == TK_CHOL)
+        k_cholesky<EMU><<<grid, DCLNO_SOLVE_THREADS, smem, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems, q);
+    else if (kernel == TK_CONG)
+        k_congruence<EMU><<<grid, DCLNO_SOLVE_THREADS, smem, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems,
+                                                                         q);
+    else
+        k_tridiag<EMU><<<grid, DCLNO_SOLVE_THREADS, smem, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, two,
+                                                                      nitems, q);
+    DCLNO_LAUNCHED(c);
+    return DCLNO_OK;
+}
+
+// shared memory of a cubic kernel with engine e on clusters of dimension <= maxn
+static size_t cubic_smem(int kernel, int e, int maxn) {
+    const size_t g = (ENGINE_SMEM_BYTES(e) + 7) / 8;
+    if (kernel == TK_TRI) return std::max(g, (size_t)(2 + DCLNO_SOLVE_THREADS / 32) * maxn + 32 + 2 * NB) * sizeof(double);
+    return (size_t)(NB * DK_LD + NB + g) * sizeof(double);
+}
+
+static bool bucket_all_two_stage(const dclno_ctx* c, const Bucket& k) {
+    for (int o = k.obeg; o < k.oend; ++o) {
+        const ClusterDesc& d = c->cl[c->order[o]];
+        if (!(d.q2_off >= 0 && d.split && d.n >= DCLNO_TWO_STAGE_MIN)) return false;
+    }
+    return true;
+}
+
+static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only, bool mixed) {
     const int N = b.oend - b.obeg;  // clusters of the batch
     if (N == 0) return DCLNO_OK;
     const int maxn = b.maxn;
     const int* order = c->d_order + b.obeg;
     const int nw = DCLNO_SOLVE_THREADS / 32;
-    const size_t gemm_doubles = (ENGINE_SMEM_BYTES(EMU) + 7) / 8;
-    size_t sm_chol = (size_t)(NB * DK_LD + NB + gemm_doubles) * sizeof(double);
-    size_t sm_tri = std::max(gemm_doubles, (size_t)(2 + nw) * maxn + 32 + 2 * NB) * sizeof(double);
     // strip rows per shared-memory chunk of k_apply_q_rows: at most DCLNO_RPW per warp, within 200 KB
     const int rch = (int)std::min<long long>(std::min(2 * b.mcmax, DCLNO_RPW * nw),
                                              (200LL * 1024 / 8 - DCLNO_MAX_M * DCLNO_MAX_M) / std::max(maxn, 1));
     size_t sm_q = (size_t)(DCLNO_MAX_M * DCLNO_MAX_M + (size_t)std::max(rch, 1) * maxn) * sizeof(double);
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_cholesky<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_congruence<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_chol));
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_tridiag<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tri));
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_apply_q_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_q));
-    if (sm_tri > 227 * 1024 || sm_q > 227 * 1024 || rch < 1)
+    if (cubic_smem(TK_TRI, 0, maxn) > 227 * 1024 || sm_q > 227 * 1024 || rch < 1)
         return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the FP64 solver (n = " + std::to_string(maxn) + ")");
-
-    {
-        ProfScope ps__(c, "k_cholesky");
-        k_cholesky<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-    }
-    DCLNO_LAUNCHED(c);
-    {
-        ProfScope ps__(c, "k_congruence");
-        k_congruence<EMU><<<N, DCLNO_SOLVE_THREADS, sm_chol, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-    }
-    DCLNO_LAUNCHED(c);
     const int two = c->solved_two ? 1 : 0;
-    {
-        ProfScope ps__(c, "k_tridiag");
-        k_tridiag<EMU><<<N, DCLNO_SOLVE_THREADS, sm_tri, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, two);
+    const bool tune = !reduce_only;
+    static const char* names[3] = {"k_cholesky", "k_congruence", "k_tridiag"};
+    for (int kernel = TK_CHOL; kernel <= TK_TRI; ++kernel) {
+        ProfScope ps__(c, names[kernel]);
+        std::vector<char> use(b.buckets.size(), 1);
+        for (int k = 0; k < (int)b.buckets.size(); ++k)  // k_band + k_chase instead
+            if (kernel == TK_TRI && two && bucket_all_two_stage(c, b.buckets[k])) use[k] = 0;
+        for (const SchedRun& r : sched_runs(c, b, kernel, mixed, tune, use)) {
+            const Sched s = r.s;
+            cudaEvent_t e0 = nullptr;
+            if (r.cand >= 0) {
+                const dclno_status st = sched_time_begin(c, &e0);
+                if (st != DCLNO_OK) return st;
+            }
+            const size_t smem = cubic_smem(kernel, s.engine, r.maxn);
+            const int* ord = c->d_order + r.obeg;
+            const int ni = r.oend - r.obeg;
+            dclno_status st;
+            if (s.engine == 2) st = launch_cubic_t<2>(c, kernel, ord, ni, smem, s.persistent, two);
+            else if (s.engine == 1) st = launch_cubic_t<1>(c, kernel, ord, ni, smem, s.persistent, two);
+            else st = launch_cubic_t<0>(c, kernel, ord, ni, smem, s.persistent, two);
+            if (st == DCLNO_OK && r.cand >= 0) st = sched_time_end(c, b, r.k0, kernel, mixed, r.cand, e0);
+            if (st != DCLNO_OK) return st;
+        }
     }
-    DCLNO_LAUNCHED(c);
     if (two) {
-        const dclno_status st = launch_two_stage(c, b, EMU);
+        const dclno_status st = launch_two_stage(c, b, mixed, tune);
         if (st != DCLNO_OK) return st;
     }
     if (reduce_only) {
@@ -1009,7 +1052,7 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only)
     }
     DCLNO_LAUNCHED(c);
     {
-        const dclno_status st = launch_mgemm(c, b, 0, 0, EMU);
+        const dclno_status st = launch_mgemm(c, b, 0, 0, mixed ? 2 : 0);
         if (st != DCLNO_OK) return st;
     }
     {
@@ -1024,6 +1067,7 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only)
     DCLNO_CUDA(c, cudaMemcpyAsync(st.data(), c->d_status + b.id_lo, sizeof(int) * nid, cudaMemcpyDeviceToHost,
                                   c->stream));
     DCLNO_CUDA(c, cudaStreamSynchronize(c->stream));
+    sched_collect(c);
     for (int k = 0; k < nid; ++k) {
         const int i = b.id_lo + k;
         if (st[k] == ST_NOT_SPD)
@@ -1040,8 +1084,8 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only)
 }
 
 dclno_status launch_solve_fp64(dclno_ctx* c, const Batch& b, bool reduce_only) {
-    return launch_solve<0>(c, b, reduce_only);
+    return launch_solve(c, b, reduce_only, false);
 }
 dclno_status launch_solve_mixed(dclno_ctx* c, const Batch& b, bool reduce_only) {
-    return c->mixed_engine == 1 ? launch_solve<1>(c, b, reduce_only) : launch_solve<2>(c, b, reduce_only);
+    return launch_solve(c, b, reduce_only, true);
 }

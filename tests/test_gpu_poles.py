@@ -70,8 +70,7 @@ def test_poles_match_spectral_rows(lattice7, prec, mode):
     s = lattice7
     rho_in = T.synthetic_density(s, seed=3)
     R = to_dev(rho_in)
-    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
-    ctx.set_tridiag(mode)
+    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=mode)
     dims = ctx.cluster_info()[0]
     assert dims.min() >= 128
     out = torch.zeros(len(s.S), dtype=torch.float64, device="cuda:0")

@@ -18,7 +18,7 @@ import oracle as O  # noqa: E402
 import tbsystems as T  # noqa: E402
 from gpu_helpers import (check_sampled_clusters, eps_tol, gpu_context, oracle_sample, rho_row_tol,  # noqa: E402
                          spectral_moments, state_tol, to_dev)
-from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED  # noqa: E402
+from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, DclnoError  # noqa: E402
 
 TWO_STAGE_MIN = 128
 
@@ -38,8 +38,7 @@ def test_two_stage_lno_step_cfg1(cfg1, cfg1_dc0, prec):
     dims = np.array([r.cluster.dim for r in res.values()])
     assert dims.max() >= TWO_STAGE_MIN and np.any(dims % 32 != 0)
 
-    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
-    ctx.set_tridiag(2)
+    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=2)
     ctx.set_profiling(True)
     ctx.compute_lnos(to_dev(rho0))
     ctx.solve_clusters(prec)
@@ -77,7 +76,7 @@ def test_two_stage_full_size_clusters(periodic512, prec):
     rho_in = T.synthetic_density(s, seed=11)
     sample = [0, 255, 511]
     _, V, res = oracle_sample(s, rho_in, sample)
-    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
+    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=2)
     out = torch.zeros(len(s.S), dtype=torch.float64, device="cuda:0")
     R = to_dev(rho_in)
     per = {}
@@ -102,21 +101,37 @@ def test_two_stage_batches_match_single_workspace(periodic512):
     R = to_dev(T.synthetic_density(s, seed=11))
     outs = []
     for limit in (0, None):
-        ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno) if limit == 0 else None
+        ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=2) if limit == 0 else None
         if ctx is None:
             from paper_1809_05637_gb300 import Context
-            probe = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
+            probe = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=2)
             ws1 = probe.batch_info()[1]
             probe.close()
             ctx = Context()
+            ctx.set_tridiag(2)
             ctx.set_workspace_limit(ws1 // 3 + (1 << 20))
             ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, to_dev(s.H),
                                to_dev(s.S), s.r_core, s.r_lno, s.k_lno)
             assert ctx.batch_info()[0] >= 3
-        ctx.set_tridiag(2)
         out = torch.zeros_like(R)
         mu, n, e = ctx.step(R, out, s.n_electrons, s.kT, precision=DCLNO_MIXED)
         outs.append((mu, e, out.cpu().numpy()))
         ctx.close()
     assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1]
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_two_stage_needs_its_layout(cfg1):
+    """Mode 2 selected after a build without the chase-reflector log is refused, the
+    context keeps solving in the one-stage form; modes 0 and 1 switch freely."""
+    s = cfg1
+    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
+    with pytest.raises(DclnoError, match="before building"):
+        ctx.set_tridiag(2)
+    ctx.set_tridiag(1)
+    ctx.set_tridiag(0)
+    ctx.set_profiling(True)
+    out = torch.zeros(len(s.S), dtype=torch.float64, device="cuda:0")
+    ctx.step(to_dev(T.synthetic_density(s, seed=3)), out, s.n_electrons, s.kT)
+    assert _ran(ctx, "k_band") == 0 and _ran(ctx, "k_tridiag") >= 1
+    ctx.close()

@@ -1,5 +1,6 @@
 """The 1,728-atom gapped rock-salt workload at full size, in the benchmark's launch
-configuration (all clusters in one batch), in FP64 and in the mixed-precision form.
+configuration (all clusters in one batch), in FP64 and in the mixed-precision form,
+the latter also with the two-stage tridiagonalisation (dense -> band -> tridiagonal).
 
 Sampled clusters are recomputed by the oracle one by one from the same seeded
 input density and compared with both GPU solves (eigenvalues within each
@@ -19,21 +20,26 @@ from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED  # noqa: E402
 
 SAMPLE = [0, 777, 1727]
 MU_TEST = -0.25  # a fixed chemical potential for element-wise rho comparison
-PRECISIONS = {"fp64": DCLNO_FP64, "mixed": DCLNO_MIXED}
+# name: (precision, tridiagonalisation form)
+PRECISIONS = {"fp64": (DCLNO_FP64, 0), "mixed": (DCLNO_MIXED, 0), "mixed_two": (DCLNO_MIXED, 2)}
 
 
 @pytest.fixture(scope="module")
 def run():
     s = T.make_system(2)
     rho_in = T.synthetic_density(s, seed=11)
-    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno)
+    ctx = gpu_context(s, s.r_core, s.r_lno, s.k_lno, tridiag=2)
     ctx.compute_lnos(to_dev(rho_in))
     lnos = ctx.lnos()
     dims = ctx.cluster_info()[0]
     out = torch.zeros(len(s.S), dtype=torch.float64, device="cuda:0")
     per = {}
-    for name, prec in PRECISIONS.items():
+    for name, (prec, form) in PRECISIONS.items():
+        ctx.set_tridiag(form)
+        ctx.set_profiling(True)
         ctx.solve_clusters(prec)
+        assert (ctx.kernel_time("k_band")[1] > 0) == (form == 2)
+        ctx.set_profiling(False)
         mu, n = ctx.find_mu(s.n_electrons, s.kT)
         e_band = ctx.density_matrix(mu, s.kT, out)
         rho_mu = out.cpu().numpy()
@@ -77,6 +83,7 @@ def test_sampled_clusters_match_oracle(run, oracle_res, prec):
     _, V, res = oracle_res
     r = run[prec]
     row_tol = (lambda rr, big: 1e-9 + 4e-9 * big) if prec == "fp64" else rho_row_tol
+    # (the two-stage form's extra reflectors keep it within the same bounds)
     worst_eps, worst_rho = check_sampled_clusters(
         s, V, res, r["spec"], r["rho_test"], MU_TEST, row_tol, np.linspace(-0.9, 0.1, 11))
     print(f"{prec}: eigenvalues {worst_eps:.3g} of the first-order bound, rho rows {worst_rho:.3g} of the row max")
@@ -94,9 +101,10 @@ def test_invariants_at_full_size(run, prec):
     assert abs(2 * float(np.dot(rho, s.H)) - r["e_band"]) < 1e-8 * abs(r["e_band"])
 
 
-def test_mixed_band_energy_target(run):
+@pytest.mark.parametrize("name", ["mixed", "mixed_two"])
+def test_mixed_band_energy_target(run, name):
     """The mixed form's band energy per atom within 1e-6 Ha of the FP64 form."""
     s = run["s"]
-    d = abs(run["mixed"]["e_band"] - run["fp64"]["e_band"]) / s.natoms
-    print(f"mixed vs fp64: E_band/atom {d:.3e} Ha, mu {abs(run['mixed']['mu'] - run['fp64']['mu']):.3e}")
+    d = abs(run[name]["e_band"] - run["fp64"]["e_band"]) / s.natoms
+    print(f"{name} vs fp64: E_band/atom {d:.3e} Ha, mu {abs(run[name]['mu'] - run['fp64']['mu']):.3e}")
     assert d <= 1e-6

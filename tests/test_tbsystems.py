@@ -124,3 +124,62 @@ def test_streamed_rows_equal_full_build():
     for i in (3, 250):
         o, e = int(b.blk_off[b.row_ptr[i]]), int(b.blk_off[b.row_ptr[i + 1]])
         assert np.array_equal(b.S[o:e], a.S[o:e]) and np.array_equal(b.H[o:e], a.H[o:e])
+
+
+def _rsa_brute(n, L, dmin, rng, batch=65536):
+    """Random sequential addition one candidate at a time (the definition): a candidate
+    is kept when no kept point lies within dmin (minimum image) and its grid cell
+    (width >= dmin / sqrt(3)) holds no kept point."""
+    g = max(1, int(L / (dmin / np.sqrt(3.0))))
+    cw = L / g
+    pts, cells = [], set()
+    while len(pts) < n:
+        cand = rng.uniform(0.0, L, size=(batch, 3))
+        for x in cand:
+            c = tuple(np.minimum((x // cw).astype(np.int64), g - 1))
+            if c in cells:
+                continue
+            if pts:
+                d = np.asarray(pts) - x
+                d -= L * np.round(d / L)
+                if np.min(np.einsum("kd,kd->k", d, d)) < dmin * dmin:
+                    continue
+            pts.append(x)
+            cells.add(c)
+            if len(pts) == n:
+                break
+    return np.asarray(pts)
+
+
+@pytest.mark.parametrize("n,L", [(150, 40.0), (120, 22.0)])
+def test_rsa_matches_sequential_definition(n, L):
+    """The batched packing (KD-tree screen, conflict graph within a batch) places the
+    same points, in the same order, as the one-candidate-at-a-time definition; the
+    second case is dense enough to need several batches and in-batch conflicts."""
+    fast = T._rsa(n, L, 3.8, np.random.default_rng(5), batch=4096)
+    ref = _rsa_brute(n, L, 3.8, np.random.default_rng(5), batch=4096)
+    np.testing.assert_array_equal(fast, ref)
+
+
+def test_streamed_rows_match_full_build():
+    """The tabled, threaded row generator of streamed systems gives the structure and
+    the values of the per-block construction (a ragged-path BsrRows), and the
+    synthetic density rows agree with synthetic_density."""
+    s = T.make_system(5, n_atoms=300)
+    st = T.make_system_streamed(5, n_atoms=300)
+    for a in ("row_ptr", "col", "shift", "blk_off"):
+        np.testing.assert_array_equal(getattr(st, a), getattr(s, a))
+    Sv, Hv, Rv = np.empty(len(s.S)), np.empty(len(s.S)), np.empty(len(s.S))
+    for i0, i1, o0, sv, hv, rv in T.row_chunks(st, 37, workers=3, density_seed=11):
+        Sv[o0:o0 + len(sv)], Hv[o0:o0 + len(hv)], Rv[o0:o0 + len(rv)] = sv, hv, rv
+    np.testing.assert_array_equal(Sv, s.S)
+    np.testing.assert_array_equal(Hv, s.H)
+    np.testing.assert_array_equal(Rv, T.synthetic_density(s, seed=11))
+    ragged = T.BsrRows(st.pos, st.cell, st.pbc, st.exps, st.onsite)
+    ragged.tabled = False
+    for i0, i1 in ((0, 3), (150, 152), (297, 300)):
+        for (c1, sh1, s1, h1), (c2, sh2, s2, h2) in zip(ragged.rows(i0, i1), st.source.rows(i0, i1)):
+            np.testing.assert_array_equal(c1, c2)
+            np.testing.assert_array_equal(sh1, sh2)
+            np.testing.assert_allclose(s1, s2, rtol=1e-14, atol=0)
+            np.testing.assert_allclose(h1, h2, rtol=1e-14, atol=0)
