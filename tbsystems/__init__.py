@@ -36,6 +36,7 @@ Conventions
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 
 import numpy as np
@@ -128,7 +129,14 @@ def _image_shifts(cell: np.ndarray, pbc: np.ndarray, rcut: float) -> np.ndarray:
 
 class BsrRows:
     """Rows of the block-sparse S and H on demand: (i, j, R) pairs with a kept
-    overlap entry, Wolfsberg-Helmholz H.  One KD-tree over the periodic images."""
+    overlap entry, Wolfsberg-Helmholz H.  One KD-tree over the periodic images.
+
+    When every atom carries the same exponents (all workloads here) the blocks of a
+    row range are computed in one vectorised pass from per-exponent-pair tables
+    (prefactor and decay of the Gaussian overlap), and the structure alone (which
+    pairs are kept) needs only the block's largest entry, the most diffuse exponent
+    with itself, except in a thin shell around the cutoff where the whole block is
+    evaluated.  Other bases take a per-block loop."""
 
     def __init__(self, pos, cell, pbc, exps, onsite, drop_tol=DROP_TOL):
         from scipy.spatial import cKDTree
@@ -141,64 +149,124 @@ class BsrRows:
         self.shifts = _image_shifts(cell, pbc, self.rcut)
         self.imgpos = (pos[None, :, :] + (self.shifts @ cell)[:, None, :]).reshape(-1, 3)
         self.tree = cKDTree(self.imgpos)
-        self.uniform = bool(np.all(self.norb == self.norb[0]))
+        e0 = np.asarray(exps[0], dtype=np.float64)
+        self.tabled = all(len(e) == len(e0) and np.array_equal(e, e0) for e in exps)
+        if self.tabled:
+            a, b = e0[:, None], e0[None, :]
+            p = a + b
+            self.pref = (2.0 * np.sqrt(a * b) / p) ** 1.5  # gaussian_overlap's factors, per exponent pair
+            self.decay = a * b / p
+            k = int(np.argmin(e0))
+            self.kmin = k  # the block's largest entry at every distance: pref 1, slowest decay
+            self.onsite_tab = np.stack([np.asarray(h, dtype=np.float64) for h in onsite])
+
+    def _candidates(self, i0, i1):
+        """(row, col, shift, r2) of the images within the cutoff of rows i0 .. i1-1,
+        sorted by (row, col, shift)."""
+        lists = self.tree.query_ball_point(self.pos[i0:i1], self.rcut * (1 + 1e-12) + 1e-9)
+        cnt = np.fromiter((len(x) for x in lists), dtype=np.int64, count=i1 - i0)
+        idx = np.fromiter(itertools.chain.from_iterable(lists), dtype=np.int64, count=int(cnt.sum()))
+        row = np.repeat(np.arange(i0, i1, dtype=np.int64), cnt)
+        j = idx % self.n
+        sh = self.shifts[idx // self.n]
+        d = self.imgpos[idx] - self.pos[row]
+        r2 = np.einsum("kd,kd->k", d, d)
+        order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], j, row))
+        return row[order], j[order], sh[order], r2[order]
+
+    def _blocks(self, row, j, sh, r2):
+        """S and H blocks (K, M, M) of tabled pairs, entries below drop_tol zeroed."""
+        sblk = self.pref[None, :, :] * np.exp(-self.decay[None, :, :] * r2[:, None, None])
+        sblk[sblk < self.drop_tol] = 0.0
+        ea = self.onsite_tab[row][:, :, None]
+        eb = self.onsite_tab[j][:, None, :]
+        self_mask = (j == row) & np.all(sh == 0, axis=1)
+        kfac = np.where(self_mask, 1.0, WH_K)[:, None, None]
+        hblk = kfac * sblk * 0.5 * (ea + eb)
+        return sblk, hblk
+
+    def _kept(self, row, j, sh, r2):
+        """Which candidate pairs keep a block: some entry >= drop_tol.  The diffuse
+        entry decides away from the cutoff (>= 2 tol: kept; < tol / 2: every entry is
+        below tol); in between the whole block is evaluated."""
+        k = self.kmin
+        smax = self.pref[k, k] * np.exp(-self.decay[k, k] * r2)
+        keep = smax >= 2.0 * self.drop_tol
+        edge = np.nonzero(~keep & (smax >= 0.5 * self.drop_tol))[0]
+        if len(edge):
+            sblk, _ = self._blocks(row[edge], j[edge], sh[edge], r2[edge])
+            keep[edge] = np.any(sblk != 0.0, axis=(1, 2))
+        return keep
 
     def rows(self, i0, i1):
         """[(col, shift, S, H)] of rows i0 .. i1-1, blocks sorted by (col, shift)."""
+        if self.tabled:
+            row, j, sh, r2 = self._candidates(i0, i1)
+            sblk, hblk = self._blocks(row, j, sh, r2)
+            keep = np.any(sblk != 0.0, axis=(1, 2))
+            row, j, sh, sblk, hblk = row[keep], j[keep], sh[keep], sblk[keep], hblk[keep]
+            bounds = np.searchsorted(row, np.arange(i0, i1 + 1))
+            return [(j[b0:b1].astype(np.int32), sh[b0:b1].astype(np.int8), sblk[b0:b1].reshape(-1),
+                     hblk[b0:b1].reshape(-1)) for b0, b1 in zip(bounds[:-1], bounds[1:])]
         n, pos, exps, onsite, drop_tol = self.n, self.pos, self.exps, self.onsite, self.drop_tol
         out = []
         lists = self.tree.query_ball_point(pos[i0:i1], self.rcut * (1 + 1e-12) + 1e-9)
-        for ii, lst in enumerate(lists):
+        for ii, lst in enumerate(lists):  # ragged basis: per-block loop
             i = i0 + ii
             idx = np.asarray(sorted(lst), dtype=np.int64)
             j = idx % n
             sh = self.shifts[idx // n]
             d = self.imgpos[idx] - pos[i]
             r2 = np.einsum("kd,kd->k", d, d)
-            if self.uniform:
-                a = exps[i][None, :, None]
-                b = np.stack([exps[jj] for jj in j])[:, None, :]
-                sblk = gaussian_overlap(a, b, r2[:, None, None])
-                sblk[sblk < drop_tol] = 0.0
-                ea = onsite[i][None, :, None]
-                eb = np.stack([onsite[jj] for jj in j])[:, None, :]
-                self_mask = (j == i) & np.all(sh == 0, axis=1)
-                kfac = np.where(self_mask, 1.0, WH_K)[:, None, None]
-                hblk = kfac * sblk * 0.5 * (ea + eb)
-                keep = np.any(sblk != 0.0, axis=(1, 2))
-                order = np.lexsort((sh[:, 2], sh[:, 1], sh[:, 0], j))
-                order = order[keep[order]]
-                out.append((j[order].astype(np.int32), sh[order].astype(np.int8), sblk[order].reshape(-1),
-                            hblk[order].reshape(-1)))
-            else:  # ragged basis: per-block loop
-                blocks = []
-                for k in range(len(idx)):
-                    jj = int(j[k])
-                    a = exps[i][:, None]
-                    b = exps[jj][None, :]
-                    sb = gaussian_overlap(a, b, r2[k])
-                    sb[sb < drop_tol] = 0.0
-                    if not np.any(sb != 0.0):
-                        continue
-                    kf = 1.0 if (jj == i and not np.any(sh[k])) else WH_K
-                    hb = kf * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
-                    blocks.append((jj, tuple(int(x) for x in sh[k]), sb, hb))
-                blocks.sort(key=lambda t: (t[0],) + t[1])
-                out.append((np.array([t[0] for t in blocks], dtype=np.int32),
-                            np.array([t[1] for t in blocks], dtype=np.int8).reshape(-1, 3),
-                            np.concatenate([t[2].reshape(-1) for t in blocks]),
-                            np.concatenate([t[3].reshape(-1) for t in blocks])))
+            blocks = []
+            for k in range(len(idx)):
+                jj = int(j[k])
+                sb = gaussian_overlap(exps[i][:, None], exps[jj][None, :], r2[k])
+                sb[sb < drop_tol] = 0.0
+                if not np.any(sb != 0.0):
+                    continue
+                kf = 1.0 if (jj == i and not np.any(sh[k])) else WH_K
+                hb = kf * sb * 0.5 * (onsite[i][:, None] + onsite[jj][None, :])
+                blocks.append((jj, tuple(int(x) for x in sh[k]), sb, hb))
+            blocks.sort(key=lambda t: (t[0],) + t[1])
+            out.append((np.array([t[0] for t in blocks], dtype=np.int32),
+                        np.array([t[1] for t in blocks], dtype=np.int8).reshape(-1, 3),
+                        np.concatenate([t[2].reshape(-1) for t in blocks]),
+                        np.concatenate([t[3].reshape(-1) for t in blocks])))
         return out
 
-    def structure(self, chunk=256):
-        """row_ptr, col, shift, blk_off of all rows (the values are not kept)."""
-        cols, shs, ns = [], [], []
-        for i0 in range(0, self.n, chunk):
-            for c, sh, _, _ in self.rows(i0, min(self.n, i0 + chunk)):
-                cols.append(c)
-                shs.append(sh)
-                ns.append(len(c))
+    def _structure_chunk(self, i0, i1):
+        if not self.tabled:
+            rows = self.rows(i0, i1)
+            return [len(r[0]) for r in rows], [r[0] for r in rows], [r[1] for r in rows]
+        row, j, sh, r2 = self._candidates(i0, i1)
+        keep = self._kept(row, j, sh, r2)
+        row, j, sh = row[keep], j[keep], sh[keep]
+        ns = np.bincount(row - i0, minlength=i1 - i0)
+        return list(ns), [j.astype(np.int32)], [sh.astype(np.int8)]
+
+    def structure(self, chunk=256, workers=None):
+        """row_ptr, col, shift, blk_off of all rows (the values are not kept); row
+        ranges in parallel threads."""
+        spans = [(i0, min(self.n, i0 + chunk)) for i0 in range(0, self.n, chunk)]
+        with _pool(workers) as ex:
+            parts = list(ex.map(lambda s: self._structure_chunk(*s), spans))
+        ns = [x for p in parts for x in p[0]]
+        cols = [c for p in parts for c in p[1]]
+        shs = [s for p in parts for s in p[2]]
         return _layout(self.norb, ns, cols, shs)
+
+
+def _nworkers(workers=None):
+    import os
+
+    return workers or min(32, os.cpu_count() or 1)
+
+
+def _pool(workers=None):
+    import concurrent.futures
+
+    return concurrent.futures.ThreadPoolExecutor(max_workers=_nworkers(workers))
 
 
 def _layout(norb, ns, cols, shs):
@@ -263,9 +331,47 @@ def make_system_streamed(cfg: int, seed: int | None = None, n_atoms: int | None 
 
 def row_values(system: System, i0: int, i1: int):
     """(offset, S, H) of the blocks of rows i0 .. i1-1 of a streamed system."""
-    rows = system.source.rows(i0, i1)
+    src = system.source
+    if src.tabled:
+        row, j, sh, r2 = src._candidates(i0, i1)
+        sblk, hblk = src._blocks(row, j, sh, r2)
+        keep = np.any(sblk != 0.0, axis=(1, 2))
+        sv, hv = sblk[keep].reshape(-1), hblk[keep].reshape(-1)
+    else:
+        rows = src.rows(i0, i1)
+        sv, hv = np.concatenate([r[2] for r in rows]), np.concatenate([r[3] for r in rows])
     o0 = int(system.blk_off[system.row_ptr[i0]])
-    return o0, np.concatenate([r[2] for r in rows]), np.concatenate([r[3] for r in rows])
+    o1 = int(system.blk_off[system.row_ptr[i1]]) if i1 < system.natoms else len(system.S)
+    if len(sv) != o1 - o0:
+        raise RuntimeError(f"rows {i0}..{i1}: {len(sv)} values against {o1 - o0} in the structure")
+    return o0, sv, hv
+
+
+def row_chunks(system: System, chunk: int = 128, workers=None, density_seed=None):
+    """(i0, i1, offset, S, H[, rho]) of consecutive row ranges of a streamed system,
+    in order, computed by a pool of threads a few ranges ahead of the consumer; with
+    density_seed the synthetic_density blocks of the same rows come along."""
+    import collections
+
+    def job(i0):
+        i1 = min(system.natoms, i0 + chunk)
+        o0, sv, hv = row_values(system, i0, i1)
+        if density_seed is None:
+            return i0, i1, o0, sv, hv
+        rv = np.empty(len(sv))
+        synthetic_density_rows(system, i0, i1, rv, seed=density_seed, base=o0)
+        return i0, i1, o0, sv, hv, rv
+
+    with _pool(workers) as ex:
+        depth = 2 * _nworkers(workers)
+        starts = iter(range(0, system.natoms, chunk))
+        pending = collections.deque(ex.submit(job, i0) for i0 in itertools.islice(starts, depth))
+        while pending:
+            res = pending.popleft().result()
+            nxt = next(starts, None)
+            if nxt is not None:
+                pending.append(ex.submit(job, nxt))
+            yield res
 
 
 def fill_rows(system: System, atoms) -> None:
@@ -368,11 +474,16 @@ def assemble_system(name, pos, cell, pbc, species, exps, onsite, n_electrons, kT
 def _rsa(n, L, dmin, rng, batch=65536):
     """Random sequential addition in a periodic cube with a minimum distance.
 
-    Candidates are drawn uniformly in batches; a candidate is kept when no point
-    already placed (or kept earlier in the same batch) lies within dmin under the
-    minimum-image convention.  A cell grid of width <= dmin / sqrt(3) holds at most
-    one point per cell, so every conflict lies within two cells of the candidate.
+    Candidates are drawn uniformly in batches and considered in draw order; a
+    candidate is kept when no point kept before it lies within dmin under the
+    minimum-image convention and its cell of a grid of width >= dmin / sqrt(3) holds
+    no kept point (one point per cell, so every conflict lies within
+    ceil(dmin / width) cells).  Within a batch, the candidates free of the points of
+    earlier batches are resolved in draw order over their conflict graph (pairs
+    closer than dmin or sharing a cell).
     """
+    from scipy.spatial import cKDTree
+
     g = max(1, int(L / (dmin / np.sqrt(3.0))))
     cw = L / g
     reach = int(np.ceil(dmin / cw))
@@ -388,24 +499,48 @@ def _rsa(n, L, dmin, rng, batch=65536):
         cand = rng.uniform(0.0, L, size=(batch, 3))
         tries += batch
         cell = np.minimum((cand // cw).astype(np.int64), g - 1)
-        nb = (cell[:, None, :] + off[None, :, :]) % g
-        who = occ[nb[..., 0], nb[..., 1], nb[..., 2]]
-        d = pts[np.maximum(who, 0)] - cand[:, None, :]
-        d -= L * np.round(d / L)
-        bad = (who >= 0) & (np.einsum("bkd,bkd->bk", d, d) < dmin * dmin)
-        for b in np.nonzero(~bad.any(axis=1))[0]:
-            c = cell[b]
-            if occ[c[0], c[1], c[2]] >= 0:
+        ok = occ[cell[:, 0], cell[:, 1], cell[:, 2]] < 0
+        if k:
+            # nearest earlier point by a KD-tree; the exact minimum-image test near dmin
+            near = cKDTree(np.mod(pts[:k], L), boxsize=L).query(np.mod(cand, L), k=1,
+                                                                   distance_upper_bound=dmin * (1 + 1e-6))[0]
+            ok &= near >= dmin * (1 - 1e-6)
+            edge = np.nonzero(ok & (near < dmin * (1 + 1e-6)))[0]
+            if len(edge):
+                nb = (cell[edge][:, None, :] + off[None, :, :]) % g
+                who = occ[nb[..., 0], nb[..., 1], nb[..., 2]]
+                d = pts[np.maximum(who, 0)] - cand[edge][:, None, :]
+                d -= L * np.round(d / L)
+                ok[edge] = ~((who >= 0) & (np.einsum("bkd,bkd->bk", d, d) < dmin * dmin)).any(axis=1)
+        free = np.nonzero(ok)[0]
+        if len(free) == 0:
+            continue
+        # conflicts among the free candidates: same cell, or closer than dmin
+        fp = cand[free]
+        pairs = cKDTree(np.mod(fp, L), boxsize=L).query_pairs(max(dmin, cw * np.sqrt(3.0)) * (1 + 1e-9),
+                                                              output_type="ndarray")
+        if len(pairs):
+            pairs.sort(axis=1)  # (earlier, later) in draw order
+            a, b = pairs[:, 0], pairs[:, 1]
+            dd = fp[a] - fp[b]
+            dd -= L * np.round(dd / L)
+            hit = np.all(cell[free[a]] == cell[free[b]], axis=1) | (np.einsum("kd,kd->k", dd, dd) < dmin * dmin)
+            a, b = a[hit], b[hit]
+            order = np.argsort(b, kind="stable")
+            a, b = a[order], b[order]
+            starts = np.searchsorted(b, np.arange(len(free) + 1))
+        else:
+            a = np.zeros(0, dtype=np.int64)
+            starts = np.zeros(len(free) + 1, dtype=np.int64)
+        kept = np.zeros(len(free), dtype=bool)
+        al = a.tolist()
+        st = starts.tolist()
+        for f in range(len(free)):
+            if any(kept[x] for x in al[st[f]:st[f + 1]]):
                 continue
-            near = (c[None, :] + off) % g
-            w = occ[near[:, 0], near[:, 1], near[:, 2]]
-            w = w[w >= 0]
-            if len(w):  # points placed earlier in this batch
-                dd = pts[w] - cand[b]
-                dd -= L * np.round(dd / L)
-                if np.min(np.einsum("kd,kd->k", dd, dd)) < dmin * dmin:
-                    continue
-            pts[k] = cand[b]
+            kept[f] = True
+            c = cell[free[f]]
+            pts[k] = cand[free[f]]
             occ[c[0], c[1], c[2]] = k
             k += 1
             if k == n:
