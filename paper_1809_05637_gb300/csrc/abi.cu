@@ -460,10 +460,10 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     // the two-stage reduction's chase reflectors (kept until the density rows are written),
     // laid out only when the context is in two-stage mode; it also borrows the merge-matrix
     // area as scratch, so only torn clusters qualify
-    c->layout_two = c->tridiag_mode == 2;
-    const bool two = c->layout_two;
-    auto q2_doubles = [two](const ClusterDesc& d) {
-        return (two && d.split && d.n >= DCLNO_TWO_STAGE_MIN) ? (long long)DCLNO_BW * band_refl_count(d.n) : 0LL;
+    c->layout_mode = c->tridiag_mode;
+    const int qmin = c->layout_mode == 2 ? DCLNO_TWO_STAGE_MIN : c->layout_mode == 0 ? DCLNO_TWO_STAGE_AUTO_MIN : 1 << 30;
+    auto q2_doubles = [qmin](const ClusterDesc& d) {
+        return (d.split && d.n >= qmin) ? (long long)DCLNO_BW * band_refl_count(d.n) : 0LL;
     };
     auto ws_doubles = [&](const ClusterDesc& d) {
         const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap * nseg(d) +
@@ -759,11 +759,13 @@ static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
 // mode (0) takes the form measured faster on the 1,728-atom step in each precision:
 // one-stage in FP64 (2.61 against 3.33 s per step), two-stage in the mixed path
 // (1.58 against 1.75 s).
-// mode 0 is the one-stage form in both precisions: measured faster on GB300 on every
-// workload here (the 1,728-atom step and the bcc slab, FP64 and mixed)
+// Whether the solve may use the two-stage form; which clusters do is fixed by the layout
+// (a cluster takes it when its workspace holds a chase-reflector log).  Mode 0: the mixed
+// path only (FP64 two-stage is slower on GB300, whose FP64 tile products barely beat its
+// FP64 vector rate); mode 2: both paths.
 static bool resolve_two_stage(const dclno_ctx* c, dclno_precision prec) {
-    (void)prec;
-    return c->tridiag_mode == 2 && c->layout_two;
+    if (c->tridiag_mode == 2) return c->layout_mode == 2;
+    return c->tridiag_mode == 0 && prec == DCLNO_MIXED;
 }
 
 // every batch: assemble + solve (eps and q of all clusters)
@@ -913,7 +915,7 @@ extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
     if (!c) return DCLNO_ERR_ARG;
     c->err.clear();
     if (mode < 0 || mode > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_tridiag: mode must be 0, 1 or 2");
-    if (mode == 2 && c->built && !c->layout_two)
+    if (mode == 2 && c->built && c->layout_mode != 2)
         return set_err(c, DCLNO_ERR_ARG,
                        "dclno_set_tridiag: the two-stage form keeps its chase reflectors in the cluster workspace, "
                        "laid out by dclno_build_clusters: select mode 2 before building the clusters");

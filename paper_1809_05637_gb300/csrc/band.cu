@@ -30,6 +30,8 @@
 
 #define BW DCLNO_BW
 #define TL (BW + 1)  // row stride of the BW x BW shared-memory blocks
+static_assert(BW == 32, "the panel factorisation maps a panel column to a lane");
+#define PQ 8  // panel rows per warp whose loads are issued together
 
 // shared memory of k_band: GEMM staging (also the mirror's transpose tiles and step 8's
 // operand columns), reduction scratch
@@ -52,9 +54,15 @@ __device__ static void mirror_lower(double* A, int ld, int r0, int n, double* ti
         while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
         const int bj = t - bi * (bi + 1) / 2;
         const int rb = r0 + 32 * bi, cb = r0 + 32 * bj;
-        for (int r = 0; r < 32; ++r) {
-            const int gr = rb + r, gc = cb + lane;
-            T[r * 33 + lane] = (gr < n && gc < n && gc <= gr) ? A[(size_t)gr * ld + gc] : 0.0;
+        for (int r0b = 0; r0b < 32; r0b += 16) {  // 16 rows' loads in flight
+            double x[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int gr = rb + r0b + i, gc = cb + lane;
+                x[i] = (gr < n && gc < n && gc <= gr) ? A[(size_t)gr * ld + gc] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) T[(r0b + i) * 33 + lane] = x[i];
         }
         __syncwarp();
         // element (gr, gc), gc < gr, goes to (gc, gr): row cb + c of the upper triangle
@@ -78,65 +86,111 @@ __device__ __forceinline__ void band_one(const ClusterDesc* __restrict__ cls, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     double* A = arena + d.mat_off;
     double* tauv = arena + d.aux_off + 2 * ld;
-    double* W = arena + d.aux_off + 3 * ld;   // m x BW (stride BW)
-    double* Vx = arena + d.m_off;             // m x BW (stride BW): the panel's reflectors, explicit
-    double* NVt = Vx + (size_t)BW * ld;       // BW x m (stride ld): -V^T
-    double* Yt = NVt + (size_t)BW * ld;       // BW x m (stride ld): Y^T = V^T A22
-    double* GZ = Yt + (size_t)BW * ld;        // [-V^T V | V^T Y], BW x 2BW (row stride gz)
+    // scratch in the merge-matrix area (2 n ld doubles, n >= DCLNO_TWO_STAGE_MIN)
+    double* NVt = arena + d.m_off;            // BW x m (stride ld): -V^T
+    double* Yt = NVt + (size_t)BW * ld;       // BW x m (stride ld): Y^T
+    double* WV = NVt;                         // m x 2BW: [W | V], once -V^T and Y^T are dead
+    double* Yr = Yt + (size_t)BW * ld;        // m x BW: Y = A22 V
+    double* VW = Yr + (size_t)BW * ld;        // m x 2BW: [V | W]
+    double* GZ = VW + (size_t)2 * BW * ld;    // [-V^T V | V^T Y], BW x 2BW (row stride gz)
     const int gz = 2 * BW + 1;
     double* Ts = GZ + BW * gz;                // T (upper triangular), BW x TL
     double* Ms = Ts + BW * TL;                // T^T (V^T Y) T, BW x TL
+    double* NTt = Ms + BW * TL;               // -T^T, BW x BW
+    double* HM = NTt + BW * BW;               // M / 2, BW x BW
     double* G = sm;
-    double* red = sm + band_gemm_doubles(EMU);
+    double* vscale = sm + band_gemm_doubles(EMU);  // BW: the panel columns' reflector scalings
+    constexpr int V2 = 2 * BW;
 
     for (int t = tid; t < n; t += blockDim.x) tauv[t] = 0.0;
     __syncthreads();
     for (int c0 = 0; c0 + BW < n; c0 += BW) {
         const int r0 = c0 + BW, m = n - r0;
         const int nbr = min(BW, m);  // reflectors of this panel (one per column with rows below the band)
-        // (1) Householder QR of the panel block A[r0:n, c0:c0+BW]; reflector j acts on rows r0+j ..
-        for (int j = 0; j < nbr; ++j) {
-            const int c = c0 + j, rs = r0 + j;
-            const double alpha = A[(size_t)rs * ld + c];
-            double sig = 0.0;
-            for (int r = rs + 1 + tid; r < n; r += blockDim.x) {
-                const double a = A[(size_t)r * ld + c];
-                sig = fma(a, a, sig);
+        // (1) Householder QR of the panel block A[r0:n, c0:c0+BW]; reflector j acts on rows
+        // r0+j ..  A lane per panel column, the warps over rows, one pass over the panel per
+        // reflector: it applies reflector j and, on the updated rows, forms the products
+        // d_l = x_{j+1}^T x_l below the next top row that reflector j+1 needs (its norm is
+        // d_{j+1}; its scaling factors out of v^T x_l).  Every pass reads whole panel rows
+        // (coalesced); the column sums go through shared memory, two buffers in turn.
+        {
+            double* cred = G;  // 2 x nw x BW partial column sums
+            int cb = 0;
+            double acc = 0.0;  // d_l for the first column
+            for (int rb = r0 + 1 + warp; rb < n; rb += PQ * nw) {
+                double x[PQ];
+#pragma unroll
+                for (int i = 0; i < PQ; ++i) {
+                    const int r = rb + i * nw;
+                    x[i] = r < n ? A[(size_t)r * ld + c0 + lane] : 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < PQ; ++i) acc = fma(__shfl_sync(0xffffffffu, x[i], 0), x[i], acc);
             }
-            sig = block_sum(sig, red);
-            double tau = 0.0, beta = alpha, scale = 0.0;
-            if (sig > 0.0) {
-                const double nrm = sqrt(alpha * alpha + sig);
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                scale = 1.0 / (alpha - beta);
-            }
-            for (int r = rs + 1 + tid; r < n; r += blockDim.x) A[(size_t)r * ld + c] *= scale;
+            cred[cb * nw * BW + warp * BW + lane] = acc;
             __syncthreads();
-            if (tid == 0) {
-                A[(size_t)rs * ld + c] = beta;
-                tauv[c] = tau;
-            }
-            if (tau != 0.0) {
-                // the remaining panel columns: x <- x - tau (v . x) v over rows rs .. n-1
-                for (int cc = c + 1 + warp; cc < c0 + BW; cc += nw) {
-                    double w = (lane == 0) ? A[(size_t)rs * ld + cc] : 0.0;
-                    for (int r = rs + 1 + lane; r < n; r += 32) w = fma(A[(size_t)r * ld + c], A[(size_t)r * ld + cc], w);
-                    w = tau * warp_sum(w);
-                    if (lane == 0) A[(size_t)rs * ld + cc] -= w;
-                    for (int r = rs + 1 + lane; r < n; r += 32)
-                        A[(size_t)r * ld + cc] = fma(-w, A[(size_t)r * ld + c], A[(size_t)r * ld + cc]);
+            double d = 0.0;  // lane l: d_l of the next reflector
+            for (int q = 0; q < nw; ++q) d += cred[cb * nw * BW + q * BW + lane];
+            cb ^= 1;
+            for (int j = 0; j < nbr; ++j) {
+                const int c = c0 + j, rs = r0 + j;
+                const double alpha = A[(size_t)rs * ld + c];
+                const double sig = __shfl_sync(0xffffffffu, d, j);
+                double tau = 0.0, beta = alpha, scale = 0.0;
+                if (sig > 0.0) {
+                    const double nrm = sqrt(alpha * alpha + sig);
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                }
+                const double xtop = A[(size_t)rs * ld + c0 + lane];
+                const double w = tau * fma(scale, d, xtop);  // tau v^T x_l, v = 1 on the top row
+                const double ws = w * scale;                 // x_l <- x_l - ws x_j below the top row
+                double na = 0.0;
+                for (int rb = rs + 1 + warp; rb < n; rb += PQ * nw) {
+                    double x[PQ];  // PQ rows' loads in flight before any store
+#pragma unroll
+                    for (int i = 0; i < PQ; ++i) {
+                        const int r = rb + i * nw;
+                        x[i] = r < n ? A[(size_t)r * ld + c0 + lane] : 0.0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < PQ; ++i) {
+                        const int r = rb + i * nw;
+                        const double xj = __shfl_sync(0xffffffffu, x[i], j);
+                        if (lane > j) {
+                            x[i] = fma(-ws, xj, x[i]);
+                            if (r < n) A[(size_t)r * ld + c0 + lane] = x[i];
+                        }
+                        const double u = __shfl_sync(0xffffffffu, x[i], (j + 1) & (BW - 1));
+                        if (r > rs + 1 && r < n) na = fma(u, x[i], na);
+                    }
+                }
+                cred[cb * nw * BW + warp * BW + lane] = na;
+                __syncthreads();
+                d = 0.0;
+                for (int q = 0; q < nw; ++q) d += cred[cb * nw * BW + q * BW + lane];
+                cb ^= 1;
+                // the top row, after every thread has read it (later reflectors start below it)
+                if (warp == 0) {
+                    if (lane > j) A[(size_t)rs * ld + c0 + lane] = xtop - w;
+                    if (lane == j) {
+                        A[(size_t)rs * ld + c] = beta;
+                        tauv[c] = tau;
+                        vscale[j] = scale;  // column j below the top row holds v / scale until step (2)
+                    }
                 }
             }
-            __syncthreads();
         }
-        // (2) explicit V (unit diagonal, zero above) and -V^T; the reflectors' row-contiguous
-        // copies for the back-transforms in the upper triangle (row c from column c + BW);
-        // the lower triangle below the band is cleared for the chase
+        // (2) explicit V (unit diagonal, zero above) as [V | .] and -V^T; the reflectors'
+        // row-contiguous copies for the back-transforms in the upper triangle (row c from
+        // column c + BW on); the lower triangle below the band is cleared for the chase
+        __syncthreads();
         for (int e = tid; e < m * BW; e += blockDim.x) {
             const int t = e / BW, j = e % BW;
-            const double v = (j >= nbr || t < j) ? 0.0 : (t == j ? 1.0 : A[(size_t)(r0 + t) * ld + c0 + j]);
-            Vx[e] = v;
+            const double v =
+                (j >= nbr || t < j) ? 0.0 : (t == j ? 1.0 : A[(size_t)(r0 + t) * ld + c0 + j] * vscale[j]);
+            VW[(size_t)t * V2 + j] = v;
             NVt[(size_t)j * ld + t] = -v;
             if (j < nbr && t >= j) A[(size_t)(c0 + j) * ld + r0 + t] = v;
         }
@@ -144,18 +198,21 @@ __device__ __forceinline__ void band_one(const ClusterDesc* __restrict__ cls, in
         for (int e = tid; e < m * BW; e += blockDim.x) {
             const int t = e / BW, j = e % BW;
             if (j < nbr && t > j) A[(size_t)(r0 + t) * ld + c0 + j] = 0.0;
+            Yr[e] = 0.0;
         }
         // (3) the trailing block in full (upper triangle from the lower) for Y = A22 V
         mirror_lower(A, ld, r0, n, G);
         __syncthreads();
-        // (4) Y^T = V^T A22: C -= (-V^T) A22^T with A22 symmetric
+        // (4) Y = A22 V: C -= A22 (-V^T)^T; then Y^T for the next product
         double* A22 = A + (size_t)r0 * ld + r0;
-        for (int e = tid; e < BW * m; e += blockDim.x) Yt[(size_t)(e / m) * ld + e % m] = 0.0;
-        __syncthreads();
-        if constexpr (EMU == 2)  // Y = A22 V, one FP64 epilogue per element, written as Y^T
-            cta_gemm_tc_longk<true>(Yt, ld, A22, ld, NVt, ld, m, BW, m, reinterpret_cast<unsigned char*>(G), &tcs);
+        if constexpr (EMU == 2)  // one FP64 epilogue per element
+            cta_gemm_tc_longk<false>(Yr, BW, A22, ld, NVt, ld, m, BW, m, reinterpret_cast<unsigned char*>(G), &tcs);
         else
-            tile_update_longk<EMU>(Yt, ld, NVt, ld, A22, ld, BW, m, m, G, &tcs);
+            tile_update_longk<EMU>(Yr, BW, A22, ld, NVt, ld, m, BW, m, G, &tcs);
+        for (int e = tid; e < BW * m; e += blockDim.x) {
+            const int a = e / m, t = e % m;
+            Yt[(size_t)a * ld + t] = Yr[(size_t)t * BW + a];
+        }
         // (5) [-V^T V | V^T Y] = -(-V^T) [-V^T ; Y^T]^T ... as C -= A B^T with B = the 2BW rows
         // of NVt and Yt (contiguous, stride ld): C = -(V^T V) on the left, +V^T Y on the right
         for (int e = tid; e < BW * gz; e += blockDim.x) GZ[e] = 0.0;
@@ -202,33 +259,34 @@ __device__ __forceinline__ void band_one(const ClusterDesc* __restrict__ cls, in
             }
         }
         __syncthreads();
-        // (8) W = Y T - 1/2 V M (m x BW), one row t per thread, in two passes; the row's
-        // operands are staged in the (now idle) GEMM area, one column per thread
-        {
-            double* Zs = G;  // BW x blockDim
-            const int nt = blockDim.x;
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int t0 = 0; t0 < m; t0 += nt) {
-                    const int t = t0 + tid;
-                    if (t < m) {
-                        for (int a = 0; a < BW; ++a)
-                            Zs[a * nt + tid] = pass == 0 ? Yt[(size_t)a * ld + t] : Vx[(size_t)t * BW + a];
-                        for (int b = 0; b < BW; ++b) {
-                            double s = pass == 0 ? 0.0 : W[(size_t)t * BW + b];
-                            if (pass == 0)
-                                for (int a = 0; a <= b; ++a) s = fma(Ts[a * TL + b], Zs[a * nt + tid], s);
-                            else
-                                for (int a = 0; a < BW; ++a) s = fma(-0.5 * Ms[a * TL + b], Zs[a * nt + tid], s);
-                            W[(size_t)t * BW + b] = s;
-                        }
-                    }
-                }
-            }
+        // (8) W = Y T - 1/2 V M (m x BW) as two tile products into the right half of [V | W]:
+        // B operands -T^T and M/2 (M is symmetric), both row-major with K contiguous
+        for (int e = tid; e < BW * BW; e += blockDim.x) {
+            const int b = e / BW, a = e % BW;
+            NTt[e] = -Ts[a * TL + b];
+            HM[e] = 0.5 * Ms[a * TL + b];
+        }
+        for (int e = tid; e < m * BW; e += blockDim.x) VW[(size_t)(e / BW) * V2 + BW + e % BW] = 0.0;
+        __syncthreads();
+        tile_update<false, EMU>(VW + BW, V2, Yr, BW, NTt, BW, m, BW, BW, 0, G, &tcs);
+        tile_update<false, EMU>(VW + BW, V2, VW, V2, HM, BW, m, BW, BW, 0, G, &tcs);
+        for (int e = tid; e < m * BW; e += blockDim.x) {
+            const int t = e / BW, b = e % BW;
+            WV[(size_t)t * V2 + b] = VW[(size_t)t * V2 + BW + b];
+            WV[(size_t)t * V2 + BW + b] = VW[(size_t)t * V2 + b];
         }
         __syncthreads();
-        // (9) A22 <- A22 - V W^T - W V^T (lower triangle)
-        tile_update<true, EMU>(A22, ld, Vx, BW, W, BW, m, m, BW, 0, G, &tcs);
-        tile_update<true, EMU>(A22, ld, W, BW, Vx, BW, m, m, BW, 0, G, &tcs);
+        // (9) A22 <- A22 - V W^T - W V^T (lower triangle).  FP64 tiles take [V | W] [W | V]^T
+        // with K = 2 BW in one pass; the emulated engines take the two products apart: a
+        // row of [V | W] sliced against its largest exponent would hold V (entries of
+        // order 1) with as many fewer bits as W (of order |A|) is larger, and the slice
+        // levels kept are relative to the product of the row maxima
+        if constexpr (EMU == 0) {
+            cta_gemm_nt_sub<true>(A22, ld, VW, V2, WV, V2, m, m, V2, 0, G);
+        } else {
+            tile_update<true, EMU>(A22, ld, VW, V2, WV, V2, m, m, BW, 0, G, &tcs);
+            tile_update<true, EMU>(A22, ld, VW + BW, V2, WV + BW, V2, m, m, BW, 0, G, &tcs);
+        }
     }
     if (EMU == 2 && tcs.failed && tid == 0) status[ci] = ST_TIMEOUT;
 }

@@ -48,6 +48,9 @@ struct ClusterDesc {
 // with p = j + 1 + k BW while p + 1 < n.
 #define DCLNO_BW 32
 #define DCLNO_TWO_STAGE_MIN 128  // clusters of at least this dimension (and torn) may use it
+// the automatic choice: the mixed path's clusters of at least this dimension (measured on
+// GB300: two-stage faster at n ~ 650-705, one-stage at n ~ 150-285)
+#define DCLNO_TWO_STAGE_AUTO_MIN 384
 __host__ __device__ inline long long chase_steps(int n, int j) {
     const int r = n - 2 - j;
     return r > 0 ? (r + DCLNO_BW - 1) / DCLNO_BW : 0;
@@ -199,7 +202,7 @@ struct dclno_ctx {
     // 1 = one-stage, 2 = two-stage (for the clusters that qualify); solved_two = the form
     // the last solve used (the density pass applies the same Q)
     int tridiag_mode = 0;
-    bool layout_two = false;  // the workspace holds chase-reflector logs (built in mode 2)
+    int layout_mode = -1;     // tridiagonalisation mode when the workspace was laid out (-1: not yet)
     bool solved_two = false;
     // engine of the mixed path's K <= 32 tile products (Cholesky, congruence, one-stage
     // tridiagonalisation): 0 = chosen per kernel and bucket by the tuner, 1 = mma.sync,
@@ -662,25 +665,35 @@ __device__ void cta_gemm_nt_sub(double* __restrict__ C, int ldc, const double* _
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
         for (int k0 = 0; k0 < K; k0 += GT_K) {
-            // stage A[r0:r0+64, k0:k0+32] and B[c0:c0+64, k0:k0+32] (zero-filled)
-            for (int e = tid; e < GT_M * GT_K / 2; e += blockDim.x) {
+            // stage A[r0:r0+64, k0:k0+32] and B[c0:c0+64, k0:k0+32] (zero-filled); all of a
+            // thread's loads are issued before its shared-memory stores
+            constexpr int PER = GT_M * GT_K / 2 / DCLNO_SOLVE_THREADS;
+            double2 va[PER], vb[PER];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int e = tid + i * DCLNO_SOLVE_THREADS;
                 const int r = e / (GT_K / 2), kk = (e % (GT_K / 2)) * 2;
-                double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+                va[i] = vb[i] = make_double2(0.0, 0.0);
                 const int gk = k0 + kk;
                 if (r0 + r < M) {
                     const double* p = A + (size_t)(r0 + r) * lda + gk;
-                    if (gk + 1 < K) va = *reinterpret_cast<const double2*>(p);
-                    else if (gk < K) va.x = p[0];
+                    if (gk + 1 < K) va[i] = *reinterpret_cast<const double2*>(p);
+                    else if (gk < K) va[i].x = p[0];
                 }
                 if (c0 + r < N) {
                     const double* p = B + (size_t)(c0 + r) * ldb + gk;
-                    if (gk + 1 < K) vb = *reinterpret_cast<const double2*>(p);
-                    else if (gk < K) vb.x = p[0];
+                    if (gk + 1 < K) vb[i] = *reinterpret_cast<const double2*>(p);
+                    else if (gk < K) vb[i].x = p[0];
                 }
-                As[r * GT_LD + kk] = va.x;
-                As[r * GT_LD + kk + 1] = va.y;
-                Bs[r * GT_LD + kk] = vb.x;
-                Bs[r * GT_LD + kk + 1] = vb.y;
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int e = tid + i * DCLNO_SOLVE_THREADS;
+                const int r = e / (GT_K / 2), kk = (e % (GT_K / 2)) * 2;
+                As[r * GT_LD + kk] = va[i].x;
+                As[r * GT_LD + kk + 1] = va[i].y;
+                Bs[r * GT_LD + kk] = vb[i].x;
+                Bs[r * GT_LD + kk + 1] = vb[i].y;
             }
             __syncthreads();
 #pragma unroll
@@ -697,21 +710,27 @@ __device__ void cta_gemm_nt_sub(double* __restrict__ C, int ldc, const double* _
             }
             __syncthreads();
         }
+        // C's elements are all loaded before any is stored (the loads overlap)
+        double cv[2][4][2];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = r0 + wr + 8 * i + fr;
-            if (r >= M) continue;
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int cc = c0 + wc + 8 * j + 2 * fk + h;
-                    if (cc >= N) continue;
-                    if (LOWER && r + diag < cc) continue;
-                    C[(size_t)r * ldc + cc] -= acc[i][j][h];
+                    const int r = r0 + wr + 8 * i + fr, cc = c0 + wc + 8 * j + 2 * fk + h;
+                    const bool ok = r < M && cc < N && !(LOWER && r + diag < cc);
+                    cv[i][j][h] = ok ? C[(size_t)r * ldc + cc] : 0.0;
                 }
-            }
-        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = r0 + wr + 8 * i + fr, cc = c0 + wc + 8 * j + 2 * fk + h;
+                    if (r < M && cc < N && !(LOWER && r + diag < cc)) C[(size_t)r * ldc + cc] = cv[i][j][h] - acc[i][j][h];
+                }
     }
     __syncthreads();
 }

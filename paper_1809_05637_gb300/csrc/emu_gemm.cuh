@@ -45,10 +45,18 @@ __device__ __forceinline__ int eg_exp(double x) {
 // read from global memory once and the row's exponent is a warp maximum.
 __device__ __forceinline__ void eg_slice_tile(const double* __restrict__ X, int ld, int r0, int nrows, int k0,
                                               int K, __nv_bfloat16* sl, int* expo) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < EG_M; r += nw) {
-        const int gr = r0 + r, gk = k0 + lane;
-        const double x = (gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = EG_M / NW;
+    double xs[PER];  // the warp's rows, all loads issued before the slices are stored
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int gr = r0 + warp + i * NW, gk = k0 + lane;
+        xs[i] = (gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int r = warp + i * NW;
+        const double x = xs[i];
         const long long b = __double_as_longlong(x);
         const int ebits = (int)((b >> 52) & 0x7ff);
         int e = ebits == 0 ? -100000 : ebits - 1023;
@@ -154,7 +162,19 @@ __device__ void cta_gemm_nt_sub_emu(double* __restrict__ C, int ldc, const doubl
                         tot[i][j][v] += (L <= 4) ? (a << (32 - 8 * L)) : (a >> (8 * L - 32));
                     }
         }
-        // value = 2^(ea+eb-46) tot; tot >> 3 fits the 53-bit mantissa (units of 2^(ea+eb-43))
+        // value = 2^(ea+eb-46) tot; tot >> 3 fits the 53-bit mantissa (units of 2^(ea+eb-43));
+        // C's elements are all loaded before any is stored
+        double cv[2][2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = r0 + wr + 16 * i + g + (v >= 2 ? 8 : 0);
+                    const int cc = c0 + wc + 8 * j + 2 * tg + (v & 1);
+                    cv[i][j][v] = (r < M && cc < N && !(LOWER && r + diag < cc)) ? C[(size_t)r * ldc + cc] : 0.0;
+                }
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -169,8 +189,7 @@ __device__ void cta_gemm_nt_sub_emu(double* __restrict__ C, int ldc, const doubl
                     const int es = ea[rl] + eb[cl] - 43 + 1023;
                     if (es < 1 || es > 2046) continue;  // a zero row or column (or far outside range)
                     const long long q = tot[i][j][v] >> 3;
-                    double* pc = C + (size_t)r * ldc + cc;
-                    *pc = fma(-(double)q, __longlong_as_double((long long)es << 52), *pc);
+                    C[(size_t)r * ldc + cc] = fma(-(double)q, __longlong_as_double((long long)es << 52), cv[i][j][v]);
                 }
         __syncthreads();
     }

@@ -5,15 +5,14 @@
 // exactly in FP32 (K <= 32), the levels combined exactly in 64-bit integers, two FP64
 // instructions per output element.
 //
-// Tile 128 x 64 outputs, K <= 32 per call.  The slices sit in shared memory in the
+// Tile 128 x 32 outputs, K <= 32 per call.  The slices sit in shared memory in the
 // K-major core-matrix layout of the MMA (8 rows x 16 bytes per core matrix; core
-// matrices 128 bytes apart along K, 512 bytes apart along M/N).  One thread issues
-// the level's (L+1) x 2 MMAs (M = 128, N = 64, K = 16) into one of two tensor-memory
-// buffers of 64 FP32 columns and commits them to that buffer's mbarrier; all eight
-// warps then read the level back (warp w: lanes 32 (w mod 4) .. + 31 = tile rows,
-// columns 32 (w / 4) .. + 31) and add it into their integer totals, while the
-// tensor cores already work on level L + 1.  A buffer is reissued (level L + 2)
-// only after every warp has read it.
+// matrices 128 bytes apart along K, 512 bytes apart along M/N).  One thread issues the
+// MMAs of all eight levels at once (level L: (L+1) x 2 MMAs of M = 128, N = 32, K = 16
+// into its own 32 tensor-memory columns, 256 columns in all) behind one commit; after
+// one wait every warp reads the eight levels of its 32 rows x 16 columns back
+// (tcgen05.ld) and adds them into its integer totals.  One round trip per tile (or per
+// K-chunk of the long-K product) instead of one per level.
 //
 // Waits on the mbarriers are bounded: on expiry the CTA's status word is set and the
 // update is abandoned (its result is then garbage, the caller reports the status).
@@ -24,15 +23,19 @@
 #include "dclno_internal.cuh"
 
 #define TC_M 128
-#define TC_N 64
+#define TC_N 32
 #define TC_K 32
 #define TC_SL 8
 #define TC_A_SLICE_BYTES (TC_M * TC_K * 2)  // 8192
-#define TC_B_SLICE_BYTES (TC_N * TC_K * 2)  // 4096
+#define TC_B_SLICE_BYTES (TC_N * TC_K * 2)  // 2048
+#define TC_B_REGION (TC_M * TC_N * 8)       // B slices (16 KB), or a tile of totals as doubles (32 KB)
 #define TC_LBO 128                          // core matrices along K
 #define TC_SBO 512                          // 8-row groups along M / N
-#define TC_TMEM_COLS 128                    // two level buffers of TC_N columns
-#define TC_SMEM_BYTES (TC_SL * (TC_A_SLICE_BYTES + TC_B_SLICE_BYTES) + (TC_M + TC_N) * 4 + 64)
+#define TC_TMEM_COLS 256                    // eight level accumulators of TC_N columns
+#define TC_SMEM_BYTES (TC_SL * TC_A_SLICE_BYTES + TC_B_REGION + (TC_M + TC_N) * 4 + 64)
+// at most two such CTAs fit an SM's 228 KB of shared memory, so their tensor memory
+// (2 x 256 of the SM's 512 columns) is always available to both
+static_assert(3 * (TC_SMEM_BYTES + 1024) > 228 * 1024 && 2 * TC_TMEM_COLS <= 512, "tensor-memory budget");
 #define TC_WAIT_LIMIT 4000000
 
 // per-CTA state of the engine (in shared memory)
@@ -111,11 +114,20 @@ __device__ __forceinline__ void tc_end(TcState* st) {
 template <int ROWS>
 __device__ __forceinline__ void tc_slice_tile(const double* __restrict__ X, int ld, int r0, int nrows, int K,
                                               unsigned char* sl, int slice_bytes, int* expo) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int kofs = (lane >> 3) * TC_LBO + (lane & 7) * 2;
-    for (int r = warp; r < ROWS; r += nw) {
-        const int gr = r0 + r;
-        const double x = (gr < nrows && lane < K) ? X[(size_t)gr * ld + lane] : 0.0;
+    constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = (ROWS + NW - 1) / NW;
+    double xs[PER];  // the warp's rows, all loads issued before the slices are stored
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int r = warp + i * NW, gr = r0 + r;
+        xs[i] = (r < ROWS && gr < nrows && lane < K) ? X[(size_t)gr * ld + lane] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int r = warp + i * NW;
+        if (r >= ROWS) break;
+        const double x = xs[i];
         const long long b = __double_as_longlong(x);
         const int ebits = (int)((b >> 52) & 0x7ff);
         int e = ebits == 0 ? -100000 : ebits - 1023;
@@ -138,29 +150,72 @@ __device__ __forceinline__ void tc_slice_tile(const double* __restrict__ X, int 
     }
 }
 
-// issue the MMAs of level L into buffer buf (one thread)
-__device__ __forceinline__ void tc_issue_level(TcState* st, const unsigned char* As, const unsigned char* Bs, int L,
-                                               int buf) {
-    const uint32_t d = st->tmem + (uint32_t)(buf * TC_N);
+// issue the MMAs of all levels (level L into tensor-memory columns [32 L, 32 L + 32))
+// and commit them to barrier 0 (one thread)
+__device__ __forceinline__ void tc_issue_levels(TcState* st, const unsigned char* As, const unsigned char* Bs) {
     const uint32_t id = tc_idesc(TC_M, TC_N);
     const uint32_t a0 = tc_smem_u32(As), b0 = tc_smem_u32(Bs);
-    int first = 1;
-    for (int t = 0; t <= L; ++t) {
-        const int u = L - t;
+#pragma unroll 1
+    for (int L = 0; L < TC_SL; ++L) {
+        const uint32_t d = st->tmem + (uint32_t)(L * TC_N);
+        for (int t = 0; t <= L; ++t) {
+            const int u = L - t;
 #pragma unroll
-        for (int ks = 0; ks < TC_K / 16; ++ks) {
-            const uint64_t ad = tc_desc(a0 + t * TC_A_SLICE_BYTES + ks * 2 * TC_LBO);
-            const uint64_t bd = tc_desc(b0 + u * TC_B_SLICE_BYTES + ks * 2 * TC_LBO);
-            asm volatile(
-                "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(d),
-                "l"(ad), "l"(bd), "r"(id), "r"(first ? 0 : 1));
-            first = 0;
+            for (int ks = 0; ks < TC_K / 16; ++ks) {
+                const uint64_t ad = tc_desc(a0 + t * TC_A_SLICE_BYTES + ks * 2 * TC_LBO);
+                const uint64_t bd = tc_desc(b0 + u * TC_B_SLICE_BYTES + ks * 2 * TC_LBO);
+                asm volatile(
+                    "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(id), "r"((t == 0 && ks == 0) ? 0 : 1));
+            }
         }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        tc_smem_u32(&st->mbar[buf])));
-    st->issued[buf] += 1;
+        tc_smem_u32(&st->mbar[0])));
+    st->issued[0] += 1;
+}
+
+// Issue all levels of the staged slices, wait, and add the levels of this warp's 32 rows
+// (lane quarter q) x 16 columns (half h) into tot (all threads call it; it ends with a
+// barrier after which the tensor memory may be reissued).  False once a wait ran out.
+__device__ __forceinline__ bool tc_run_levels(TcState* st, const unsigned char* As, const unsigned char* Bs, int q,
+                                              int h, long long* tot) {
+    asm volatile("fence.proxy.async.shared::cta;");  // the slices, visible to the tensor cores
+    __syncthreads();
+    if (threadIdx.x == 0 && !st->failed) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tc_issue_levels(st, As, Bs);
+    }
+    __syncthreads();
+    bool ok = !st->failed && tc_wait(&st->mbar[0], st->uses[0]);
+    if (!ok) st->failed = 1;  // any thread that gave up marks the CTA
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+#pragma unroll 1
+        for (int L = 0; L < TC_SL; ++L) {
+            uint32_t r[16];
+            const uint32_t ta = st->tmem + (uint32_t)(L * TC_N + 16 * h) + ((uint32_t)(32 * q) << 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+                " [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+                tot[j] += (L <= 4) ? (v << (32 - 8 * L)) : (v >> (8 * L - 32));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // every warp has read the accumulators
+    if (threadIdx.x == 0 && !st->failed) st->uses[0] += 1;  // else tc_end waits this commit out
+    __syncthreads();
+    return !st->failed;
 }
 
 // C[M x N] -= A[M x K] B[N x K]^T, K <= 32; LOWER and diag as in cta_gemm_nt_sub.
@@ -171,7 +226,7 @@ __device__ void cta_gemm_nt_sub_tc(double* __restrict__ C, int ldc, const double
                                    unsigned char* smem, TcState* st) {
     unsigned char* As = smem;
     unsigned char* Bs = As + TC_SL * TC_A_SLICE_BYTES;
-    int* ea = reinterpret_cast<int*>(Bs + TC_SL * TC_B_SLICE_BYTES);
+    int* ea = reinterpret_cast<int*>(Bs + TC_B_REGION);
     int* eb = ea + TC_M;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter (rows 32 q ..) and column half
@@ -187,79 +242,41 @@ __device__ void cta_gemm_nt_sub_tc(double* __restrict__ C, int ldc, const double
             sliced_ti = ti;
         }
         tc_slice_tile<TC_N>(B, ldb, c0, N, K, Bs, TC_B_SLICE_BYTES, eb);
-        asm volatile("fence.proxy.async.shared::cta;");  // the slices, visible to the tensor cores
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            tc_issue_level(st, As, Bs, 0, 0);
-            tc_issue_level(st, As, Bs, 1, 1);
-        }
-        long long tot[32];
+        long long tot[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tot[j] = 0;
-        bool ok = true;
-        for (int L = 0; L < TC_SL; ++L) {
-            const int buf = L & 1;
-            ok = ok && tc_wait(&st->mbar[buf], st->uses[buf]);
-            if (!ok) st->failed = 1;  // any thread that gave up marks the CTA
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            uint32_t r[32];
-            if (ok) {
-                const uint32_t ta = st->tmem + (uint32_t)(buf * TC_N + 32 * h) + ((uint32_t)(32 * q) << 16);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long long a = (long long)__float2int_rn(__uint_as_float(r[j]));
-                    tot[j] += (L <= 4) ? (a << (32 - 8 * L)) : (a >> (8 * L - 32));
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();  // every warp has read buffer buf
-            if (tid == 0) {
-                ok = ok && !st->failed;
-                st->uses[buf] += 1;
-                if (ok && L + 2 < TC_SL) {
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    tc_issue_level(st, As, Bs, L + 2, buf);
-                }
-            }
-            __syncthreads();
-            ok = !st->failed;
-        }
-        if (!ok) break;
+        for (int j = 0; j < 16; ++j) tot[j] = 0;
+        if (!tc_run_levels(st, As, Bs, q, h, tot)) break;
         // value = 2^(ea+eb-46) tot; tot >> 3 fits the 53-bit mantissa (units of 2^(ea+eb-43)).
-        // The integer totals pass through shared memory (the B slices, 32 columns at a
-        // time, columns XOR-swizzled by the row) so that C is updated row-contiguously.
+        // The integer totals pass through shared memory (the B slices' region, columns
+        // XOR-swizzled by the row) so that C is updated row-contiguously.
         {
             const int rl = 32 * q + lane;
-            double* Vs = reinterpret_cast<double*>(Bs);  // TC_M x 32
-            for (int half = 0; half < TC_N / 32; ++half) {
-                if (h == half)
+            double* Vs = reinterpret_cast<double*>(Bs);  // TC_M x TC_N
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) Vs[rl * 32 + (j ^ (rl & 15))] = (double)(tot[j] >> 3);
-                __syncthreads();
-                for (int rr = warp; rr < TC_M; rr += blockDim.x >> 5) {
-                    const int r = r0 + rr, cl = 32 * half + lane, cc = c0 + cl;
-                    if (r >= M || cc >= N) continue;
-                    if (LOWER && r + diag < cc) continue;
-                    const int es = ea[rr] + eb[cl] - 43 + 1023;
-                    if (es < 1 || es > 2046) continue;  // a zero row or column (or far outside range)
-                    double* pc = C + (size_t)r * ldc + cc;
-                    *pc = fma(-Vs[rr * 32 + (lane ^ (rr & 15))], __longlong_as_double((long long)es << 52), *pc);
-                }
-                __syncthreads();
+            for (int j = 0; j < 16; ++j) {
+                const int cl = 16 * h + j;
+                Vs[rl * TC_N + (cl ^ (rl & 15))] = (double)(tot[j] >> 3);
+            }
+            __syncthreads();
+            constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = TC_M / NW;
+            double cv[PER];  // C's elements of the warp's rows, loaded before any is stored
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int r = r0 + warp + i * NW, cc = c0 + lane;
+                cv[i] = (r < M && cc < N && !(LOWER && r + diag < cc)) ? C[(size_t)r * ldc + cc] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int rr = warp + i * NW, r = r0 + rr, cl = lane, cc = c0 + cl;
+                if (r >= M || cc >= N) continue;
+                if (LOWER && r + diag < cc) continue;
+                const int es = ea[rr] + eb[cl] - 43 + 1023;
+                if (es < 1 || es > 2046) continue;  // a zero row or column (or far outside range)
+                C[(size_t)r * ldc + cc] =
+                    fma(-Vs[rr * TC_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), cv[i]);
             }
         }
-        __syncthreads();  // the slices may be overwritten by the next tile
+        __syncthreads();  // the B region may be overwritten by the next tile
     }
     __syncthreads();
 }
@@ -270,11 +287,12 @@ __device__ void cta_gemm_nt_sub_tc(double* __restrict__ C, int ldc, const double
 // (a first pass over the tile's rows), every K-chunk of 32 is sliced against them, and
 // the integer totals of all chunks are kept in registers (|total| < 2^54 per chunk, so
 // up to 500 chunks fit 64 bits); each output then costs two FP64 instructions in all,
-// instead of two per chunk.  TRANS writes element (r, c) to C[c * ldc + r].
-// smem: TC_SMEM_BYTES; tensor memory: columns [0, 64) of the CTA's allocation.
+// instead of two per chunk.  TRANS writes element (r, c) to C[c * ldc + r]; LOWER
+// (without TRANS) updates only the lower triangle r >= c of C.
+// smem: TC_SMEM_BYTES; tensor memory: the CTA's allocation (eight level accumulators).
 // ---------------------------------------------------------------------------
-#define TCL_N 32
-#define TCL_B_SLICE_BYTES (TCL_N * TC_K * 2)  // 2048
+#define TCL_N TC_N
+#define TCL_B_SLICE_BYTES TC_B_SLICE_BYTES
 
 // largest exponent of rows [r0, r0 + rows) of X over k < K (warp per row)
 __device__ __forceinline__ void tcl_row_expo(const double* __restrict__ X, int ld, int r0, int rows, int nrows, int K,
@@ -294,22 +312,29 @@ __device__ __forceinline__ void tcl_row_expo(const double* __restrict__ X, int l
     }
 }
 
-// slices of rows [r0, r0 + ROWS) x k [k0, k0 + 32) against the fixed row exponents expo[]
+// rows [r0, r0 + ROWS) x k [k0, k0 + 32) of X into registers (a warp per row, a lane per
+// k; warp w holds rows w, w + 8, ..)
 template <int ROWS>
-__device__ __forceinline__ void tcl_slice_chunk(const double* __restrict__ X, int ld, int r0, int nrows, int k0, int K,
-                                                const int* expo, unsigned char* sl, int slice_bytes) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int kofs = (lane >> 3) * TC_LBO + (lane & 7) * 2;
-    constexpr int PER = (ROWS + 7) / 8;  // rows per warp (eight warps): loads issued together
-    double x[PER];
+__device__ __forceinline__ void tcl_load_chunk(const double* __restrict__ X, int ld, int r0, int nrows, int k0, int K,
+                                               double* x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = (ROWS + NW - 1) / NW;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        const int r = warp + i * nw, gr = r0 + r, gk = k0 + lane;
+        const int r = warp + i * NW, gr = r0 + r, gk = k0 + lane;
         x[i] = (r < ROWS && gr < nrows && gk < K) ? X[(size_t)gr * ld + gk] : 0.0;
     }
+}
+
+// the loaded chunk's slices against the fixed row exponents expo[]
+template <int ROWS>
+__device__ __forceinline__ void tcl_store_chunk(const double* x, const int* expo, unsigned char* sl, int slice_bytes) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = (ROWS + NW - 1) / NW;
+    const int kofs = (lane >> 3) * TC_LBO + (lane & 7) * 2;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        const int r = warp + i * nw;
+        const int r = warp + i * NW;
         if (r >= ROWS) break;
         const long long b = __double_as_longlong(x[i]);
         const int ebits = (int)((b >> 52) & 0x7ff);
@@ -329,31 +354,7 @@ __device__ __forceinline__ void tcl_slice_chunk(const double* __restrict__ X, in
     }
 }
 
-__device__ __forceinline__ void tcl_issue_level(TcState* st, const unsigned char* As, const unsigned char* Bs, int L,
-                                                int buf) {
-    const uint32_t d = st->tmem + (uint32_t)(buf * TCL_N);
-    const uint32_t id = tc_idesc(TC_M, TCL_N);
-    const uint32_t a0 = tc_smem_u32(As), b0 = tc_smem_u32(Bs);
-    int first = 1;
-    for (int t = 0; t <= L; ++t) {
-        const int u = L - t;
-#pragma unroll
-        for (int ks = 0; ks < TC_K / 16; ++ks) {
-            const uint64_t ad = tc_desc(a0 + t * TC_A_SLICE_BYTES + ks * 2 * TC_LBO);
-            const uint64_t bd = tc_desc(b0 + u * TCL_B_SLICE_BYTES + ks * 2 * TC_LBO);
-            asm volatile(
-                "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}\n" ::"r"(d),
-                "l"(ad), "l"(bd), "r"(id), "r"(first ? 0 : 1));
-            first = 0;
-        }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        tc_smem_u32(&st->mbar[buf])));
-    st->issued[buf] += 1;
-}
-
-template <bool TRANS>
+template <bool TRANS, bool LOWER = false>
 __device__ void cta_gemm_tc_longk(double* __restrict__ C, int ldc, const double* __restrict__ A, int lda,
                                   const double* __restrict__ B, int ldb, int M, int N, int K, unsigned char* smem,
                                   TcState* st) {
@@ -361,13 +362,14 @@ __device__ void cta_gemm_tc_longk(double* __restrict__ C, int ldc, const double*
     unsigned char* Bs = As + TC_SL * TC_A_SLICE_BYTES;
     int* ea = reinterpret_cast<int*>(Bs + TC_SL * TCL_B_SLICE_BYTES);
     int* eb = ea + TC_M;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = warp & 3, h = warp >> 2;  // rows 32 q .., columns 16 h ..
     const int tilesM = (M + TC_M - 1) / TC_M, tilesN = (N + TCL_N - 1) / TCL_N;
     for (int tix = 0; tix < tilesM * tilesN; ++tix) {
         if (st->failed) break;
         const int ti = tix / tilesN, tj = tix % tilesN;
         const int r0 = ti * TC_M, c0 = tj * TCL_N;
+        if (LOWER && r0 + TC_M - 1 < c0) continue;  // uniform across the CTA
         tcl_row_expo(A, lda, r0, TC_M, M, K, ea);
         tcl_row_expo(B, ldb, c0, TCL_N, N, K, eb);
         __syncthreads();
@@ -375,51 +377,18 @@ __device__ void cta_gemm_tc_longk(double* __restrict__ C, int ldc, const double*
 #pragma unroll
         for (int j = 0; j < 16; ++j) tot[j] = 0;
         bool ok = true;
+        // the next chunk's loads are in flight while the tensor cores work on this one
+        double xa[TC_M / 8], xb[TCL_N / 8];
+        tcl_load_chunk<TC_M>(A, lda, r0, M, 0, K, xa);
+        tcl_load_chunk<TCL_N>(B, ldb, c0, N, 0, K, xb);
         for (int k0 = 0; k0 < K && ok; k0 += TC_K) {
-            tcl_slice_chunk<TC_M>(A, lda, r0, M, k0, K, ea, As, TC_A_SLICE_BYTES);
-            tcl_slice_chunk<TCL_N>(B, ldb, c0, N, k0, K, eb, Bs, TCL_B_SLICE_BYTES);
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                tcl_issue_level(st, As, Bs, 0, 0);
-                tcl_issue_level(st, As, Bs, 1, 1);
+            tcl_store_chunk<TC_M>(xa, ea, As, TC_A_SLICE_BYTES);
+            tcl_store_chunk<TCL_N>(xb, eb, Bs, TCL_B_SLICE_BYTES);
+            if (k0 + TC_K < K) {
+                tcl_load_chunk<TC_M>(A, lda, r0, M, k0 + TC_K, K, xa);
+                tcl_load_chunk<TCL_N>(B, ldb, c0, N, k0 + TC_K, K, xb);
             }
-            for (int L = 0; L < TC_SL; ++L) {
-                const int buf = L & 1;
-                ok = ok && tc_wait(&st->mbar[buf], st->uses[buf]);
-                if (!ok) st->failed = 1;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (ok) {
-                    uint32_t r[16];
-                    const uint32_t ta = st->tmem + (uint32_t)(buf * TCL_N + 16 * h) + ((uint32_t)(32 * q) << 16);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-                        " [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(ta));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long a = (long long)__float2int_rn(__uint_as_float(r[j]));
-                        tot[j] += (L <= 4) ? (a << (32 - 8 * L)) : (a >> (8 * L - 32));
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
-                if (tid == 0) {
-                    ok = ok && !st->failed;
-                    st->uses[buf] += 1;
-                    if (ok && L + 2 < TC_SL) {
-                        asm volatile("tcgen05.fence::after_thread_sync;");
-                        tcl_issue_level(st, As, Bs, L + 2, buf);
-                    }
-                }
-                __syncthreads();
-                ok = !st->failed;
-            }
+            ok = tc_run_levels(st, As, Bs, q, h, tot);
         }
         if (!ok) break;
         // one epilogue: (tot >> 3) 2^(ea + eb - 43), staged through shared memory (the A
@@ -434,24 +403,40 @@ __device__ void cta_gemm_tc_longk(double* __restrict__ C, int ldc, const double*
             }
         }
         __syncthreads();
-        if (!TRANS) {
-            for (int rr = warp; rr < TC_M; rr += nw) {
-                const int r = r0 + rr, cl = lane, cc = c0 + cl;
-                if (r >= M || cc >= N) continue;
+        // C's elements are all loaded before any is stored (the loads overlap)
+        constexpr int NW = DCLNO_SOLVE_THREADS / 32, PER = TC_M * TCL_N / DCLNO_SOLVE_THREADS;
+        double cv[PER];
+        if (!TRANS) {  // warp per row, lane per column
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int r = r0 + warp + i * NW, cc = c0 + lane;
+                cv[i] = (r < M && cc < N && !(LOWER && r < cc)) ? C[(size_t)r * ldc + cc] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int rr = warp + i * NW, r = r0 + rr, cl = lane, cc = c0 + cl;
+                if (r >= M || cc >= N || (LOWER && r < cc)) continue;
                 const int es = ea[rr] + eb[cl] - 43 + 1023;
                 if (es < 1 || es > 2046) continue;
-                double* pc = C + (size_t)r * ldc + cc;
-                *pc = fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), *pc);
+                C[(size_t)r * ldc + cc] =
+                    fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), cv[i]);
             }
-        } else {
-            for (int idx = tid; idx < TC_M * TCL_N; idx += blockDim.x) {
-                const int cl = idx / TC_M, rr = idx % TC_M;
+        } else {  // thread per row of a column
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = tid + i * DCLNO_SOLVE_THREADS, cl = idx / TC_M, rr = idx % TC_M;
+                const int r = r0 + rr, cc = c0 + cl;
+                cv[i] = (r < M && cc < N) ? C[(size_t)cc * ldc + r] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = tid + i * DCLNO_SOLVE_THREADS, cl = idx / TC_M, rr = idx % TC_M;
                 const int r = r0 + rr, cc = c0 + cl;
                 if (r >= M || cc >= N) continue;
                 const int es = ea[rr] + eb[cl] - 43 + 1023;
                 if (es < 1 || es > 2046) continue;
-                double* pc = C + (size_t)cc * ldc + r;
-                *pc = fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), *pc);
+                C[(size_t)cc * ldc + r] =
+                    fma(-Vs[rr * TCL_N + (cl ^ (rr & 15))], __longlong_as_double((long long)es << 52), cv[i]);
             }
         }
         __syncthreads();
