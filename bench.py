@@ -52,10 +52,11 @@ def parse():
     p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
     p.add_argument("--no-amorphous", action="store_true",
                    help="skip the one-step measurement of the 32,000-atom amorphous workload (run on one GPU only)")
-    p.add_argument("--workload", choices=["rocksalt1728", "rocksalt512", "small64", "amorphous32000"],
+    p.add_argument("--workload", choices=["rocksalt1728", "rocksalt512", "rocksalt216", "small64", "amorphous32000"],
                    default="rocksalt1728",
                    help="rocksalt512: the same rock-salt recipe on 8^3 sites (the same cluster dimensions, one "
-                        "wave of clusters in flight: the case for ncu captures of the cubic kernels); "
+                        "wave of clusters in flight); rocksalt216: on 6^3 sites (the same cluster dimensions, "
+                        "under 5 GB on the device: the case for DRAM-traffic captures of the cubic kernels); "
                         "small64: a 64-cluster periodic lattice (n ~ 525) for ncu captures of single kernels; "
                         "amorphous32000: the 32,000-atom random packing, generated row range by row range "
                         "into device memory and solved through memory-admitted batches")
@@ -78,6 +79,8 @@ def make_workload(name):
                                k_lno=3, periodic=True, name="small64")
     if name == "rocksalt512":
         return T.make_system(2, n_cells=8)
+    if name == "rocksalt216":
+        return T.make_system(2, n_cells=6)
     return T.make_system(2)
 
 
@@ -473,16 +476,32 @@ def roofline_report(kernel, path, n, k_ms, k_n, dfma, dmma, bf16, bf16_src):
         src = (f"FP64 part on measured FP64 FMA {dfma:.3f} TFLOP/s; tile products as {SLICE_PRODUCTS} BF16 slice "
                f"products per FP64 multiply-add at {bf16:.0f} TFLOP/s BF16, {bf16_src}")
     launch_s = k_ms / max(k_n, 1) / 1e3 if k_n else None
+    per = TRAFFIC_PER_CLUSTER.get((kernel, path))
+    traffic = per * len(n) if per is not None else None
+    traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per cluster of this kernel on the 216-cluster "
+                   "rock-salt case (same cluster dimensions), times the clusters of this launch"
+                   if per is not None else "no capture of this kernel on this path")
     achieved = flops / launch_s / 1e12 if launch_s else None
     peak = flops / floor_s / 1e12
     return {"bound": "alu", "kernel": kernel, "path": path, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s (FP64-equivalent)" if path == "mixed" else "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "traffic_source": "not measured in this run: DRAM bytes per launch are in profiles/ from a one-wave "
-                              "capture (the per-cluster traffic depends on how many clusters share L2)",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_source": traffic_src,
             "peak_source": src, "flops_per_launch": flops, "floor_ms": floor_s * 1e3,
             "launch_ms": launch_s * 1e3 if launch_s else None}
 
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cluster of one launch,
+# from an ncu capture of each kernel on the 216-cluster rock-salt case (the benchmark's
+# recipe on 6^3 sites: the same cluster dimensions, 654-702), scaled to a launch by its
+# clusters: in both cases each cluster's trailing matrix (3.7 MB) is many times its
+# share of the L2, so every pass over it goes to DRAM.  Taken on the kernels as they
+# are now; a change to a kernel voids its entry.
+TRAFFIC_PER_CLUSTER = {
+    ("k_tridiag", "fp64"): (83441013504 + 7083535104) / 216,
+    ("k_band", "mixed"): (15157292800 + 10908427520) / 216,
+    ("k_chase", "mixed"): (519777792 + 6987047936) / 216,
+}
 
 TUNE_STEPS = 4  # eager solves the schedule tuner needs to decide (its largest candidate set)
 
