@@ -211,6 +211,23 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
 dclno_status dclno_set_tridiag(dclno_ctx *ctx, int mode);
 
 /*
+ * Cuppen's tear of the tridiagonal eigenproblem (Sec. II.C step (iii)): clusters of
+ * dimension >= 64 are torn at n/2, their two halves solved by implicit QL (a dependent
+ * chain of rotations per half) and merged through the secular equation.  Torn twice,
+ * each half is torn again at its middle: four QL chains of about a quarter of the
+ * rotations each, two merges of halves, then the merge of the halves.  The results
+ * are the same eigenpairs up to rounding.
+ *   0  automatic (default): twice for clusters of dimension >= 384, once below;
+ *   1  once;
+ *   2  twice for every torn cluster (dimension >= 64).
+ * The segments' rotation logs and the merge matrices are laid out by
+ * dclno_build_clusters for the mode selected then (a cluster torn twice holds merge
+ * matrices of 4 n ld doubles instead of 2 n ld); selecting another mode after the
+ * build returns DCLNO_ERR_ARG, and so does a mode outside 0..2.
+ */
+dclno_status dclno_set_tear(dclno_ctx *ctx, int mode);
+
+/*
  * Tensor-core engine of the mixed path's emulated FP64 tile products (the same
  * arithmetic and the same bits either way: eight 8-bit slices per FP64 row, exact
  * FP32 level sums, exact 64-bit level combination) for the products with K <= 32

@@ -25,7 +25,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
            "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles",
            "dclno_set_mixed_engine", "dclno_set_schedule", "dclno_set_tuning_cache", "dclno_tuning_report",
-           "dclno_set_bucket_min"]
+           "dclno_set_bucket_min", "dclno_set_tear"]
 
 
 class DclnoError(RuntimeError):
@@ -98,6 +98,7 @@ def load_library():
         "dclno_set_mixed_engine": ([P, I], I),
         "dclno_set_schedule": ([P, I], I),
         "dclno_set_bucket_min": ([P, I], I),
+        "dclno_set_tear": ([P, I], I),
         "dclno_set_tuning_cache": ([P, ctypes.c_char_p], I),
         "dclno_tuning_report": ([P, ctypes.c_char_p, ctypes.c_size_t, P], I),
     }
@@ -234,6 +235,10 @@ class Context:
     def set_schedule(self, mode):
         """Grid form of the cubic kernels: 0 tuned, 1 one CTA per cluster, 2 persistent."""
         self._check(self.lib.dclno_set_schedule(self.h, int(mode)))
+
+    def set_tear(self, mode):
+        """Cuppen's tear: 0 automatic (twice from dimension 384), 1 once, 2 twice (from 64); before the build."""
+        self._check(self.lib.dclno_set_tear(self.h, int(mode)))
 
     def set_bucket_min(self, count):
         """Minimum clusters per size bucket (0: twice the SM count; 1: every 64-wide bucket)."""

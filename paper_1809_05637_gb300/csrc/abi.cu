@@ -38,6 +38,8 @@ static void free_clusters(dclno_ctx* c) {
     dfree(c->d_moff);
     dfree(c->d_cl);
     dfree(c->d_order);
+    dfree(c->d_l1);
+    dfree(c->d_l2);
     dfree(c->d_mem);
     dfree(c->d_mem_cl);
     dfree(c->d_pairblk);
@@ -290,6 +292,112 @@ static double kappa_radius(const std::vector<double>& dd, const std::vector<char
     return best_r;
 }
 
+// Tear positions of a cluster: once at n/2 (split) and, for a cluster torn twice, also at
+// the middle of each half (split1, split3), by the context's tear mode.
+static void set_tears(const dclno_ctx* c, ClusterDesc& d) {
+    d.split2 = 0;
+    d.split1 = d.split3 = 0;
+    if (!d.split) return;
+    const bool twice = c->tear_mode == 2 ? d.n >= DCLNO_TEAR_MIN : c->tear_mode == 0 ? d.n >= DCLNO_TEAR2_MIN : false;
+    if (!twice) return;
+    d.split2 = 1;
+    d.split1 = d.split / 2;
+    d.split3 = d.split + (d.n - d.split) / 2;
+}
+
+static long long longest_segment(const ClusterDesc& d) {
+    if (!d.split) return d.n;
+    if (!d.split2) return std::max(d.split, d.n - d.split);
+    return std::max(std::max(d.split1, d.split - d.split1), std::max(d.split3 - d.split, d.n - d.split3));
+}
+
+// merge matrices and their transposes: the cluster's (2 n ld) and, torn twice, its halves' (2 n ld)
+static long long merge_area(const ClusterDesc& d) { return d.split ? (d.split2 ? 4LL : 2LL) * d.n * d.ld : 0LL; }
+
+// a cluster's own problem: status and W-block offsets
+static void set_problem_offsets(ClusterDesc& d, int i) {
+    const long long W = d.aux_off + 3LL * d.ld;
+    d.sidx = i;
+    d.g_row0 = 0;
+    d.x2_mode = 0;
+    d.w_off = W;
+    d.gb_off = W;
+    d.scr_off = W;
+    d.x2_off = W + w_row(d.ld, DCLNO_W_X2);
+}
+
+// The two half problems of a cluster torn twice (n = 0 otherwise), in the cluster's
+// workspace: d, e from the half's first row, its strips' rows, the second pair of its
+// four segments' rotation logs and sweep headers for the second half, its merge matrix
+// after the cluster's; its z row and the rows its QL carries in the cluster's W block.
+static void make_halves(dclno_ctx* c, int i) {
+    const ClusterDesc& d = c->cl[i];
+    for (int h = 0; h < 2; ++h) {
+        ClusterDesc& e = c->clh[2 * (size_t)i + h];
+        e = ClusterDesc{};
+        e.sidx = i;
+        e.q2_off = -1;
+        if (!d.split2) continue;
+        const int r0 = h ? d.split : 0;
+        const long long W = d.aux_off + 3LL * d.ld;
+        e.centre = d.centre;
+        e.n = h ? d.n - d.split : d.split;
+        e.ld = d.ld;
+        e.nmem = d.nmem;
+        e.mbeg = d.mbeg;
+        e.mat_off = d.mat_off;
+        e.eig_off = d.eig_off + r0;
+        e.cc_off = d.cc_off + (long long)r0 * 2 * d.mc;
+        e.rot_off = d.rot_off + 2LL * h * 2 * d.rot_cap;  // two segments' logs of 2 doubles per rotation
+        e.it_off = d.it_off + 2LL * h * d.it_cap;
+        e.aux_off = d.aux_off + r0;
+        e.rot_cap = d.rot_cap;
+        e.it_cap = d.it_cap;
+        e.mc = d.mc;
+        e.split = (h ? d.split3 : d.split1) - r0;
+        e.pair_off = d.pair_off;
+        e.m_off = d.m_off + 2LL * d.n * d.ld + (h ? 2LL * d.split * d.ld : 0LL);
+        e.g_row0 = r0;
+        e.x2_mode = h ? 1 : 2;
+        e.w_off = W + w_row(d.ld, h ? DCLNO_W_HALF1 : DCLNO_W_HALF0);
+        e.gb_off = W;
+        e.scr_off = W + (h ? 16LL * d.ld : 0LL);  // each half's strips' scratch: at most 13 ld
+        e.x2_off = W + w_row(d.ld, DCLNO_W_X2);
+    }
+}
+
+// per batch, in its decreasing-n order: the two-segment problems (a cluster torn at most
+// once, or both halves of one torn twice) and the clusters torn twice
+static void build_problem_lists(dclno_ctx* c) {
+    c->l1.clear();
+    c->l2.clear();
+    for (Batch& b : c->batches) {
+        b.l1beg = (int)c->l1.size();
+        b.l2beg = (int)c->l2.size();
+        b.segmax = 1;
+        b.l1maxn = 1;
+        for (int o = b.obeg; o < b.oend; ++o) {
+            const int i = c->order[o];
+            const ClusterDesc& d = c->cl[i];
+            if (d.split2) {
+                for (int h = 0; h < 2; ++h) {
+                    const ClusterDesc& e = c->clh[2 * (size_t)i + h];
+                    c->l1.push_back(c->N + 2 * i + h);
+                    b.segmax = std::max(b.segmax, std::max(seg_len(e, 0), seg_len(e, 1)));
+                    b.l1maxn = std::max(b.l1maxn, e.n);
+                }
+                c->l2.push_back(i);
+            } else {
+                c->l1.push_back(i);
+                b.segmax = std::max(b.segmax, std::max(seg_len(d, 0), seg_len(d, 1)));
+                b.l1maxn = std::max(b.l1maxn, d.n);
+            }
+        }
+        b.l1end = (int)c->l1.size();
+        b.l2end = (int)c->l2.size();
+    }
+}
+
 static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_core, double r_lno, int k_lno,
                                double kappa, double s_fna) {
     const bool rule = kappa >= 0.0;
@@ -428,7 +536,8 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
             if (it != keys.end() && it->first == key[b]) rowblk_member[b] = it->second;
         }
         d.split = d.n >= DCLNO_TEAR_MIN ? d.n / 2 : 0;
-        const long long sm = d.split ? std::max(d.split, d.n - d.split) : d.n;  // longest segment
+        set_tears(c, d);
+        const long long sm = longest_segment(d);
         d.rot_cap = (int)std::min<long long>(3 * sm * sm / 2 + 64 * sm + 64, 2000000000LL);
         d.it_cap = (int)(24 * sm + 64);
         d.eig_off = eig;
@@ -456,7 +565,8 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     // ---- memory admission: per-cluster workspace (doubles): A, L (n x ld each), d/e/tau (ld each),
     // W (32 ld), P ([n][2 mc]), rotation logs (2 rot_cap per segment), for a torn problem the merge
     // matrix and its transpose (n x ld each); 256-byte aligned.  Sweep headers: it_cap ints per segment.
-    auto nseg = [](const ClusterDesc& d) { return d.split ? 2LL : 1LL; };
+    auto nseg = [](const ClusterDesc& d) { return d.split2 ? 4LL : d.split ? 2LL : 1LL; };
+    c->layout_tear = c->tear_mode;
     // the two-stage reduction's chase reflectors (kept until the density rows are written),
     // laid out only when the context is in two-stage mode; it also borrows the merge-matrix
     // area as scratch, so only torn clusters qualify
@@ -467,7 +577,7 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     };
     auto ws_doubles = [&](const ClusterDesc& d) {
         const long long m = 2LL * d.n * d.ld + 35LL * d.ld + 2LL * d.mc * d.ld + 2LL * d.rot_cap * nseg(d) +
-                            (d.split ? 2LL * d.n * d.ld : 0LL) + ((q2_doubles(d) + 3) & ~3LL);
+                            merge_area(d) + ((q2_doubles(d) + 3) & ~3LL);
         return (m + 31) & ~31LL;
     };
     auto ws_bytes = [&](const ClusterDesc& d) { return 8 * ws_doubles(d) + 4LL * d.it_cap * nseg(d); };
@@ -532,7 +642,8 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
             d.cc_off = d.aux_off + 35LL * d.ld;
             d.rot_off = d.cc_off + 2LL * d.mc * d.ld;
             d.m_off = d.rot_off + 2LL * d.rot_cap * nseg(d);
-            d.q2_off = q2_doubles(d) ? d.m_off + (d.split ? 2LL * d.n * d.ld : 0LL) : -1;
+            d.q2_off = q2_doubles(d) ? d.m_off + merge_area(d) : -1;
+            set_problem_offsets(d, i);
             mat += ws_doubles(d);
             d.it_off = its;
             its += (long long)d.it_cap * nseg(d);
@@ -552,6 +663,9 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
         b.mend = b.id_hi < N ? c->cl[b.id_hi].mbeg : (long long)c->mem.size();
         build_buckets(c, b);
     }
+    c->clh.assign(2 * (size_t)N, ClusterDesc{});
+    for (int i = 0; i < N; ++i) make_halves(c, i);
+    build_problem_lists(c);
     c->arena_doubles = (size_t)arena_max;
     c->resident = -1;
     for (size_t k = 0; k < c->batches.size(); ++k) c->batches[k].index = (int)k;
@@ -591,7 +705,13 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     COPY(c->d_voff, voff);
     COPY(c->d_loff, loff);
     COPY(c->d_moff, moff);
-    COPY(c->d_cl, c->cl);
+    {
+        std::vector<ClusterDesc> all(c->cl);
+        all.insert(all.end(), c->clh.begin(), c->clh.end());
+        COPY(c->d_cl, all);
+    }
+    COPY(c->d_l1, c->l1);
+    COPY(c->d_l2, c->l2.empty() ? std::vector<int>{0} : c->l2);
     COPY(c->d_order, c->order);
     COPY(c->d_mem, c->mem);
     COPY(c->d_mem_cl, mem_cl);
@@ -601,7 +721,11 @@ static dclno_status build_impl(dclno_ctx* c, const dclno_system* sys, double r_c
     c->kat.assign(N, k_lno);
     COPY(c->d_kat, c->kat);
     c->layout_split.resize(N);
-    for (int i = 0; i < N; ++i) c->layout_split[i] = c->cl[i].split ? 1 : 0;
+    c->layout_split2.resize(N);
+    for (int i = 0; i < N; ++i) {
+        c->layout_split[i] = c->cl[i].split ? 1 : 0;
+        c->layout_split2[i] = c->cl[i].split2 ? 1 : 0;
+    }
 #undef COPY
     cudaError_t e;
     if ((e = cudaMalloc(&c->d_status, sizeof(int) * N)) != cudaSuccess ||
@@ -681,8 +805,16 @@ dclno_status relayout_clusters(dclno_ctx* c) {
         }
         if (off > d.ld) return set_err(c, DCLNO_ERR_ARG, "LNO counts exceed the laid-out cluster dimension");
         d.n = off;
-        // keep tearing where the layout tore: the segment logs were sized for halves
+        // keep tearing where the layout tore: the segment logs were sized for its segments
         d.split = (c->layout_split[i] && off >= 2) ? off / 2 : 0;
+        d.split2 = 0;
+        d.split1 = d.split3 = 0;
+        if (c->layout_split2[i]) {
+            if (off < 4) return set_err(c, DCLNO_ERR_ARG, "LNO counts leave a cluster torn twice too small");
+            d.split2 = 1;
+            d.split1 = d.split / 2;
+            d.split3 = d.split + (off - d.split) / 2;
+        }
         d.eig_off = eig;
         eig += off;
     }
@@ -691,7 +823,11 @@ dclno_status relayout_clusters(dclno_ctx* c) {
         b.maxn = 0;
         for (int i = b.id_lo; i < b.id_hi; ++i) b.maxn = std::max(b.maxn, c->cl[i].n);
     }
-    DCLNO_CUDA(c, cudaMemcpyAsync(c->d_cl, c->cl.data(), sizeof(ClusterDesc) * c->cl.size(), cudaMemcpyHostToDevice,
+    for (int i = 0; i < c->N; ++i) make_halves(c, i);
+    build_problem_lists(c);
+    std::vector<ClusterDesc> all(c->cl);
+    all.insert(all.end(), c->clh.begin(), c->clh.end());
+    DCLNO_CUDA(c, cudaMemcpyAsync(c->d_cl, all.data(), sizeof(ClusterDesc) * all.size(), cudaMemcpyHostToDevice,
                                   c->stream));
     DCLNO_CUDA(c, cudaMemcpyAsync(c->d_mem, c->mem.data(), sizeof(MemberDesc) * c->mem.size(),
                                   cudaMemcpyHostToDevice, c->stream));
@@ -920,6 +1056,18 @@ extern "C" dclno_status dclno_set_tridiag(dclno_ctx* c, int mode) {
                        "dclno_set_tridiag: the two-stage form keeps its chase reflectors in the cluster workspace, "
                        "laid out by dclno_build_clusters: select mode 2 before building the clusters");
     c->tridiag_mode = mode;
+    return DCLNO_OK;
+}
+
+extern "C" dclno_status dclno_set_tear(dclno_ctx* c, int mode) {
+    if (!c) return DCLNO_ERR_ARG;
+    c->err.clear();
+    if (mode < 0 || mode > 2) return set_err(c, DCLNO_ERR_ARG, "dclno_set_tear: mode must be 0, 1 or 2");
+    if (c->built && mode != c->layout_tear)
+        return set_err(c, DCLNO_ERR_ARG,
+                       "dclno_set_tear: the segments' logs and merge matrices are laid out by dclno_build_clusters: "
+                       "select the tear mode before building the clusters");
+    c->tear_mode = mode;
     return DCLNO_OK;
 }
 

@@ -454,15 +454,7 @@ __device__ __forceinline__ void chase_one(const ClusterDesc* __restrict__ cls, i
         ev[t] = (t + 1 < n) ? A[(size_t)(t + 1) * ld + t] : 0.0;
     }
     __syncwarp();
-    if (d.split && lane == 0) {
-        double* W = dv + 3 * ld;
-        const int k = d.split;
-        const double beta = ev[k - 1];
-        W[n] = beta;
-        ev[k - 1] = 0.0;
-        dv[k - 1] -= fabs(beta);
-        dv[k] -= fabs(beta);
-    }
+    if (lane == 0) tear_cluster(d, arena);
 }
 
 // one warp per cluster: a CTA per cluster, or a persistent grid on the work counter

@@ -40,6 +40,21 @@ struct ClusterDesc {
     long long m_off;    // arena offset of the merge matrix M (n x ld) and its transpose (n x ld); split only
     long long q2_off;   // arena offset of the bulge-chasing reflector log of the two-stage reduction
                         // (band_refl_count(n) slots of DCLNO_BW doubles), -1 if the cluster is too small
+    // Cuppen's tear applied twice (split2): each half [0, split), [split, n) is torn again at
+    // split1 and split3 (absolute positions); the halves' QL, merges, rotation replays and
+    // merge-matrix products run on two half descriptors (see make_halves), the cluster's
+    // own merge then joins the halves.  Half descriptors describe a half's problem with
+    // offsets into the cluster's workspace; kernels that take either kind index the status
+    // word by sidx.
+    int sidx;           // status index: the cluster itself (or, for a half, its cluster)
+    int split2;         // cluster torn twice (real descriptors only)
+    int split1, split3; // the halves' tears (absolute positions), split2 only
+    int x2_mode;        // halves: 0 none; 1 segment 0 also carries its first row; 2 segment 1 its last row
+    int g_row0;         // first row of this problem in the cluster (0, or split for the second half)
+    long long w_off;    // z row of this problem's merge (n doubles) and the tear's beta at [n]
+    long long gb_off;   // the cluster's density-column block G (row stride = columns of G)
+    long long scr_off;  // scratch of the strips' merge-matrix product (n x 2 mc doubles)
+    long long x2_off;   // the carried extra rows, indexed by row of the cluster (x2_mode != 0)
 };
 
 // Two-stage tridiagonalisation: A -> band of half-width DCLNO_BW (blocked Householder,
@@ -67,7 +82,43 @@ __host__ __device__ inline int seg_len(const ClusterDesc& d, int s) {
     return d.split ? (s ? d.n - d.split : d.split) : (s ? 0 : d.n);
 }
 #define DCLNO_TEAR_MIN 64  // tear tridiagonal matrices of at least this dimension
+// tear twice (four segments, two merge levels) in the automatic mode from this dimension on
+#define DCLNO_TEAR2_MIN 384
 #define DCLNO_QL_CANDIDATES 6  // QL lanes per warp tried by the autotuner: 4, 8, 12, 16, 24, 32
+
+// The W rows of a cluster (aux_off + 3 ld, 32 ld doubles) after the reduction, each
+// ld + 4 doubles long (a z row of n <= ld entries and the tear's beta at [n]): row 0 the
+// cluster's merge vector z; rows 1, 2 those of the halves of a cluster torn twice; row 3
+// the halves' carried extra rows.  Later the density columns G and the merge products'
+// scratch reuse the block.
+#define DCLNO_W_HALF0 1
+#define DCLNO_W_HALF1 2
+#define DCLNO_W_X2 3
+__host__ __device__ inline long long w_row(int ld, int r) { return (long long)r * (ld + 4); }
+
+// Cuppen's tear of T at k: T = diag(T1, T2) + |beta| v v^T with beta = e[k-1],
+// v = e_{k-1} + sign(beta) e_k; d[k-1], d[k] are lowered by |beta|, e[k-1] = 0 and
+// beta is kept in *beta_out.
+__host__ __device__ inline void tear_at(double* dv, double* ev, int k, double* beta_out) {
+    const double beta = ev[k - 1];
+    *beta_out = beta;
+    ev[k - 1] = 0.0;
+    dv[k - 1] -= fabs(beta);
+    dv[k] -= fabs(beta);
+}
+// every tear of a cluster (one thread): at split (beta in W row 0 at [n]); for a cluster
+// torn twice also at split1 and split3 (betas at the halves' rows, at the half's length)
+__host__ __device__ inline void tear_cluster(const ClusterDesc& d, double* arena) {
+    if (!d.split) return;
+    double* dv = arena + d.aux_off;
+    double* ev = dv + d.ld;
+    double* W = dv + 3 * (size_t)d.ld;
+    tear_at(dv, ev, d.split, W + d.n);
+    if (d.split2) {
+        tear_at(dv, ev, d.split1, W + w_row(d.ld, DCLNO_W_HALF0) + d.split);
+        tear_at(dv, ev, d.split3, W + w_row(d.ld, DCLNO_W_HALF1) + (d.n - d.split));
+    }
+}
 
 struct MemberDesc {
     int atom;   // j
@@ -151,6 +202,9 @@ struct TunePending {
 struct Batch {
     int id_lo = 0, id_hi = 0;       // clusters [id_lo, id_hi)
     int obeg = 0, oend = 0;         // the same clusters in `order` (by decreasing n)
+    int l1beg = 0, l1end = 0;       // two-segment problems in `l1`: clusters torn once, halves of the others
+    int l2beg = 0, l2end = 0;       // clusters torn twice in `l2` (their merge of the halves)
+    int segmax = 1, l1maxn = 0;     // longest segment, largest problem in l1
     long long mbeg = 0, mend = 0;   // their members
     int maxn = 0, mcmax = 1;
     long long arena_doubles = 0, iters = 0;
@@ -202,6 +256,8 @@ struct dclno_ctx {
     // 1 = one-stage, 2 = two-stage (for the clusters that qualify); solved_two = the form
     // the last solve used (the density pass applies the same Q)
     int tridiag_mode = 0;
+    int tear_mode = 0;        // 0 automatic (twice from DCLNO_TEAR2_MIN), 1 once, 2 twice where possible
+    int layout_tear = -1;     // tear mode when the workspace was laid out
     int layout_mode = -1;     // tridiagonalisation mode when the workspace was laid out (-1: not yet)
     bool solved_two = false;
     // engine of the mixed path's K <= 32 tile products (Cholesky, congruence, one-stage
@@ -227,8 +283,12 @@ struct dclno_ctx {
     size_t pole_bytes = 0;
     std::vector<MemberDesc> mem;
     long long total_dim = 0;
-    ClusterDesc* d_cl = nullptr;
+    ClusterDesc* d_cl = nullptr;  // N cluster descriptors, then 2 N half descriptors
     int* d_order = nullptr;
+    std::vector<ClusterDesc> clh;     // half descriptors (2 per cluster; meaningful where split2)
+    std::vector<int> l1, l2;          // see Batch::l1beg, l2beg (indices into d_cl)
+    int* d_l1 = nullptr;
+    int* d_l2 = nullptr;
     MemberDesc* d_mem = nullptr;
     int* d_mem_cl = nullptr;           // cluster of each member (atom order)
     int* d_pairblk = nullptr;          // per cluster, member pair -> BSR block (or -1)
@@ -264,6 +324,7 @@ struct dclno_ctx {
     int lno_mode = 0;
     long long max_row = 0;              // longest BSR row (blocks)
     std::vector<char> layout_split;     // per cluster: laid out as a torn problem
+    std::vector<char> layout_split2;    // per cluster: laid out as a problem torn twice
 
     // solve / mu
     bool solved = false;

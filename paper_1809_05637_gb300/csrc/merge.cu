@@ -197,13 +197,13 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
                                                       const int* __restrict__ order, double* __restrict__ arena,
                                                       int* __restrict__ status) {
     extern __shared__ double sm[];
-    const int ci = order[blockIdx.x];
+    const ClusterDesc dc = cls[order[blockIdx.x]];
+    const int ci = dc.sidx;
     if (status[ci] != ST_OK) return;
-    const ClusterDesc dc = cls[ci];
     if (!dc.split) return;
     const int n = dc.n, ld = dc.ld, tid = threadIdx.x;
     double* dv = arena + dc.aux_off;
-    const double* zin = dv + 3 * ld;  // W[0, n)
+    const double* zin = arena + dc.w_off;  // z[0, n), beta at [n]
     const double beta = zin[n];
     double* M = arena + dc.m_off;       // row = coordinate, column = eigenpair
     double* MT = M + (size_t)n * ld;    // row = eigenpair
@@ -412,20 +412,59 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
     if (tid == 0 && sFail) status[ci] = ST_NOT_CONVERGED;
 }
 
+// z of the merge of a cluster torn twice (one CTA per cluster): with Q_h = diag(Z_2h,
+// Z_2h+1) M_h the halves' eigenvectors and v = e_{k-1} + sign(beta) e_k at the cluster's
+// tear k, z = diag(Q_0, Q_1)^T v: the first half's part is M_0^T applied to the last row of
+// its second quarter's eigenvectors (carried by QL), the second half's part sign(beta)
+// M_1^T applied to the first row of its first quarter's.
+__global__ void __launch_bounds__(MG_THREADS) k_merge_z2(const ClusterDesc* __restrict__ cls,
+                                                         const int* __restrict__ order, double* __restrict__ arena,
+                                                         const int* __restrict__ status, int nreal) {
+    const int ci = order[blockIdx.x];
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!d.split2) return;
+    const int n = d.n, ld = d.ld, k = d.split;
+    const ClusterDesc h0 = cls[nreal + 2 * ci], h1 = cls[nreal + 2 * ci + 1];
+    double* z = arena + d.w_off;  // z[0, n), beta at [n]
+    const double* x2 = arena + d.x2_off;
+    const double sgn = z[n] < 0.0 ? -1.0 : 1.0;
+    const double* M0 = arena + h0.m_off;  // rows: the half's coordinates, columns: its eigenpairs
+    const double* M1 = arena + h1.m_off;
+    const int q1 = d.split1, q3 = d.split3;  // the first half's second quarter starts at q1, the second
+                                              // half's first quarter ends at q3
+    for (int j = threadIdx.x; j < n; j += MG_THREADS) {
+        double s = 0.0;
+        if (j < k) {
+            for (int r = q1; r < k; ++r) s = fma(M0[(size_t)r * ld + j], x2[r], s);
+        } else {
+            for (int r = k; r < q3; ++r) s = fma(M1[(size_t)(r - k) * ld + (j - k)], x2[r], s);
+            s *= sgn;
+        }
+        z[j] = s;
+    }
+}
+
 dclno_status launch_merge(dclno_ctx* c, const Batch& b) {
-    const int N = b.oend - b.obeg;
-    if (N == 0) return DCLNO_OK;
-    const int* order = c->d_order + b.obeg;
+    const int N1 = b.l1end - b.l1beg, N2 = b.l2end - b.l2beg;
+    if (N1 == 0) return DCLNO_OK;
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
     const size_t sm = (size_t)b.maxn * (10 * sizeof(double) + 6 * sizeof(int) + 3 * sizeof(float));
     if (sm > 227 * 1024) return set_err(c, DCLNO_ERR_ARG, "cluster dimension too large for the merge step");
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    {
-        ProfScope ps__(c, "k_merge");
-        k_merge<<<N, MG_THREADS, sm, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status);
-    }
+    ProfScope ps__(c, "k_merge");
+    // the two-segment problems (clusters torn once, halves of the others), then the halves'
+    // merge of the clusters torn twice
+    const size_t sm1 = (size_t)b.l1maxn * (10 * sizeof(double) + 6 * sizeof(int) + 3 * sizeof(float));
+    k_merge<<<N1, MG_THREADS, sm1, c->stream>>>(c->d_cl, c->d_l1 + b.l1beg, c->d_arena, c->d_status);
     DCLNO_LAUNCHED(c);
+    if (N2 > 0) {
+        k_merge_z2<<<N2, MG_THREADS, 0, c->stream>>>(c->d_cl, c->d_l2 + b.l2beg, c->d_arena, c->d_status, c->N);
+        DCLNO_LAUNCHED(c);
+        k_merge<<<N2, MG_THREADS, sm, c->stream>>>(c->d_cl, c->d_l2 + b.l2beg, c->d_arena, c->d_status);
+        DCLNO_LAUNCHED(c);
+    }
     return DCLNO_OK;
 }

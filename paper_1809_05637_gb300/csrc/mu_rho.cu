@@ -273,7 +273,8 @@ __global__ void k_rho_prep(int id_lo, const ClusterDesc* __restrict__ cls, doubl
 }
 
 // G <- diag(Z1, Z2) G: each segment's logged rotations in reverse order acting on rows
-// (i, i+1).  Work items are (cluster, segment); a warp packs floor(32 / w) items, one
+// (i, i+1).  Work items are (problem, segment) (a cluster torn once, or a half of one
+// torn twice, whose rows of G start at g_row0); a warp packs floor(32 / w) items, one
 // lane per column of G.
 __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, const ClusterDesc* __restrict__ cls,
                              const int* __restrict__ order, double* __restrict__ arena, const int* __restrict__ iters) {
@@ -287,7 +288,7 @@ __global__ void k_replay_rev(int nitems, int per_warp, int w_max, int with_e, co
     const int sg = item & 1;
     const int mc = with_e ? 2 * d.mc : d.mc;  // columns of G
     if (col >= mc || seg_len(d, sg) == 0) return;
-    double* G = arena + d.aux_off + 3 * d.ld + (size_t)seg_start(d, sg) * mc;
+    double* G = arena + d.gb_off + (size_t)(d.g_row0 + seg_start(d, sg)) * mc;
     const double2* rot = reinterpret_cast<const double2*>(arena + d.rot_off) + (size_t)sg * d.rot_cap;
     const int* hdr = iters + d.it_off + (size_t)sg * d.it_cap;
     const int nsw = hdr[0];
@@ -450,9 +451,10 @@ dclno_status launch_density(dclno_ctx* c, const Batch& b, double mu, double kT, 
         ProfScope ps__(c, "k_replay_rev");
         const int wmax = with_e ? 2 * b.mcmax : b.mcmax;
         const int per_warp = std::max(1, 32 / wmax);
-        const int warps = (2 * N + per_warp - 1) / per_warp;
-        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(2 * N, per_warp, wmax, with_e, c->d_cl,
-                                                                      c->d_order + b.obeg, c->d_arena, c->d_iters);
+        const int N1 = b.l1end - b.l1beg;  // two-segment problems (see launch_mgemm)
+        const int warps = (2 * N1 + per_warp - 1) / per_warp;
+        k_replay_rev<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(2 * N1, per_warp, wmax, with_e, c->d_cl,
+                                                                      c->d_l1 + b.l1beg, c->d_arena, c->d_iters);
         DCLNO_LAUNCHED(c);
     }
     // columns per shared-memory chunk of k_rho_qx: at most DCLNO_RPW per warp, within 200 KB

@@ -51,22 +51,39 @@ __global__ void k_poles(const ClusterDesc* __restrict__ cls, const int* __restri
     const int ci = order[blockIdx.x];
     const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ClusterDesc d = cls[ci];
-    __shared__ double tear;
+    __shared__ double tear[3];
+    __shared__ int tk[3];
     __shared__ int refuse;
     if (threadIdx.x == 0) {
         refuse = 0;
-        tear = (status[ci] == ST_OK && d.split) ? arena[d.aux_off + 3 * d.ld + d.n] : 0.0;
+        const double* W = arena + d.aux_off + 3 * (size_t)d.ld;
+        const bool ok = status[ci] == ST_OK && d.split;
+        tk[0] = ok ? d.split : -1;
+        tear[0] = ok ? W[d.n] : 0.0;
+        tk[1] = ok && d.split2 ? d.split1 : -1;
+        tear[1] = ok && d.split2 ? W[w_row(d.ld, DCLNO_W_HALF0) + d.split] : 0.0;
+        tk[2] = ok && d.split2 ? d.split3 : -1;
+        tear[2] = ok && d.split2 ? W[w_row(d.ld, DCLNO_W_HALF1) + (d.n - d.split)] : 0.0;
     }
     __syncthreads();
     if (status[ci] != ST_OK) return;
-    const int n = d.n, ld = d.ld, mc = d.mc, k = d.split;
+    const int n = d.n, ld = d.ld, mc = d.mc;
     const double* dv = arena + d.aux_off;
     const double* ev = dv + ld;
     const double* P = arena + d.cc_off;  // [n][2 mc]: P1 = columns 0 .. mc-1
-    double* G = arena + d.aux_off + 3 * ld;  // [n][mc] out (overlaps the tear's beta, read above)
-    // T before Cuppen's tear (d[k-1], d[k] lowered by |beta|, e[k-1] = 0 after it)
-    auto dt = [&](int t) { return dv[t] + ((k && (t == k - 1 || t == k)) ? fabs(tear) : 0.0); };
-    auto et = [&](int t) { return (k && t == k - 1) ? tear : ev[t]; };
+    double* G = arena + d.aux_off + 3 * ld;  // [n][mc] out (overlaps the tears' betas, read above)
+    // T before Cuppen's tears (at each tear k: d[k-1], d[k] lowered by |beta|, e[k-1] = 0)
+    auto dt = [&](int t) {
+        double v = dv[t];
+        for (int q = 0; q < 3; ++q)
+            if (tk[q] > 0 && (t == tk[q] - 1 || t == tk[q])) v += fabs(tear[q]);
+        return v;
+    };
+    auto et = [&](int t) {
+        for (int q = 0; q < 3; ++q)
+            if (tk[q] > 0 && t == tk[q] - 1) return tear[q];
+        return ev[t];
+    };
     // Gershgorin bound of |T - mu| against the first omitted pole
     double rad = 0.0;
     for (int t = lane; t < n; t += 32)

@@ -352,18 +352,10 @@ __device__ __forceinline__ void tridiag_one(const ClusterDesc* __restrict__ cls,
         }
     }
     if (EMU == 2 && tcs->failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
-    // Cuppen's tear: T = diag(T1, T2) + |beta| v v^T with beta = e[k-1], v = e_{k-1} + sign(beta) e_k;
-    // T1 and T2 (d[k-1], d[k] lowered by |beta|) are solved as separate QL segments and merged
-    // afterwards (k_merge).  beta is kept in W[n].
+    // Cuppen's tear (tear_cluster): the segments are solved by QL and merged afterwards
+    // (k_merge; for a cluster torn twice the halves first)
     __syncthreads();
-    if (d.split && threadIdx.x == 0) {
-        const int k = d.split;
-        const double beta = ev[k - 1];
-        W[n] = beta;
-        ev[k - 1] = 0.0;
-        dv[k - 1] -= fabs(beta);
-        dv[k] -= fabs(beta);
-    }
+    if (threadIdx.x == 0) tear_cluster(d, arena);
 }
 
 template <int EMU>
@@ -401,26 +393,33 @@ __device__ __forceinline__ bool negligible(double e, double d0, double d1) {
     return exp_bits(e) + 53 <= ed;
 }
 
+template <bool X2>
 __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const ClusterDesc* __restrict__ cls,
                                            const int* __restrict__ order, double* __restrict__ arena,
                                            int* __restrict__ iters, int* __restrict__ status) {
     extern __shared__ double sm[];
-    // lane = (cluster, segment); the lane's d, e and z row live in shared memory (segp each)
+    // lane = (problem, segment); the lane's d, e, z row and extra row live in shared memory
+    // (segp each).  A problem is a cluster torn once or a half of a cluster torn twice.
     const int t = blockIdx.x * lanes + threadIdx.x;
-    int phase = QL_DONE, n = 0, ci = -1;
-    double* d = sm + (size_t)threadIdx.x * 3 * segp;
+    int phase = QL_DONE, n = 0, si = -1;
+    // X2 when the problems include halves (their extra rows: four arrays per lane, else
+    // three; shared memory per lane bounds how many QL chains an SM holds)
+    constexpr int narr = X2 ? 4 : 3;
+    double* d = sm + (size_t)threadIdx.x * narr * segp;
     double* e = d + segp;
-    double* x = e + segp;  // z row of a torn problem: v diag(Z1, Z2) restricted to this segment
-    double* dg = nullptr;  // the segment's d in global memory (eigenvalues out)
-    double* zg = nullptr;  // the segment's part of z in W (torn problems only)
+    double* x = e + segp;   // z row of a torn problem: v diag(Z1, Z2) restricted to this segment
+    double* x2 = x + segp;  // the extra row a half carries for its cluster's merge (narr = 4)
+    double* dg = nullptr;   // the segment's d in global memory (eigenvalues out)
+    double* zg = nullptr;   // the segment's part of z (torn problems only)
+    double* x2g = nullptr;  // the segment's extra row out (halves only)
     double2* rot = nullptr;
     int* hdr = nullptr;
     int rot_cap = 0, sw_cap = 0;
     if (threadIdx.x < lanes && t < 2 * ncl) {
-        ci = order[t >> 1];
+        const ClusterDesc dsc = cls[order[t >> 1]];
         const int sg = t & 1;
-        if (status[ci] == ST_OK) {
-            const ClusterDesc dsc = cls[ci];
+        si = dsc.sidx;
+        if (status[si] == ST_OK) {
             n = seg_len(dsc, sg);
             if (n > 0) {
                 dg = arena + dsc.aux_off + seg_start(dsc, sg);
@@ -430,11 +429,17 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
                     x[k] = 0.0;
                 }
                 if (dsc.split) {
-                    // v = e_{k-1} + sign(beta) e_k, beta kept by k_tridiag in W[n]
-                    double* W = arena + dsc.aux_off + 3 * dsc.ld;
+                    // v = e_{k-1} + sign(beta) e_k, beta kept by the tear at [n] of the z row
+                    double* W = arena + dsc.w_off;
                     zg = W + seg_start(dsc, sg);
                     if (sg == 0) x[n - 1] = 1.0;
                     else x[0] = (W[dsc.n] < 0.0) ? -1.0 : 1.0;
+                }
+                if (X2 && ((dsc.x2_mode == 1 && sg == 0) || (dsc.x2_mode == 2 && sg == 1))) {
+                    // e_first of the second half's first segment, e_last of the first half's second
+                    x2g = arena + dsc.x2_off + dsc.g_row0 + seg_start(dsc, sg);
+                    for (int k = 0; k < n; ++k) x2[k] = 0.0;
+                    x2[dsc.x2_mode == 1 ? 0 : n - 1] = 1.0;
                 }
                 rot = reinterpret_cast<double2*>(arena + dsc.rot_off) + (size_t)sg * dsc.rot_cap;
                 hdr = iters + dsc.it_off + (size_t)sg * dsc.it_cap;
@@ -448,6 +453,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
     }
     int l = 0, m = 0, mm = 0, i = 0, it = 0, nrot = 0, nsw = 0, start = 0;
     double zx1 = 0.0;  // z row: value of the row the sweep carries (crow), updated with each rotation
+    double zx2 = 0.0;  // the same for the extra row
     int crow = 0;
     // the two smallest indices in [l, m] whose e is negligible after this sweep (m counts
     // as negligible): the next unreduced block is known without scanning e again
@@ -499,6 +505,11 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
                 zx1 = fma(c, xi, -s * zx1);
                 crow = i;
             }
+            if (X2 && x2g) {
+                const double xi = x2[i];
+                x2[i + 1] = fma(s, xi, c * zx2);
+                zx2 = fma(c, xi, -s * zx2);
+            }
             // deflation bookkeeping for the next sweep: e[i+1], d[i+1], d[i+2] are final now
             if (i + 1 < m && negligible(r, dn, dnext)) {
                 low2 = lowneg;
@@ -527,6 +538,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
         }
         if (phase == QL_FIN) {
             x[crow] = zx1;
+            if (X2 && x2g) x2[crow] = zx2;
             hdr[1 + 3 * nsw] = start;
             hdr[2 + 3 * nsw] = m - 1;
             hdr[3 + 3 * nsw] = nrot - start;
@@ -573,11 +585,11 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
         }
         if (phase == QL_START) {
             if (++it > 60) {
-                status[ci] = ST_NOT_CONVERGED;
+                status[si] = ST_NOT_CONVERGED;
                 hdr[0] = nsw;
                 phase = QL_DONE;
             } else if (nsw >= sw_cap || nrot + (m - l) > rot_cap) {
-                status[ci] = ST_LOG_FULL;
+                status[si] = ST_LOG_FULL;
                 hdr[0] = nsw;
                 phase = QL_DONE;
             } else {
@@ -593,6 +605,7 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
                 lowneg = m;
                 low2 = m;
                 zx1 = x[m];
+                if (X2 && x2g) zx2 = x2[m];
                 crow = m;
                 ce = e[i];
                 cd0 = d[i];
@@ -609,6 +622,8 @@ __global__ void __launch_bounds__(32) k_ql(int ncl, int lanes, int segp, const C
     for (int k = 0; k < n; ++k) dg[k] = d[k];
     if (zg)
         for (int k = 0; k < n; ++k) zg[k] = x[k];
+    if (X2 && x2g)
+        for (int k = 0; k < n; ++k) x2g[k] = x2[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -692,9 +707,10 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS) k_apply_q_rows(const Clus
 }
 
 // P <- P diag(Z1, Z2) by the logged rotations of each segment.  Work items are
-// (cluster, segment, strip) with strip 0 = the mc rows of R1 and strip 1 = the mc
-// rows of R2; a warp packs floor(32 / mc) items, one lane per row, so one FP64
-// instruction updates the rows of several clusters.
+// (problem, segment, strip) with strip 0 = the mc rows of R1 and strip 1 = the mc
+// rows of R2 (a problem: a cluster torn once or a half of one torn twice); a warp packs
+// floor(32 / mc) items, one lane per row, so one FP64 instruction updates the rows of
+// several clusters.
 __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const ClusterDesc* __restrict__ cls,
                              const int* __restrict__ order, double* __restrict__ arena,
                              const int* __restrict__ iters, const int* __restrict__ status) {
@@ -704,9 +720,8 @@ __global__ void k_replay_fwd(int nitems, int per_warp, int mc_max, const Cluster
     if (grp >= per_warp) return;
     const int item = wid * per_warp + grp;
     if (item >= nitems) return;
-    const int ci = order[item >> 2];
-    if (status[ci] != ST_OK) return;
-    const ClusterDesc d = cls[ci];
+    const ClusterDesc d = cls[order[item >> 2]];
+    if (status[d.sidx] != ST_OK) return;
     const int sg = (item >> 1) & 1;
     if (row >= d.mc || seg_len(d, sg) == 0) return;
     const int w2 = 2 * d.mc;
@@ -774,16 +789,16 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
                                                                int* __restrict__ status, int dir, int with_e) {
     extern __shared__ double sm[];
     __shared__ TcState tcs;
-    const int ci = order[blockIdx.x];
+    const ClusterDesc d = cls[order[blockIdx.x]];
+    const int ci = d.sidx;
     if (status[ci] != ST_OK) return;
-    const ClusterDesc d = cls[ci];
     if (!d.split) return;
     const int n = d.n, ld = d.ld;
     const int w = (dir == 0 || with_e) ? 2 * d.mc : d.mc;
     double* M = arena + d.m_off;
     double* MT = M + (size_t)n * ld;
-    double* Y = (dir == 0) ? arena + d.cc_off : arena + d.aux_off + 3 * ld;
-    double* Bt = (dir == 0) ? arena + d.aux_off + 3 * ld : MT;
+    double* Y = (dir == 0) ? arena + d.cc_off : arena + d.gb_off + (size_t)d.g_row0 * w;
+    double* Bt = (dir == 0) ? arena + d.scr_off : MT;
     const double* X = (dir == 0) ? MT : M;
     if constexpr (EMU == 0) {
         for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Bt[e] = Y[e];
@@ -791,43 +806,58 @@ __global__ void __launch_bounds__(DCLNO_SOLVE_THREADS, 2) k_mgemm(const ClusterD
         tall_gemm_fp64(Y, X, ld, Bt, n, w);
         return;
     } else {
+    // -Y^T staged with row stride bst: n rounded up to 4 in the scratch (w x bst doubles: the
+    // two halves of a cluster torn twice use disjoint parts of its W block), ld in MT
+    const int bst = (dir == 0) ? ((n + 3) & ~3) : ld;
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) {
         const int t = (int)(e / w), a = (int)(e % w);
-        Bt[(size_t)a * ld + t] = -Y[e];
+        Bt[(size_t)a * bst + t] = -Y[e];
     }
     __syncthreads();
     for (size_t e = threadIdx.x; e < (size_t)n * w; e += blockDim.x) Y[e] = 0.0;
     __syncthreads();
     ENGINE_BEGIN(EMU, &tcs);
     if constexpr (EMU == 2)
-        cta_gemm_tc_longk<false>(Y, w, X, ld, Bt, ld, n, w, n, reinterpret_cast<unsigned char*>(sm), &tcs);
+        cta_gemm_tc_longk<false>(Y, w, X, ld, Bt, bst, n, w, n, reinterpret_cast<unsigned char*>(sm), &tcs);
     else
-        tile_update_longk<EMU>(Y, w, X, ld, Bt, ld, n, w, n, sm, &tcs);
+        tile_update_longk<EMU>(Y, w, X, ld, Bt, bst, n, w, n, sm, &tcs);
     ENGINE_END(EMU, &tcs);
     if (EMU == 2 && tcs.failed && threadIdx.x == 0) status[ci] = ST_TIMEOUT;
     }
 }
 
 template <int EMU>
-static dclno_status launch_mgemm_t(dclno_ctx* c, const Batch& b, int N, int dir, int with_e) {
+static dclno_status launch_mgemm_t(dclno_ctx* c, const int* list, int N, int dir, int with_e) {
+    if (N == 0) return DCLNO_OK;
     const size_t smb = EMU ? (size_t)ENGINE_SMEM_BYTES(EMU) : 0;
     DCLNO_CUDA(c, cudaFuncSetAttribute(k_mgemm<EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-    k_mgemm<EMU><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, c->d_order + b.obeg, c->d_arena, c->d_status,
-                                                             dir, with_e);
+    k_mgemm<EMU><<<N, DCLNO_SOLVE_THREADS, smb, c->stream>>>(c->d_cl, list, c->d_arena, c->d_status, dir, with_e);
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
 
+// Y <- merge matrices of a batch: the two-segment problems' (clusters torn once and the
+// halves of clusters torn twice), then the halves' merge of the clusters torn twice;
+// dir 0 (strips, P <- M^T P) in that order, dir 1 (density columns, G <- M G) reversed
 dclno_status launch_mgemm(dclno_ctx* c, const Batch& b, int dir, int with_e, int emu) {
-    const int N = b.oend - b.obeg;
-    if (N == 0) return DCLNO_OK;
+    const int N1 = b.l1end - b.l1beg, N2 = b.l2end - b.l2beg;
     bool any = false;
     for (int i = b.id_lo; i < b.id_hi; ++i) any = any || c->cl[i].split;
     if (!any) return DCLNO_OK;
     ProfScope ps__(c, dir == 0 ? "k_mgemm_fwd" : "k_mgemm_rev");
-    if (emu == 2) return launch_mgemm_t<2>(c, b, N, dir, with_e);
-    if (emu == 1) return launch_mgemm_t<1>(c, b, N, dir, with_e);
-    return launch_mgemm_t<0>(c, b, N, dir, with_e);
+    const int* l1 = c->d_l1 + b.l1beg;
+    const int* l2 = c->d_l2 + b.l2beg;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool first = (pass == 0) == (dir == 0);
+        const int* list = first ? l1 : l2;
+        const int n = first ? N1 : N2;
+        dclno_status st;
+        if (emu == 2) st = launch_mgemm_t<2>(c, list, n, dir, with_e);
+        else if (emu == 1) st = launch_mgemm_t<1>(c, list, n, dir, with_e);
+        else st = launch_mgemm_t<0>(c, list, n, dir, with_e);
+        if (st != DCLNO_OK) return st;
+    }
+    return DCLNO_OK;
 }
 
 // eigenvalues and weights: eps_mu = d_mu, q_mu = sum_a P[mu][a] P[mu][mc + a]
@@ -849,11 +879,17 @@ __global__ void k_weights(const ClusterDesc* __restrict__ cls, const int* __rest
 }
 
 
-static dclno_status launch_ql(dclno_ctx* c, const int* order, int N, int segp, int lanes) {
-    const size_t smq = (size_t)lanes * 3 * segp * sizeof(double);
-    DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
-    k_ql<<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
-                                                             c->d_iters, c->d_status);
+static dclno_status launch_ql(dclno_ctx* c, const int* order, int N, int segp, int narr, int lanes) {
+    const size_t smq = (size_t)lanes * narr * segp * sizeof(double);
+    if (narr == 4) {
+        DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+        k_ql<true><<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
+                                                                       c->d_iters, c->d_status);
+    } else {
+        DCLNO_CUDA(c, cudaFuncSetAttribute(k_ql<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+        k_ql<false><<<(2 * N + lanes - 1) / lanes, 32, smq, c->stream>>>(N, lanes, segp, c->d_cl, order, c->d_arena,
+                                                                        c->d_iters, c->d_status);
+    }
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
@@ -881,7 +917,7 @@ __global__ void k_save_de(const ClusterDesc* __restrict__ cls, const int* __rest
 // count depends on the cluster count and segment lengths; each candidate is timed
 // once on this batch's own tridiagonal matrices (d and e restored before each try;
 // every lane's arithmetic is the same whatever the grouping, so the results are too).
-static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int N, int segp, int fit) {
+static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int N, int segp, int narr, int fit) {
     static const int cand[DCLNO_QL_CANDIDATES] = {4, 8, 12, 16, 24, 32};
     int ldmax = 0;
     for (int i = b.id_lo; i < b.id_hi; ++i) ldmax = std::max(ldmax, c->cl[i].n);
@@ -907,7 +943,7 @@ static dclno_status tune_ql(dclno_ctx* c, const Batch& b, const int* order, int 
         k_save_de<<<N, 128, 0, c->stream>>>(c->d_cl, order, c->d_arena, c->d_tune, stride, 1);
         c->launches++;
         cudaEventRecord(e0, c->stream);
-        st = launch_ql(c, order, N, segp, cand[k]);
+        st = launch_ql(c, order, N, segp, narr, cand[k]);
         cudaEventRecord(e1, c->stream);
         float ms = 0.0f;
         if (st == DCLNO_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
@@ -1015,20 +1051,22 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only,
         DCLNO_LAUNCHED(c);
         return DCLNO_OK;  // statuses are read by the caller after the pole sum
     }
+    // the two-segment problems: clusters torn once (or not at all), halves of those torn twice
+    const int* l1 = c->d_l1 + b.l1beg;
+    const int N1 = b.l1end - b.l1beg;
     {
-        int segmax = 1;
-        for (int i = b.id_lo; i < b.id_hi; ++i) segmax = std::max(segmax, std::max(seg_len(c->cl[i], 0), seg_len(c->cl[i], 1)));
-        const int segp = segmax | 1;  // odd: lanes' arrays start in different banks
-        const int fit = (int)std::min<long long>(32, (200LL * 1024) / (24LL * segp));  // shared memory bound
+        const int segp = b.segmax | 1;  // odd: lanes' arrays start in different banks
+        const int narr = b.l2end > b.l2beg ? 4 : 3;
+        const int fit = (int)std::min<long long>(32, (200LL * 1024) / (8LL * narr * segp));  // shared memory bound
         if (fit < 1) return set_err(c, DCLNO_ERR_ARG, "tridiagonal segment too long for the QL kernel");
         int& lanes = c->ql_lanes[b.index];
         if (lanes == 0 && c->autotune && !c->deferred) {
-            const dclno_status st = tune_ql(c, b, order, N, segp, fit);
+            const dclno_status st = tune_ql(c, b, l1, N1, segp, narr, fit);
             if (st != DCLNO_OK) return st;
         }
         const int use = lanes > 0 ? std::min(lanes, fit) : fit;
         ProfScope ps__(c, "k_ql");
-        const dclno_status st = launch_ql(c, order, N, segp, use);
+        const dclno_status st = launch_ql(c, l1, N1, segp, narr, use);
         if (st != DCLNO_OK) return st;
     }
     {
@@ -1045,9 +1083,9 @@ static dclno_status launch_solve(dclno_ctx* c, const Batch& b, bool reduce_only,
         ProfScope ps__(c, "k_replay_fwd");
         const int mcmax = b.mcmax;
         const int per_warp = std::max(1, 32 / mcmax);
-        const int items = 4 * N;
+        const int items = 4 * N1;
         const int warps = (items + per_warp - 1) / per_warp;
-        k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, order,
+        k_replay_fwd<<<(warps * 32 + 127) / 128, 128, 0, c->stream>>>(items, per_warp, mcmax, c->d_cl, l1,
                                                                       c->d_arena, c->d_iters, c->d_status);
     }
     DCLNO_LAUNCHED(c);

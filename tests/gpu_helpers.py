@@ -9,14 +9,16 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
 
 
-def gpu_context(s, r_core, r_lno, k_lno, H=None, S=None, tridiag=None):
-    """A context with the system's clusters built; tridiag (if given) is selected before
-    the build (the two-stage form lays out its reflector log there)."""
+def gpu_context(s, r_core, r_lno, k_lno, H=None, S=None, tridiag=None, tear=None):
+    """A context with the system's clusters built; tridiag and tear (if given) are
+    selected before the build (the layout depends on both)."""
     H = to_dev(s.H) if H is None else H
     S = to_dev(s.S) if S is None else S
     ctx = Context()
     if tridiag is not None:
         ctx.set_tridiag(tridiag)
+    if tear is not None:
+        ctx.set_tear(tear)
     ctx.build_clusters(s.pos, s.cell, s.pbc, s.norb, s.row_ptr, s.col, s.shift, s.blk_off, H, S,
                        r_core, r_lno, k_lno)
     return ctx
