@@ -217,7 +217,7 @@ dclno_status dclno_set_tridiag(dclno_ctx *ctx, int mode);
  * each half is torn again at its middle: four QL chains of about a quarter of the
  * rotations each, two merges of halves, then the merge of the halves.  The results
  * are the same eigenpairs up to rounding.
- *   0  automatic (default): twice for clusters of dimension >= 384, once below;
+ *   0  automatic (default): twice for clusters of dimension >= 512, once below;
  *   1  once;
  *   2  twice for every torn cluster (dimension >= 64).
  * The segments' rotation logs and the merge matrices are laid out by

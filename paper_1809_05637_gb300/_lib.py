@@ -237,7 +237,7 @@ class Context:
         self._check(self.lib.dclno_set_schedule(self.h, int(mode)))
 
     def set_tear(self, mode):
-        """Cuppen's tear: 0 automatic (twice from dimension 384), 1 once, 2 twice (from 64); before the build."""
+        """Cuppen's tear: 0 automatic (twice from dimension 512), 1 once, 2 twice (from 64); before the build."""
         self._check(self.lib.dclno_set_tear(self.h, int(mode)))
 
     def set_bucket_min(self, count):

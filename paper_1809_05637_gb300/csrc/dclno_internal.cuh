@@ -83,7 +83,7 @@ __host__ __device__ inline int seg_len(const ClusterDesc& d, int s) {
 }
 #define DCLNO_TEAR_MIN 64  // tear tridiagonal matrices of at least this dimension
 // tear twice (four segments, two merge levels) in the automatic mode from this dimension on
-#define DCLNO_TEAR2_MIN 384
+#define DCLNO_TEAR2_MIN 512
 #define DCLNO_QL_CANDIDATES 6  // QL lanes per warp tried by the autotuner: 4, 8, 12, 16, 24, 32
 
 // The W rows of a cluster (aux_off + 3 ld, 32 ld doubles) after the reduction, each

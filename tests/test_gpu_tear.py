@@ -2,7 +2,7 @@
 halves merged: dclno_set_tear), in both precisions and both tridiagonalisation forms,
 against the oracle (which diagonalises each cluster whole); the pole form of the
 density undoes all three tears.  The full-size workloads take the automatic mode,
-which tears clusters of dimension >= 384 twice (tests/test_gpu_workload_cfg2.py)."""
+which tears clusters of dimension >= 512 twice (tests/test_gpu_workload_cfg2.py)."""
 import numpy as np
 import pytest
 
