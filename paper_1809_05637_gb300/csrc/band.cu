@@ -350,10 +350,19 @@ __device__ static void chase_two_sided(double* A, int ld, int p, int len, const 
     const double y = h.tau * (y0 + y1);
     const double dot = warp_sum(lane < len ? h.v * y : 0.0);
     const double w = y - 0.5 * h.tau * dot * h.v;
-    for (int i = 0; i < len; ++i) {
-        const double vi = __shfl_sync(0xffffffffu, h.v, i), wi = __shfl_sync(0xffffffffu, w, i);
-        if (lane <= i) A[(size_t)(p + i) * ld + p + lane] = Ds[i * TL + lane] - vi * w - wi * h.v;
+    // D - v w^T - w v^T on the lower triangle: the off-diagonal elements of rows i and
+    // len-1-i share a warp instruction (i + (len-1-i) lanes), then the diagonal; every
+    // FP64 instruction then updates up to 31 elements instead of i + 1
+    for (int i = 0; 2 * i < len; ++i) {
+        const int r2 = len - 1 - i;
+        const bool first = lane < i;
+        const int row = first ? i : r2, col = first ? lane : lane - i;
+        const bool on = first || (r2 > i && col < r2);
+        const double vr = __shfl_sync(0xffffffffu, h.v, row), wr = __shfl_sync(0xffffffffu, w, row);
+        const double vc = __shfl_sync(0xffffffffu, h.v, col & 31), wc = __shfl_sync(0xffffffffu, w, col & 31);
+        if (on) A[(size_t)(p + row) * ld + p + col] = Ds[row * TL + col] - vr * wc - wr * vc;
     }
+    if (lane < len) A[(size_t)(p + lane) * ld + p + lane] = Ds[lane * TL + lane] - h.v * w - w * h.v;
     __syncwarp();
 }
 
