@@ -107,16 +107,29 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
     int o;
     double lo, hi, tau;
     SecVal v;
+    SecValF vf;
     if (j < K - 1) {
         const double gap = dk[j + 1] - dk[j];
         const double mid = 0.5 * gap;
-        v = sec_eval(K, dk, w, j, mid, j);
-        if (1.0 + v.psi + v.phi >= 0.0) {  // root in (d_j, mid]: origin d_j
+        // the side of the midpoint from the FP32 sums when their sign is certain (|f|
+        // well above their rounding bound, K + 8 terms of 2^-23 relative each, sum |t|
+        // = phi - psi at the midpoint), else from the FP64 sums
+        vf = sec_eval_f(K, dh, dl, wf, j, (float)mid, j);
+        const float f32 = 1.0f + vf.psi + vf.phi;
+        bool up;
+        if (fabsf(f32) > 8.0f * (float)(K + 8) * 5.96e-8f * (1.0f + vf.phi - vf.psi)) {
+            up = f32 >= 0.0f;
+        } else {
+            v = sec_eval(K, dk, w, j, mid, j);
+            up = 1.0 + v.psi + v.phi >= 0.0;
+            vf = {(float)v.psi, (float)v.dpsi, (float)v.phi, (float)v.dphi};
+        }
+        if (up) {  // root in (d_j, mid]: origin d_j
             o = j;
             lo = 0.0;
             hi = mid;
             tau = mid;
-        } else {                            // root in (mid, d_{j+1}): origin d_{j+1}
+        } else {   // root in (mid, d_{j+1}): origin d_{j+1}
             o = j + 1;
             lo = mid - gap;
             hi = 0.0;
@@ -127,13 +140,12 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
         lo = 0.0;
         hi = wsum;  // f(d_K + sum w) >= 0
         tau = 0.5 * wsum;
-        v = sec_eval(K, dk, w, o, tau, j);
+        vf = sec_eval_f(K, dh, dl, wf, o, (float)tau, j);
     }
-    // up to three model steps on the FP32 preview, from the FP64 value at the start;
-    // the FP64 iteration below then starts where they end (if that lies in its bracket)
+    // up to three model steps on the FP32 preview from the start; the FP64 iteration
+    // below then starts where they end (if that lies in its bracket)
     {
         float tf = (float)tau, lof = (float)lo, hif = (float)hi;
-        SecValF vf = {(float)v.psi, (float)v.dpsi, (float)v.phi, (float)v.dphi};
         const float dpj = (float)(dk[j] - dk[o]);
         const float dqj = (j < K - 1) ? (float)(dk[j + 1] - dk[o]) : 0.f;
         for (int s = 0; s < 3; ++s) {
@@ -158,10 +170,8 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
             tf = tn;
         }
         const double ts = (double)tf;
-        if (ts > lo && ts < hi && ts != tau) {
-            tau = ts;
-            v = sec_eval(K, dk, w, o, tau, j);
-        }
+        if (ts > lo && ts < hi) tau = ts;
+        v = sec_eval(K, dk, w, o, tau, j);
     }
     int it = 0;
     for (; it < 100; ++it) {
