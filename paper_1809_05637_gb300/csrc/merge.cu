@@ -30,11 +30,16 @@ struct SecVal {
     double psi, dpsi, phi, dphi, abs;
 };
 
-__device__ static SecVal sec_eval(int K, const double* dk, const double* w, int o, double tau, int j) {
+// The reciprocals 1 / (d_i - lam) are also stored in the root's column of the merge
+// matrix (rcol[kidx[i] * ld]): the last evaluation is at the converged root, where they
+// are the eigenvector's entries up to the factor z_i.
+__device__ static SecVal sec_eval(int K, const double* dk, const double* w, int o, double tau, int j, double* rcol,
+                                  int ld, const int* kidx) {
     SecVal v = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double dorg = dk[o];
     for (int i = 0; i <= j; ++i) {
         const double r = 1.0 / ((dk[i] - dorg) - tau);
+        rcol[(size_t)kidx[i] * ld] = r;
         const double t = w[i] * r;
         v.psi += t;
         v.dpsi = fma(t, r, v.dpsi);
@@ -42,6 +47,7 @@ __device__ static SecVal sec_eval(int K, const double* dk, const double* w, int 
     }
     for (int i = j + 1; i < K; ++i) {
         const double r = 1.0 / ((dk[i] - dorg) - tau);
+        rcol[(size_t)kidx[i] * ld] = r;
         const double t = w[i] * r;
         v.phi += t;
         v.dphi = fma(t, r, v.dphi);
@@ -102,7 +108,8 @@ __device__ static T quad_root_in(T A, T B, T C, T lo, T hi) {
 // Root j of 1 + sum_i w_i/(d_i - lam) = 0 (d ascending, w > 0, wsum = sum w):
 // lam = d_o + tau.  Returns the number of iterations (> 100: not converged).
 __device__ static int sec_root(int K, const double* dk, const double* w, const float* dh, const float* dl,
-                               const float* wf, double wsum, int j, double& tau_out, int& org_out) {
+                               const float* wf, double wsum, int j, double& tau_out, int& org_out, double* rcol,
+                               int ld, const int* kidx) {
     const double u = 1.1102230246251565e-16;  // 2^-53
     int o;
     double lo, hi, tau;
@@ -120,7 +127,7 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
         if (fabsf(f32) > 8.0f * (float)(K + 8) * 5.96e-8f * (1.0f + vf.phi - vf.psi)) {
             up = f32 >= 0.0f;
         } else {
-            v = sec_eval(K, dk, w, j, mid, j);
+            v = sec_eval(K, dk, w, j, mid, j, rcol, ld, kidx);
             up = 1.0 + v.psi + v.phi >= 0.0;
             vf = {(float)v.psi, (float)v.dpsi, (float)v.phi, (float)v.dphi};
         }
@@ -171,7 +178,7 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
         }
         const double ts = (double)tf;
         if (ts > lo && ts < hi) tau = ts;
-        v = sec_eval(K, dk, w, o, tau, j);
+        v = sec_eval(K, dk, w, o, tau, j, rcol, ld, kidx);
     }
     int it = 0;
     for (; it < 100; ++it) {
@@ -196,7 +203,7 @@ __device__ static int sec_root(int K, const double* dk, const double* w, const f
         if (!(tn > lo && (tn < hi || (j == K - 1 && tn == hi)))) tn = 0.5 * (lo + hi);
         if (tn == tau) break;
         tau = tn;
-        v = sec_eval(K, dk, w, o, tau, j);
+        v = sec_eval(K, dk, w, o, tau, j, rcol, ld, kidx);
     }
     tau_out = tau;
     org_out = o;
@@ -349,11 +356,14 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
         sWsum = s;
     }
     __syncthreads();
-    // secular roots
+    // M = 0; the secular roots (each root's last evaluation leaves 1 / (d_i - lam_j) in
+    // column j of M)
+    for (size_t e = tid; e < (size_t)n * ld; e += MG_THREADS) M[e] = 0.0;
+    __syncthreads();
     for (int j = tid; j < K; j += MG_THREADS) {
         double t;
         int o;
-        if (sec_root(K, dk, w, dhf, dlf, wff, sWsum, j, t, o) > 100) sFail = 1;
+        if (sec_root(K, dk, w, dhf, dlf, wff, sWsum, j, t, o, M + j, ld, kidx) > 100) sFail = 1;
         tau[j] = t;
         org[j] = o;
     }
@@ -379,16 +389,16 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge(const ClusterDesc* __restr
         const double prod = ldexp(pn / pd, en - ed);
         zh[i] = copysign(sqrt(fmax(prod, 0.0)), zk[i]);
     }
-    // M = 0
-    for (size_t e = tid; e < (size_t)n * ld; e += MG_THREADS) M[e] = 0.0;
     __syncthreads();
-    // root columns: u_j = (z_i / (d_i - lam_j))_i at the non-deflated coordinates
+    // root columns: u_j = (z_i / (d_i - lam_j))_i at the non-deflated coordinates, from the
+    // reciprocals the roots' last evaluations left in M
     for (int j = tid; j < K; j += MG_THREADS) {
         const double dj = dk[org[j]], tj = tau[j];
         double s = 0.0;
         for (int i = 0; i < K; ++i) {
-            const double uij = zh[i] / ((dk[i] - dj) - tj);
-            M[(size_t)kidx[i] * ld + j] = uij;
+            double* mij = M + (size_t)kidx[i] * ld + j;
+            const double uij = zh[i] * *mij;
+            *mij = uij;
             s = fma(uij, uij, s);
         }
         nrm[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
