@@ -500,7 +500,6 @@ def roofline_report(kernel, path, n, k_ms, k_n, dfma, dmma, bf16, bf16_src):
 TRAFFIC_PER_CLUSTER = {
     ("k_tridiag", "fp64"): (83441013504 + 7083535104) / 216,
     ("k_band", "mixed"): (15157292800 + 10908427520) / 216,
-    ("k_chase", "mixed"): (519777792 + 6987047936) / 216,
 }
 
 TUNE_STEPS = 4  # eager solves the schedule tuner needs to decide (its largest candidate set)
