@@ -27,6 +27,7 @@
 // used until after the tridiagonal eigensolve, is k_band's scratch.
 #include "dclno_internal.cuh"
 #include "emu_gemm.cuh"
+#include "df32.cuh"
 
 #define BW DCLNO_BW
 #define TL (BW + 1)  // row stride of the BW x BW shared-memory blocks
@@ -466,8 +467,275 @@ __device__ __forceinline__ void chase_one(const ClusterDesc* __restrict__ cls, i
     if (lane == 0) tear_cluster(d, arena);
 }
 
-// one warp per cluster: a CTA per cluster, or a persistent grid on the work counter
-__global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
+// ---------------------------------------------------------------------------
+// The same bulge chasing in double-float arithmetic (df32.cuh), for the mixed path.
+// The band is first copied into a compact double-float layout in the merge-matrix
+// area: row r holds the entries (r, r - k), k = 0 .. 2 BW - 1 (the band and the
+// bulges), at Bd[r * BD + k].  The chase then takes the steps of chase_one on Bd.
+// Each reflector is formed in FP64 from its column (norm, square root, division, as in
+// warp_householder) and logged in FP64 for the back-transforms; its application, the
+// bulk of the work (about 6 BW^2 multiply-adds per reflector), runs on the FP32 pipe.
+// The diagonal and subdiagonal go back to FP64 at the end.
+//
+// A cluster's band (n x 2 BW entries) and those of the other clusters in flight do not
+// fit in L2, so every block a step reads comes from HBM.  Each step's two blocks are
+// fetched by asynchronous copies (cp.async, one 8-byte entry per lane and row) issued
+// ahead of their use: the diagonal block D of step k + 1 while step k multiplies its
+// block below the window, that block O while step k updates D.  Neither region is
+// written between the copy and its use: within a sweep, step k writes rows
+// [p, p + BW) only, and the sweep before has finished.
+// ---------------------------------------------------------------------------
+#define BD (2 * BW)
+
+__device__ __forceinline__ df32 df_zero() { return df_make(0.0f, 0.0f); }
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// copies of D's lower triangle (rows [p, p + len)) into Ds, one group
+__device__ __forceinline__ void fetch_d(const df32* Bd, int p, int len, df32* Ds) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < len; ++i) cp_async8(&Ds[i * TL + lane], &Bd[(size_t)(p + i) * BD + i - lane]);
+    cp_async_commit();
+}
+
+// copies of the block below the window (rows [p + len, p + len + nr) x cols [p, p + len))
+// into Os, one group; columns >= len are zero
+__device__ __forceinline__ void fetch_o(const df32* Bd, int p, int len, int nr, df32* Os) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < nr; ++r) {
+        if (lane < len) cp_async8(&Os[r * TL + lane], &Bd[(size_t)(p + len + r) * BD + len + r - lane]);
+        else Os[r * TL + lane] = df_zero();
+    }
+    cp_async_commit();
+}
+
+// Shared memory of a chase warp (double-float): the blocks D and O (BW x TL each), then
+// the reflector v, the vector w of the two-sided update and the row scalings s (BW each)
+#define CH_VS (2 * BW * TL)
+#define CH_WS (CH_VS + BW)
+#define CH_SS (CH_WS + BW)
+#define CH_DF_ENTRIES (CH_SS + BW)
+
+// The step functions take the window length len and the rows nr below it; FULL (len ==
+// nr == BW, every step but a sweep's last one or two) fixes both at compile time, so the
+// loops unroll without guards, by CH_UNROLL_DOT term pairs in the dot products and
+// CH_UNROLL_UPD rows in the updates.  Measured on the 1,728-cluster rock-salt step
+// (k_chase per launch): 97 ms at 4 / 8, 98-100 ms at 2-4 / 2-8, 107 ms without
+// unrolling, 112-123 ms at 8-16 / 16, 144 ms fully unrolled (168 registers and spills).
+constexpr int CH_UNROLL_DOT = 4;
+constexpr int CH_UNROLL_UPD = 8;
+
+// D <- H D H for the window [p, p + len) (H = I - tau v v^T); Ds holds D's lower
+// triangle, Vs the reflector
+template <bool FULL>
+__device__ static void chase_two_sided_df(df32* Bd, int p, int len_rt, df32 v, df32 tau, const df32* Ds,
+                                          const df32* Vs, df32* Ws) {
+    const int lane = threadIdx.x & 31;
+    const int len = FULL ? BW : len_rt;
+    df_acc y0 = df_acc_zero(), y1 = df_acc_zero();
+#pragma unroll(FULL ? CH_UNROLL_DOT : 1)
+    for (int c = 0; c < len; c += 2) {
+        if (FULL || lane < len) {
+            df_acc_add(y0, Ds[c <= lane ? lane * TL + c : c * TL + lane], Vs[c]);
+            if (FULL || c + 1 < len) df_acc_add(y1, Ds[c + 1 <= lane ? lane * TL + c + 1 : (c + 1) * TL + lane], Vs[c + 1]);
+        }
+    }
+    const df32 y = df_mul(tau, df_acc_merge(y0, y1));
+    const df32 dot = df_warp_sum((FULL || lane < len) ? df_mul(v, y) : df_zero());
+    const df32 hc = df_mul(df_make(0.5f * tau.hi, 0.5f * tau.lo), dot);
+    const df32 w = df_fma(df_neg(hc), v, y);
+    Ws[lane] = w;
+    __syncwarp();
+    // rows i and len-1-i of the lower triangle in one pass (as in chase_two_sided)
+#pragma unroll(FULL ? CH_UNROLL_DOT : 1)
+    for (int i = 0; 2 * i < len; ++i) {
+        const int r2 = len - 1 - i;
+        const bool first = lane < i;
+        const int row = first ? i : r2, col = first ? lane : lane - i;
+        const bool on = first || (r2 > i && col < r2);
+        if (on)
+            Bd[(size_t)(p + row) * BD + row - col] = df_sub2(Ds[row * TL + col], Vs[row], Ws[col], Ws[row], Vs[col]);
+    }
+    if (FULL || lane < len) Bd[(size_t)(p + lane) * BD] = df_sub2(Ds[lane * TL + lane], v, w, w, v);
+    __syncwarp();
+}
+
+// O <- O H for the fetched block below the window (nr rows)
+template <bool FULL>
+__device__ static void chase_right_df(int len_rt, int nr_rt, df32 v, df32 tau, df32* Os, const df32* Vs, df32* Ss) {
+    const int lane = threadIdx.x & 31;
+    const int len = FULL ? BW : len_rt, nr = FULL ? BW : nr_rt;
+    df_acc s0 = df_acc_zero(), s1 = df_acc_zero();
+#pragma unroll(FULL ? CH_UNROLL_DOT : 1)
+    for (int c = 0; c < len; c += 2) {
+        if (FULL || lane < nr) {
+            df_acc_add(s0, Os[lane * TL + c], Vs[c]);
+            if (FULL || c + 1 < len) df_acc_add(s1, Os[lane * TL + c + 1], Vs[c + 1]);
+        }
+    }
+    Ss[lane] = df_neg(df_mul(tau, df_acc_merge(s0, s1)));
+    __syncwarp();
+#pragma unroll(FULL ? CH_UNROLL_UPD : 1)
+    for (int r = 0; r < nr; ++r)
+        if (FULL || lane < len) Os[r * TL + lane] = df_fma(Ss[r], v, Os[r * TL + lane]);
+    __syncwarp();
+}
+
+// O <- H O on the carried block's columns 1 .. BW-1 (lane = column; len rows)
+template <bool FULL>
+__device__ static void chase_left_df(int len_rt, df32 tau, df32* Os, const df32* Vs) {
+    const int lane = threadIdx.x & 31;
+    const int len = FULL ? BW : len_rt;
+    df_acc s0 = df_acc_zero(), s1 = df_acc_zero();
+#pragma unroll(FULL ? CH_UNROLL_DOT : 1)
+    for (int i = 0; i < len; i += 2) {
+        df_acc_add(s0, Vs[i], Os[i * TL + lane]);
+        if (FULL || i + 1 < len) df_acc_add(s1, Vs[i + 1], Os[(i + 1) * TL + lane]);
+    }
+    const df32 ns = df_neg(df_mul(tau, df_acc_merge(s0, s1)));
+#pragma unroll(FULL ? CH_UNROLL_UPD : 1)
+    for (int i = 0; i < len; ++i)
+        if (lane >= 1) Os[i * TL + lane] = df_fma(ns, Vs[i], Os[i * TL + lane]);
+    __syncwarp();
+}
+
+// rows [row0, row0 + nr) x cols [col0, col0 + nc) of the band <- Os
+__device__ static void chase_store_df(df32* Bd, int row0, int col0, int nr, int nc, const df32* Os) {
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < nr; ++r)
+        if (lane < nc) Bd[(size_t)(row0 + r) * BD + row0 + r - col0 - lane] = Os[r * TL + lane];
+    __syncwarp();
+}
+
+// Reflector H = I - tau v v^T with H x = beta e_0 for this lane's entry x of the column
+// (lanes >= len hold 0), as in warp_householder but in double-float (norm, square root
+// and divisions included); v goes to Vs, tau and v to the FP64 log slot.
+__device__ __forceinline__ void df_reflector(df32 x, int len, double* slot, df32* Vs, df32& v, df32& tau,
+                                             df32& beta) {
+    const int lane = threadIdx.x & 31;
+    const df32 alpha = df_shfl(x, 0);
+    const df32 sig = df_warp_sum((lane >= 1 && lane < len) ? df_mul(x, x) : df_zero());
+    tau = df_zero();
+    beta = alpha;
+    v = df_make(lane == 0 ? 1.0f : 0.0f, 0.0f);
+    if (sig.hi > 0.0f) {  // the same for every lane
+        const df32 nrm = df_sqrt(df_fma(alpha, alpha, sig));
+        beta = (alpha.hi >= 0.0f) ? df_neg(nrm) : nrm;
+        const df32 am = df_add(alpha, df_neg(beta));  // alpha - beta
+        tau = df_div(df_neg(am), beta);
+        const df32 inv = df_div(df_make(1.0f, 0.0f), am);
+        if (lane >= 1 && lane < len) v = df_mul(x, inv);
+    }
+    Vs[lane] = v;
+    if (lane == 0) slot[0] = df_to_double(tau);
+    else if (lane < len) slot[lane] = df_to_double(v);
+    __syncwarp();
+}
+
+__device__ __forceinline__ void chase_one_df(const ClusterDesc* __restrict__ cls, int ci, double* __restrict__ arena,
+                                             const int* __restrict__ status) {
+    extern __shared__ double sm[];
+    df32* Ds = reinterpret_cast<df32*>(sm);
+    df32* Os = Ds + BW * TL;
+    df32* Vs = Ds + CH_VS;
+    df32* Ws = Ds + CH_WS;
+    df32* Ss = Ds + CH_SS;
+    if (status[ci] != ST_OK) return;
+    const ClusterDesc d = cls[ci];
+    if (!two_stage_cluster(d)) return;
+    const int n = d.n, ld = d.ld, lane = threadIdx.x;
+    const double* A = arena + d.mat_off;
+    df32* Bd = reinterpret_cast<df32*>(arena + d.m_off);  // n x BD (merge area: 2 n ld doubles)
+    double* slot = arena + d.q2_off;
+    // the band (k <= BW) and zeros for the bulges, eight rows' loads in flight
+    for (int r0 = 0; r0 < n; r0 += 8) {
+        double x[8][2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + q, k = lane + 32 * h, c = r - k;
+                x[q][h] = (r < n && k <= BW && c >= 0) ? A[(size_t)r * ld + c] : 0.0;
+            }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (r0 + q < n) Bd[(size_t)(r0 + q) * BD + lane + 32 * h] = df_from_double(x[q][h]);
+    }
+    __syncwarp();
+    if (n > 2) fetch_d(Bd, 1, min(BW, n - 1), Ds);
+    df32 v, tau, beta;
+    for (int j = 0; j + 2 < n; ++j) {
+        const int nsteps = (int)chase_steps(n, j);
+        int p = j + 1, len = min(BW, n - p), nr = 0;
+        for (int k = 0; k < nsteps; ++k) {
+            if (k == 0) {
+                // column j below its subdiagonal (entries (p + lane, j): k = 1 + lane)
+                df32* colj = Bd + (size_t)p * BD + 1;
+                df_reflector(lane < len ? colj[(size_t)lane * (BD + 1)] : df_zero(), len, slot, Vs, v, tau, beta);
+                if (lane < len) colj[(size_t)lane * (BD + 1)] = (lane == 0) ? beta : df_zero();
+            } else {
+                // the carried block O holds rows [p + BW, ...) x cols [p, p + BW) (len == BW)
+                const int pp = p;
+                p = pp + BW;
+                len = min(BW, n - p);  // == nr
+                df_reflector(lane < len ? Os[lane * TL] : df_zero(), len, slot, Vs, v, tau, beta);
+                if (lane < len) Os[lane * TL] = (lane == 0) ? beta : df_zero();
+                __syncwarp();
+                if (len == BW) chase_left_df<true>(len, tau, Os, Vs);
+                else chase_left_df<false>(len, tau, Os, Vs);
+                chase_store_df(Bd, p, pp, len, BW, Os);
+            }
+            slot += BW;
+            // this step's block below the window into Os (free now), D (fetched ahead)
+            nr = max(0, min(BW, n - p - len));
+            const bool full = len == BW && nr == BW;
+            fetch_o(Bd, p, len, nr, Os);
+            cp_async_wait<1>();
+            __syncwarp();
+            if (full) chase_two_sided_df<true>(Bd, p, len, v, tau, Ds, Vs, Ws);
+            else chase_two_sided_df<false>(Bd, p, len, v, tau, Ds, Vs, Ws);
+            // the next step's D while this step multiplies O
+            if (k + 1 < nsteps) {
+                fetch_d(Bd, p + BW, min(BW, n - p - BW), Ds);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            if (full) chase_right_df<true>(len, nr, v, tau, Os, Vs, Ss);
+            else chase_right_df<false>(len, nr, v, tau, Os, Vs, Ss);
+        }
+        chase_store_df(Bd, p + len, p, nr, len, Os);
+        // the next sweep's first D (its rows are final once this sweep's stores are done)
+        if (j + 3 < n) fetch_d(Bd, j + 2, min(BW, n - j - 2), Ds);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    double* dv = arena + d.aux_off;
+    double* ev = dv + ld;
+    for (int t = lane; t < n; t += 32) {
+        dv[t] = df_to_double(Bd[(size_t)t * BD]);
+        ev[t] = (t + 1 < n) ? df_to_double(Bd[(size_t)(t + 1) * BD + 1]) : 0.0;
+    }
+    __syncwarp();
+    if (lane == 0) tear_cluster(d, arena);
+}
+
+// one warp per cluster: a CTA per cluster, or a persistent grid on the work counter;
+// DF: the double-float form (mixed path)
+template <bool DF>
+__global__ void __launch_bounds__(32, DF ? 12 : 1) k_chase(const ClusterDesc* __restrict__ cls, const int* __restrict__ order,
                                               double* __restrict__ arena, const int* __restrict__ status, int nitems,
                                               int* __restrict__ queue) {
     for (int it = blockIdx.x;;) {
@@ -478,7 +746,8 @@ __global__ void __launch_bounds__(32) k_chase(const ClusterDesc* __restrict__ cl
             it = __shfl_sync(0xffffffffu, v, 0);
         }
         if (it >= nitems) break;
-        chase_one(cls, order[it], arena, status);
+        if constexpr (DF) chase_one_df(cls, order[it], arena, status);
+        else chase_one(cls, order[it], arena, status);
         if (!queue) break;
     }
 }
@@ -496,12 +765,14 @@ static dclno_status launch_band_t(dclno_ctx* c, const int* order, int nitems, in
     return DCLNO_OK;
 }
 
+template <bool DF>
 static dclno_status launch_chase_s(dclno_ctx* c, const int* order, int nitems, int persistent) {
-    const size_t sm2 = 2 * BW * TL * sizeof(double);
-    const int grid = sched_grid(c, (const void*)k_chase, 32, sm2, nitems, persistent != 0);
+    static_assert(sizeof(df32) == sizeof(double), "one double-float entry takes the space of an FP64 one");
+    const size_t sm2 = (DF ? CH_DF_ENTRIES : 2 * BW * TL) * sizeof(double);
+    const int grid = sched_grid(c, (const void*)k_chase<DF>, 32, sm2, nitems, persistent != 0);
     int* q = persistent ? c->d_queue : nullptr;
     if (q) DCLNO_CUDA(c, cudaMemsetAsync(q, 0, sizeof(int), c->stream));
-    k_chase<<<grid, 32, sm2, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems, q);
+    k_chase<DF><<<grid, 32, sm2, c->stream>>>(c->d_cl, order, c->d_arena, c->d_status, nitems, q);
     DCLNO_LAUNCHED(c);
     return DCLNO_OK;
 }
@@ -530,7 +801,8 @@ dclno_status launch_two_stage(dclno_ctx* c, const Batch& b, bool mixed, bool tun
             const int* ord = c->d_order + r.obeg;
             const int ni = r.oend - r.obeg;
             dclno_status st;
-            if (kernel == TK_CHASE) st = launch_chase_s(c, ord, ni, s.persistent);
+            if (kernel == TK_CHASE) st = mixed ? launch_chase_s<true>(c, ord, ni, s.persistent)
+                                               : launch_chase_s<false>(c, ord, ni, s.persistent);
             else if (s.engine == 2) st = launch_band_t<2>(c, ord, ni, s.persistent);
             else if (s.engine == 1) st = launch_band_t<1>(c, ord, ni, s.persistent);
             else st = launch_band_t<0>(c, ord, ni, s.persistent);
