@@ -193,7 +193,7 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
  * Form of the Householder tridiagonalisation in dclno_solve_clusters (Sec. II.C
  * step (iii); both give the same T up to rounding and the same eigenpairs):
  *   0  automatic (default): the form measured faster on GB300: one-stage in FP64;
- *      in the mixed path two-stage for clusters of dimension >= 384 (torn ones),
+ *      in the mixed path two-stage for clusters of dimension >= 128 (torn ones),
  *      one-stage below;
  *   1  one-stage: blocked Householder with a symmetric matrix-vector product per
  *      column (each column reads the whole trailing matrix);
@@ -201,8 +201,8 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
  *      products are all matrix-matrix tile products), band -> tridiagonal by
  *      Householder bulge chasing.
  * The two-stage form keeps a log of about n^2/2 doubles of chase reflectors per
- * cluster, reserved by dclno_build_clusters according to the mode at that time: mode
- * 2 for clusters of dimension >= 128, mode 0 for dimension >= 384, mode 1 none.  A
+ * cluster, reserved by dclno_build_clusters according to the mode at that time: modes
+ * 0 and 2 for clusters of dimension >= 128, mode 1 none.  A
  * cluster uses the two-stage form when the solve allows it (mode 2; mode 0 in the
  * mixed path) and its log exists.  Modes 0 and 1 can be selected at any time, mode 2
  * on a context built in mode 2; each takes effect at the next solve.  Errors:

@@ -64,8 +64,9 @@ struct ClusterDesc {
 #define DCLNO_BW 32
 #define DCLNO_TWO_STAGE_MIN 128  // clusters of at least this dimension (and torn) may use it
 // the automatic choice: the mixed path's clusters of at least this dimension (measured on
-// GB300: two-stage faster at n ~ 650-705, one-stage at n ~ 150-285)
-#define DCLNO_TWO_STAGE_AUTO_MIN 384
+// GB300 with the double-float bulge chasing: two-stage faster at n ~ 147-285 (763 against
+// 827 ms per step), 231-385 (602 against 631 ms) and 654-702; the FP64 path stays one-stage)
+#define DCLNO_TWO_STAGE_AUTO_MIN 128
 __host__ __device__ inline long long chase_steps(int n, int j) {
     const int r = n - 2 - j;
     return r > 0 ? (r + DCLNO_BW - 1) / DCLNO_BW : 0;

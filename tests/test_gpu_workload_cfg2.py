@@ -22,7 +22,7 @@ from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED  # noqa: E402
 SAMPLE = [0, 777, 1727]
 MU_TEST = -0.25  # a fixed chemical potential for element-wise rho comparison
 # name: (precision, tridiagonalisation form); the automatic form (0) is two-stage in the
-# mixed path for these clusters (n >= 384) and one-stage in FP64
+# mixed path for these clusters (n >= 128) and one-stage in FP64
 PRECISIONS = {"fp64": (DCLNO_FP64, 0), "mixed": (DCLNO_MIXED, 0), "mixed_one": (DCLNO_MIXED, 1)}
 
 
