@@ -472,9 +472,10 @@ __device__ __forceinline__ void chase_one(const ClusterDesc* __restrict__ cls, i
 // The band is first copied into a compact double-float layout in the merge-matrix
 // area: row r holds the entries (r, r - k), k = 0 .. 2 BW - 1 (the band and the
 // bulges), at Bd[r * BD + k].  The chase then takes the steps of chase_one on Bd.
-// Each reflector is formed in FP64 from its column (norm, square root, division, as in
-// warp_householder) and logged in FP64 for the back-transforms; its application, the
-// bulk of the work (about 6 BW^2 multiply-adds per reflector), runs on the FP32 pipe.
+// Each reflector is formed in double-float from its column (norm, square root and
+// divisions: df_reflector, the steps of warp_householder) and logged in FP64 for the
+// back-transforms; its application, the bulk of the work (about 6 BW^2 multiply-adds
+// per reflector), runs on the FP32 pipe as well.
 // The diagonal and subdiagonal go back to FP64 at the end.
 //
 // A cluster's band (n x 2 BW entries) and those of the other clusters in flight do not
