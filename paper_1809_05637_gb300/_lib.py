@@ -163,6 +163,30 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _require_doubles(name, x, count, where, device=None):
+    """Refuse a buffer that the C library would read or write past: it must hold at
+    least `count` contiguous float64 values, on CUDA device `device` (where="device":
+    a torch tensor) or in host memory (where="host": a numpy array or a CPU tensor).
+    The C entry points receive bare pointers and cannot check any of this."""
+    if isinstance(x, np.ndarray):
+        ok = where == "host" and x.dtype == np.float64 and x.flags.c_contiguous
+        n = x.size
+    else:
+        import torch
+
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor or a numpy array, not {type(x).__name__}")
+        on_gpu = x.is_cuda
+        ok = x.dtype == torch.float64 and x.is_contiguous() and (
+            (where == "device" and on_gpu and x.device.index == device) or (where == "host" and not on_gpu))
+        n = x.numel()
+    if not ok:
+        at = f"CUDA tensor on cuda:{device}" if where == "device" else "host array"
+        raise ValueError(f"{name} must be a contiguous float64 {at}")
+    if n < count:
+        raise ValueError(f"{name} holds {n} values; the system's H, S and rho hold {count}")
+
+
 def _dptr(v: ctypes.c_double):
     return ctypes.cast(ctypes.byref(v), ctypes.c_void_p)
 
@@ -175,9 +199,12 @@ class Context:
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
+        import torch
+
         h = ctypes.c_void_p()
         self._check(self.lib.dclno_create(ctypes.byref(h), ctypes.c_void_p(stream)), None)
         self.h = h
+        self.device = torch.cuda.current_device()  # the device dclno_create bound the context to
         self._keep = []
         self.natoms = 0
         self.nval = 0
@@ -282,7 +309,9 @@ class Context:
             norb=np.ascontiguousarray(norb, dtype=np.int32), row_ptr=np.ascontiguousarray(row_ptr, dtype=np.int64),
             col=np.ascontiguousarray(col, dtype=np.int32), shift=np.ascontiguousarray(shift, dtype=np.int8),
             blk_off=np.ascontiguousarray(blk_off, dtype=np.int64))
+        _require_doubles("H", H, 0, "device", self.device)
         nval = int(H.numel())
+        _require_doubles("S", S, nval, "device", self.device)
         s = dclno_system(natoms=len(host["norb"]), pos=_ptr(host["pos"]), cell=_ptr(host["cell"]),
                          pbc=_ptr(host["pbc"]), norb=_ptr(host["norb"]), nnzb=len(host["col"]), nval=nval,
                          row_ptr=_ptr(host["row_ptr"]), col=_ptr(host["col"]), shift=_ptr(host["shift"]),
@@ -299,7 +328,15 @@ class Context:
         self.norb = host["norb"]
         self.k_lno = int(k_lno)
 
+    def _dev(self, name, x):
+        """A device buffer of the system's nval values (None passes through)."""
+        if x is not None:
+            _require_doubles(name, x, self.nval, "device", self.device)
+        return _ptr(x)
+
     def compute_lnos(self, rho):
+        """LNOs from rho (device, nval values); rho None: the first step's LNO-free start."""
+        self._dev("rho", rho)
         self._check(self.lib.dclno_compute_lnos(self.h, _ptr(rho)))
 
     def solve_clusters(self, precision=DCLNO_FP64):
@@ -312,23 +349,30 @@ class Context:
 
     def density_matrix(self, mu, kT, rho_out):
         e = ctypes.c_double()
+        self._dev("rho_out", rho_out)
         self._check(self.lib.dclno_density_matrix(self.h, float(mu), float(kT), _ptr(rho_out), _dptr(e)))
         return e.value
 
     def density_matrix_poles(self, mu, kT, n_poles, rho_out, precision=DCLNO_FP64):
         """rho rows from the Matsubara pole sum (no eigenvectors); invalidates an earlier solve."""
+        self._dev("rho_out", rho_out)
         self._check(self.lib.dclno_density_matrix_poles(self.h, float(mu), float(kT), int(n_poles), int(precision),
                                                         _ptr(rho_out)))
 
     def density_matrices(self, mu, kT, rho_out, edm_out):
         """rho and the energy density matrix e (Eq. (edm)) rows; returns the band energy."""
         e = ctypes.c_double()
+        self._dev("rho_out", rho_out)
+        self._dev("edm_out", edm_out)
         self._check(self.lib.dclno_density_matrices(self.h, float(mu), float(kT), _ptr(rho_out), _ptr(edm_out),
                                                     _dptr(e)))
         return e.value
 
     def step(self, rho_in, rho_out, n_electrons, kT, host_buffers=False, precision=DCLNO_FP64):
         mu, n, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        for name, x in (("rho_in", rho_in), ("rho_out", rho_out)):
+            if x is not None:
+                _require_doubles(name, x, self.nval, "host" if host_buffers else "device", self.device)
         self._check(self.lib.dclno_step(self.h, _ptr(rho_in), _ptr(rho_out), int(bool(host_buffers)),
                                         int(precision), float(n_electrons), float(kT), _dptr(mu), _dptr(n),
                                         _dptr(e)))
@@ -341,6 +385,7 @@ class Context:
         mu = np.zeros(nsteps)
         n = np.zeros(nsteps)
         e = np.zeros(nsteps)
+        self._dev("rho", rho)
         self._check(self.lib.dclno_scf_run(self.h, _ptr(rho), int(nsteps), float(alpha), int(precision),
                                            float(n_electrons), float(kT), int(bool(use_graph)), _ptr(mu),
                                            _ptr(n), _ptr(e)))
