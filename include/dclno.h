@@ -424,7 +424,8 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
  * covers at most 8,388,608 pairs (4096 blocks x 256 threads x 8), and a larger
  * count returns DCLNO_ERR_ARG without touching the GPU.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) once and
- * keeps it.  All calls share the one array:
+ * keeps it; make that first call on each device before any stream capture
+ * begins there.  All calls share the one array:
  * calls whose GPU work overlaps (other threads or streams) race and must be
  * serialised by the caller.
  * Errors: DCLNO_ERR_ARG (null pointers, count < 1 or too large, kT <= 0),
