@@ -235,10 +235,12 @@ dclno_status dclno_set_tear(dclno_ctx *ctx, int mode);
  *   0  chosen per kernel and size bucket by the schedule tuner (default);
  *   1  mma.sync.m16n8k16 BF16 from register fragments;
  *   2  tcgen05.mma with the level accumulators in tensor memory: one thread issues
- *      the products of a level while the CTA's warps combine the previous level.
+ *      the products of all eight levels behind one commit, then every warp reads
+ *      the levels back (tcgen05.ld) and combines them.
  * The long-K products (Y = A22 V of the band reduction, the merge-matrix products)
  * always run on tcgen05 with one FP64 epilogue per output.  Each CTA using tcgen05
- * holds 128 tensor-memory columns.  A tensor-core wait that runs out fails the solve
+ * holds 256 tensor-memory columns (eight accumulators of 32), at most two such
+ * CTAs per SM.  A tensor-core wait that runs out fails the solve
  * with DCLNO_ERR_TIMEOUT (cluster in the message).  Takes effect at the next solve
  * and clears the tuned schedules; DCLNO_ERR_ARG for another value.
  */
