@@ -111,7 +111,9 @@ const char *dclno_last_error(const dclno_ctx *ctx);
  * descending, so the central atom is last.  The cluster dimension is
  * n_i = sum_core M_j + k_lno * |LNO members|.  Copies the structure of `sys` to
  * the device, keeps the device pointers sys->H and sys->S, and allocates the
- * workspace of the FP64 solver for all clusters at once.
+ * solver workspace: for all clusters at once when it fits the budget of
+ * dclno_set_workspace_limit, else for the largest of the contiguous batches of
+ * clusters that the budget admits (each solved in turn by the calls below).
  * Errors: DCLNO_ERR_ARG (radii, k_lno > M_j, unsorted rows, missing on-site
  * block), DCLNO_ERR_OOM.
  */
@@ -145,7 +147,8 @@ dclno_status dclno_build_clusters_kappa(dclno_ctx *ctx, const dclno_system *sys,
  * their span, each with its largest-magnitude component positive (only the
  * span enters the cluster problem).  A selected complex pair contributes its
  * real and imaginary parts; a pair split by the cut contributes its real part.
- * No-op when k_lno = 0 or r_lno = r_core.
+ * No-op when k_lno = 0 or r_lno = r_core (rho may then be NULL); otherwise a NULL
+ * rho is DCLNO_ERR_ARG.
  */
 dclno_status dclno_compute_lnos(dclno_ctx *ctx, const double *rho);
 
@@ -199,7 +202,7 @@ dclno_status dclno_set_autotune(dclno_ctx *ctx, int on);
  *      column (each column reads the whole trailing matrix);
  *   2  two-stage: dense -> band of half-width 32 (blocked Householder whose
  *      products are all matrix-matrix tile products), band -> tridiagonal by
- *      Householder bulge chasing.
+ *      Householder bulge chasing (in double-float arithmetic in the mixed path).
  * The two-stage form keeps a log of about n^2/2 doubles of chase reflectors per
  * cluster, reserved by dclno_build_clusters according to the mode at that time: modes
  * 0 and 2 for clusters of dimension >= 128, mode 1 none.  A
@@ -326,12 +329,15 @@ dclno_status dclno_get_lno_counts(dclno_ctx *ctx, int *counts);
 dclno_status dclno_set_lno_mode(dclno_ctx *ctx, dclno_lno_mode mode);
 
 /*
- * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)).  FP64 path:
- * Cholesky S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation,
- * implicit QL on the two halves of the tridiagonal matrix torn at n/2 (Cuppen's
- * divide and conquer, the halves merged through the secular equation), and the
- * central-atom rows of the
- * eigenvectors C = L^-T Q Z.  Keeps per cluster the eigenvalues eps_mu,
+ * Assemble and solve every cluster (Sec. II.C steps (ii)-(iii)): Cholesky
+ * S^(i) = L L^T, A = L^-1 H^(i) L^-T, Householder tridiagonalisation A = Q T Q^T
+ * (one stage, or dense -> band -> tridiagonal: dclno_set_tridiag), T = Z Theta Z^T
+ * by Cuppen's divide and conquer (T torn at n/2, or twice from dimension 512:
+ * dclno_set_tear; implicit QL on the segments, merges through the secular
+ * equation), and the central-atom rows of the eigenvectors C = L^-T Q Z.  In
+ * DCLNO_MIXED the cubic contractions run as emulated FP64 on BF16 tensor cores
+ * (dclno_set_mixed_engine) and the two-stage form's bulge chasing in double-float
+ * arithmetic on the FP32 pipe; QL, merges and everything after stay FP64.  Keeps per cluster the eigenvalues eps_mu,
  * the weights q_mu = sum_{alpha in i} C_{alpha mu} (S^(i) C)_{alpha mu}
  * (sum_mu q_mu = M_i) and what dclno_density_matrix needs.
  * Errors: DCLNO_ERR_NO_LNOS, DCLNO_ERR_NOT_SPD, DCLNO_ERR_NOT_CONVERGED (cluster id

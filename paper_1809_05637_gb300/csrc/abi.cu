@@ -893,8 +893,8 @@ static dclno_status solve_batch(dclno_ctx* c, int bi, dclno_precision prec) {
 
 // The tridiagonalisation form of a solve: mode 1 one-stage, 2 two-stage; the automatic
 // mode (0) takes the form measured faster on the 1,728-atom step in each precision:
-// one-stage in FP64 (2.61 against 3.33 s per step), two-stage in the mixed path
-// (1.58 against 1.75 s).
+// one-stage in FP64 (2.6 against 3.3 s per step), two-stage in the mixed path (1.1
+// against 1.4 s, its bulge chasing in double-float arithmetic).
 // Whether the solve may use the two-stage form; which clusters do is fixed by the layout
 // (a cluster takes it when its workspace holds a chase-reflector log).  Mode 0: the mixed
 // path only (FP64 two-stage is slower on GB300, whose FP64 tile products barely beat its
