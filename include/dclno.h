@@ -404,7 +404,8 @@ dclno_status dclno_density_matrix_poles(dclno_ctx *ctx, double mu, double kT, in
  * One whole DC-LNO step: compute_lnos(rho_in), solve_clusters(precision),
  * find_mu, density_matrix(rho_out).  With host_buffers != 0, rho_in and rho_out
  * are host arrays [nval] copied to and from the context's device buffers inside
- * the call; otherwise they are device arrays.  mu_out, nelec_out, eband_out are
+ * the call; otherwise they are device arrays.  rho_in may be NULL where
+ * dclno_compute_lnos allows it (no LNO region).  mu_out, nelec_out, eband_out are
  * host scalars (nullable).
  */
 dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
