@@ -265,6 +265,7 @@ def measure_scf(world):
     """Five SCF steps (dclno_scf_run, captured graph) in each precision, CUDA events
     on the context's stream; inputs resident on the device."""
     import torch
+    import torch.distributed as dist
 
     import tbsystems as T
     from paper_1809_05637_gb300 import DCLNO_FP64, DCLNO_MIXED, Context
@@ -290,12 +291,17 @@ def measure_scf(world):
             ctx.scf_run(rho, 1, 0.3, s.n_electrons, s.kT, prec, use_graph=True)  # warm-up
             rho = rho0.clone()
             stream.synchronize()
+            if world > 1:
+                dist.barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             mu, n, eb = ctx.scf_run(rho, SCF_STEPS, 0.3, s.n_electrons, s.kT, prec, use_graph=True)
             e1.record(stream)
             stream.synchronize()
-            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            if world > 1:
+                dist.barrier()
+            # the reduction's tensor lives on this rank's GPU (NCCL reduces device tensors only)
+            ms = max_over_ranks(e0.elapsed_time(e1), world, torch.device("cuda", torch.cuda.current_device()))
             out[name] = {"value": replica_throughput(world, s.natoms, SCF_STEPS, ms / 1e3), "unit": "clusters/s",
                          "ms_per_step": ms / SCF_STEPS, "mu_last": float(mu[-1]), "e_band_last": float(eb[-1])}
         out["schedules"] = schedule_summary(ctx.tuning_report())
