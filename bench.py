@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-scf", action="store_true", help="skip the SCF-loop measurement on the bcc slab")
     p.add_argument("--no-amorphous", action="store_true",
                    help="skip the one-step measurement of the 32,000-atom amorphous workload (run on one GPU only)")
+    p.add_argument("--no-refine", action="store_true",
+                   help="skip the measurement of the refinement sweeps (dclno_refine_eigenpairs)")
     p.add_argument("--workload", choices=["rocksalt1728", "rocksalt512", "rocksalt216", "small64", "amorphous32000"],
                    default="rocksalt1728",
                    help="rocksalt512: the same rock-salt recipe on 8^3 sites (the same cluster dimensions, one "
@@ -308,6 +310,57 @@ def measure_scf(world):
         ctx.close()
     out["e_band_diff_per_atom_mixed_vs_fp64"] = abs(out["mixed"]["e_band_last"] - out["fp64"]["e_band_last"]) / s.natoms
     return out
+
+
+# ---------------------------------------------------------------------------
+# Ogita-Aishima refinement sweeps (dclno_refine_eigenpairs) at the benchmark's
+# cluster dimension
+# ---------------------------------------------------------------------------
+REFINE_PENCILS, REFINE_N, REFINE_SWEEPS = 32, 680, 2
+REFINE_WORKLOAD = (f"{REFINE_PENCILS} pencils (H, S) of dimension {REFINE_N} (the 1728-atom step's cluster "
+                   "dimension) with known eigenpairs (cond(S) = 100, eigenvalues over [-2, 2]), starts "
+                   f"X = C (I + 1e-6 P); {REFINE_SWEEPS} sweeps per call")
+
+
+def measure_refinement(dfma):
+    """Refinement sweeps on a batch of pencils whose eigenpairs are known: time of one
+    call of REFINE_SWEEPS sweeps (CUDA events on the current stream; the call allocates
+    its workspace and synchronises inside), FP64 roofline of its 10 n^3 flops per pencil
+    and sweep against the measured FP64 FMA rate, errors against the known pairs."""
+    import numpy as np
+    import torch
+
+    import tbsystems as T
+    from paper_1809_05637_gb300 import refine_eigenpairs
+
+    H, S, C, w = T.known_pencils(REFINE_PENCILS, REFINE_N, seed=41)
+    rng = np.random.default_rng(42)
+    X0 = np.stack([C[p] @ (np.eye(REFINE_N) + 1e-6 * rng.standard_normal((REFINE_N, REFINE_N)))
+                   for p in range(REFINE_PENCILS)])
+    dH, dS, dX0 = (torch.from_numpy(a).cuda() for a in (H, S, X0))
+    dX = dX0.clone()
+    refine_eigenpairs(dH, dS, dX, nsweeps=1)  # warm-up (module load, allocator)
+    dX.copy_(dX0)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lam = refine_eigenpairs(dH, dS, dX, nsweeps=REFINE_SWEEPS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    flops = 10.0 * REFINE_N ** 3 * REFINE_PENCILS * REFINE_SWEEPS
+    achieved = flops / (ms / 1e3) / 1e12
+    lam = lam.cpu().numpy()
+    X = dX.cpu().numpy()
+    return {"workload": REFINE_WORKLOAD, "ms_per_sweep": ms / REFINE_SWEEPS,
+            "pencil_sweeps_per_s": REFINE_PENCILS * REFINE_SWEEPS / (ms / 1e3),
+            "roofline": {"bound": "alu", "kernel": "k_refine_gemm", "achieved": achieved, "peak": dfma,
+                         "unit": "TFLOP/s", "frac": achieved / dfma, "traffic": None,
+                         "peak_source": "measured in-process FP64 FMA rate (the products run on FP64 FMA)",
+                         "flops_per_call": flops},
+            "max_abs_eig_err": float(np.max(np.abs(lam - w))), "max_abs_vec_err": float(np.max(np.abs(X - C))),
+            "start_vec_err": float(np.max(np.abs(X0 - C)))}
 
 
 # ---------------------------------------------------------------------------
@@ -695,6 +748,10 @@ def run_ours(args):
         torch.cuda.empty_cache()
         amorphous = measure_amorphous(args.atoms)
 
+    refinement = None
+    if world == 1 and not args.no_refine:
+        refinement = measure_refinement(dfma)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         th = cpu_threads()
@@ -720,7 +777,7 @@ def run_ours(args):
                            "l2": "no flush: S, H and rho (5.2 GB) exceed the 129 MB L2"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "schedules": schedules,
-                "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "amorphous32000": amorphous, "mu": mu,
+                "cpu_baseline": cpu, "mixed": mixed, "scf": scf, "amorphous32000": amorphous, "refinement": refinement, "mu": mu,
                 "n_electrons": n_mu, "e_band": e_band}
         print(json.dumps(line))
     ctx.close()

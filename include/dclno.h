@@ -414,6 +414,34 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
                         double *mu_out, double *nelec_out, double *eband_out);
 
 /*
+ * Ogita-Aishima refinement of approximate generalised eigendecompositions with
+ * FP64 residuals (Ogita & Aishima, Japan J. Indust. Appl. Math. 35 (2018), every
+ * inner product taken in the S metric).  Not a step of the paper: the refinement a
+ * mixed-precision eigensolver would apply to FP32 eigenpairs.  The library's own
+ * mixed path does not call it: at the workloads' conditioning its FP32 start lies
+ * outside the region where the sweeps converge, and the emulated FP64 contractions
+ * reach FP64 accuracy directly.  For each of `count` independent pencils of
+ * dimension n, nsweeps times:
+ *   R = I - X^T S X,  G = X^T H X,  lam_i = G_ii / (1 - R_ii),
+ *   delta = 2 (||G - diag(lam)||_F + max|lam| ||R||_F),
+ *   E_ij = (G_ij + lam_j R_ij) / (lam_j - lam_i) for i != j with |lam_j - lam_i| > delta,
+ *   E_ij = R_ij / 2 otherwise,   X <- X + X E.
+ * Each sweep squares the error of eigenpairs whose error is below the gaps of
+ * their eigenvalues; pairs closer than delta only keep their S-orthonormalisation.
+ * H, S: device [count][n][n] (row-major, symmetric, S positive definite); X: device
+ * [count][n][n] (in/out, column mu the approximate eigenvector of eigenvalue mu);
+ * lam_out: device [count][n], the eigenvalue estimates of the last sweep (from that
+ * sweep's input X).  All FP64, contiguous, on the current device.  Costs 10 n^3
+ * FP64 flops per pencil and sweep; allocates a workspace of 3 count n^2 + count
+ * doubles for the call and synchronises `cuda_stream` (NULL = legacy default
+ * stream) before returning.  Errors: DCLNO_ERR_ARG (NULL pointers, n, count or
+ * nsweeps < 1, n > 2,097,120 or count > 65,535), DCLNO_ERR_OOM, DCLNO_ERR_CUDA (X is
+ * then partly updated).
+ */
+dclno_status dclno_refine_eigenpairs(const double *H, const double *S, double *X, double *lam_out,
+                                     int n, int count, int nsweeps, void *cuda_stream);
+
+/*
  * The chemical-potential search of dclno_find_mu without any device
  * allocation, for callers that cannot call cudaMalloc: applications whose own
  * pool allocator has taken all device memory up front, and control loops that

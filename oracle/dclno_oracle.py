@@ -504,9 +504,11 @@ def refine_eigenpairs(H: np.ndarray, S: np.ndarray, X: np.ndarray):
       R = I - X^T S X,   G = X^T H X,   lam_i = G_ii / (1 - R_ii),
       E_ij = (G_ij + lam_j R_ij) / (lam_j - lam_i)   where |lam_i - lam_j| > delta,
       E_ij = R_ij / 2                                  otherwise (and on the diagonal),
-      delta = 2 (||G - diag(lam)||_2 + max|lam| ||R||_2),
-    returns (X + X E, lam).  The 2-norm of H in the published threshold becomes the
-    pencil's spectral radius (max |lam|), the norm that bounds G in the S metric.
+      delta = 2 (||G - diag(lam)||_F + max|lam| ||R||_F),
+    returns (X + X E, lam).  Two readings of the published threshold: the 2-norm of H
+    becomes the pencil's spectral radius (max |lam|), the norm that bounds G in the S
+    metric; and the 2-norms become Frobenius norms, upper bounds of them that one pass
+    over the matrices computes (a larger delta only moves pairs to the close-pair rule).
     Each sweep squares the error while the starting error is below the gaps between
     eigenvalues; pairs closer than delta keep only their orthonormalisation."""
     X = np.asarray(X, dtype=np.float64)
@@ -514,7 +516,7 @@ def refine_eigenpairs(H: np.ndarray, S: np.ndarray, X: np.ndarray):
     R = np.eye(n) - X.T @ S @ X
     G = X.T @ H @ X
     lam = np.diag(G) / (1.0 - np.diag(R))
-    delta = 2.0 * (np.linalg.norm(G - np.diag(lam), 2) + np.max(np.abs(lam)) * np.linalg.norm(R, 2))
+    delta = 2.0 * (np.linalg.norm(G - np.diag(lam)) + np.max(np.abs(lam)) * np.linalg.norm(R))
     E = 0.5 * R  # the value of the close pairs and of the diagonal
     for i in range(n):
         for j in range(n):

@@ -21,8 +21,10 @@ or ``ctx.step(rho_in, rho_out, n_electrons, kT)`` for all of it, and
 loop with linear mixing.  ``set_workspace_limit`` (memory-admitted batches),
 ``set_lno_threshold`` (lambda_th selection), ``set_lno_mode`` (the symmetric
 projector form of the LNO eigenproblem) and ``set_autotune`` adjust the run.
+``refine_eigenpairs`` applies Ogita-Aishima refinement sweeps with FP64
+residuals to batched approximate eigendecompositions of pencils (H, S).
 """
 from ._lib import (  # noqa: F401
     DCLNO_FP64, DCLNO_MIXED, DCLNO_LNO_PAPER, DCLNO_LNO_SYM, LIB_PATH, Context, DclnoError, STATUS_NAMES, exported_symbols, load_library,
-    find_mu_noalloc, measure_fp64_peaks,
+    find_mu_noalloc, measure_fp64_peaks, refine_eigenpairs,
 )

@@ -25,7 +25,7 @@ SYMBOLS = ["dclno_create", "dclno_destroy", "dclno_last_error", "dclno_build_clu
            "dclno_set_autotune", "dclno_get_tuning", "dclno_build_clusters_kappa", "dclno_set_lno_threshold",
            "dclno_get_lno_counts", "dclno_set_lno_mode", "dclno_set_tridiag", "dclno_density_matrix_poles",
            "dclno_set_mixed_engine", "dclno_set_schedule", "dclno_set_tuning_cache", "dclno_tuning_report",
-           "dclno_set_bucket_min", "dclno_set_tear"]
+           "dclno_set_bucket_min", "dclno_set_tear", "dclno_refine_eigenpairs"]
 
 
 class DclnoError(RuntimeError):
@@ -101,6 +101,7 @@ def load_library():
         "dclno_set_tear": ([P, I], I),
         "dclno_set_tuning_cache": ([P, ctypes.c_char_p], I),
         "dclno_tuning_report": ([P, ctypes.c_char_p, ctypes.c_size_t, P], I),
+        "dclno_refine_eigenpairs": ([P, P, P, P, I, I, I, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -152,6 +153,31 @@ def find_mu_noalloc(eps, q, n_electrons, kT, stream=None):
     if st != 0:
         raise DclnoError(st, "dclno_find_mu_noalloc failed")
     return mu.value, n.value
+
+
+def refine_eigenpairs(H, S, X, nsweeps=1, stream=None):
+    """dclno_refine_eigenpairs on a batch of pencils: H, S, X are [count, n, n] float64
+    CUDA tensors (X updated in place); returns the eigenvalue estimates of the last
+    sweep as a [count, n] tensor."""
+    import torch
+
+    lib = load_library()
+    dev = torch.cuda.current_device()
+    for name, t in (("H", H), ("S", S), ("X", X)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 3 or t.shape[1] != t.shape[2]:
+            raise ValueError(f"refine_eigenpairs: {name} must be a [count, n, n] torch tensor")
+        _require_doubles(name, t, t.numel(), "device", dev)
+    if not (H.shape == S.shape == X.shape):
+        raise ValueError(f"refine_eigenpairs: shapes differ: H {tuple(H.shape)}, S {tuple(S.shape)}, X {tuple(X.shape)}")
+    count, n = int(X.shape[0]), int(X.shape[1])
+    lam = torch.empty((count, n), dtype=torch.float64, device=X.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.dclno_refine_eigenpairs(_ptr(H), _ptr(S), _ptr(X), _ptr(lam), n, count, int(nsweeps),
+                                     ctypes.c_void_p(stream))
+    if st != 0:
+        raise DclnoError(st, "dclno_refine_eigenpairs failed")
+    return lam
 
 
 def _ptr(x):

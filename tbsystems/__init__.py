@@ -612,3 +612,33 @@ def synthetic_density_rows(system: System, i0: int, i1: int, out: np.ndarray, se
                 blocks[ons] = np.diag(p)[None, :, :] * scale[brow[sel[ons]], None, None]
             idx = offs[sel][:, None] + np.arange(mi * mj)[None, :]
             out[idx] = blocks.reshape(len(sel), -1)
+
+
+def known_pencils(count: int, n: int, seed: int = 5, cond_s: float = 100.0):
+    """`count` symmetric pencils (H, S) of dimension n whose eigenpairs are known by
+    construction: S = U diag(s) U^T with s geometric over [0.5, 0.5 cond_s], C = U
+    diag(s^-1/2) V (so C^T S C = I), H = S C diag(w) C^T S (so H C = S C diag(w)),
+    eigenvalues w ascending over [-2, 2] (spacing 4/(n-1), each jittered by under a
+    quarter of it, so neighbours are at least half the spacing apart).
+    U, V are orthogonal factors of seeded Gaussian matrices.  Returns H, S, C as
+    [count, n, n] and w as [count, n], all float64."""
+    rng = np.random.default_rng(seed)
+    H = np.empty((count, n, n))
+    S = np.empty((count, n, n))
+    C = np.empty((count, n, n))
+    w = np.empty((count, n))
+    s = np.geomspace(0.5, 0.5 * cond_s, n)
+    step = 4.0 / max(n - 1, 1)
+    for p in range(count):
+        U = np.linalg.qr(rng.standard_normal((n, n)))[0]
+        V = np.linalg.qr(rng.standard_normal((n, n)))[0]
+        Sp = (U * s) @ U.T
+        Cp = (U / np.sqrt(s)) @ V
+        wp = np.linspace(-2.0, 2.0, n) + 0.25 * step * rng.uniform(-1.0, 1.0, n) if n > 1 else np.zeros(1)
+        SC = Sp @ Cp
+        Hp = (SC * wp) @ SC.T
+        H[p] = 0.5 * (Hp + Hp.T)
+        S[p] = 0.5 * (Sp + Sp.T)
+        C[p] = Cp
+        w[p] = wp
+    return H, S, C, w

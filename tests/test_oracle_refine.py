@@ -17,18 +17,10 @@ scipy_linalg = pytest.importorskip("scipy.linalg")
 
 
 def _pencil(n, seed):
-    """H, S with H C = S C diag(w), C^T S C = I by construction: S = U diag(s) U^T
-    (cond 1e2), C = U diag(s^-1/2) V, H = S C diag(w) C^T S, eigenvalues w spaced by
-    at least 0.05."""
-    rng = np.random.default_rng(seed)
-    U = np.linalg.qr(rng.standard_normal((n, n)))[0]
-    V = np.linalg.qr(rng.standard_normal((n, n)))[0]
-    s = np.geomspace(0.5, 50.0, n)
-    S = (U * s) @ U.T
-    C = (U / np.sqrt(s)) @ V
-    w = np.sort(np.linspace(-2.0, 2.0, n) + 0.01 * rng.uniform(-1, 1, n))
-    H = S @ C @ np.diag(w) @ C.T @ S
-    return 0.5 * (H + H.T), 0.5 * (S + S.T), w, C
+    """One pencil with known eigenpairs (tbsystems.known_pencils: cond(S) = 100,
+    eigenvalues over [-2, 2] at least half their spacing apart)."""
+    H, S, C, w = T.known_pencils(1, n, seed=seed)
+    return H[0], S[0], w[0], C[0]
 
 
 def test_refinement_squares_the_error():
