@@ -750,6 +750,7 @@ def run_ours(args):
 
     refinement = None
     if world == 1 and not args.no_refine:
+        torch.cuda.empty_cache()  # the library allocates the sweeps' workspace itself
         refinement = measure_refinement(dfma)
 
     cpu = None
