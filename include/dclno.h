@@ -431,7 +431,8 @@ dclno_status dclno_step(dclno_ctx *ctx, const double *rho_in, double *rho_out,
  * H, S: device [count][n][n] (row-major, symmetric, S positive definite); X: device
  * [count][n][n] (in/out, column mu the approximate eigenvector of eigenvalue mu);
  * lam_out: device [count][n], the eigenvalue estimates of the last sweep (from that
- * sweep's input X).  All FP64, contiguous, on the current device.  Costs 10 n^3
+ * sweep's input X).  All FP64, contiguous, on the current device; X and lam_out
+ * must not overlap each other, H or S.  Costs 10 n^3
  * FP64 flops per pencil and sweep; allocates a workspace of 3 count n^2 + count
  * doubles for the call and synchronises `cuda_stream` (NULL = legacy default
  * stream) before returning.  Errors: DCLNO_ERR_ARG (NULL pointers, n, count or
