@@ -183,3 +183,19 @@ def test_streamed_rows_match_full_build():
             np.testing.assert_array_equal(sh1, sh2)
             np.testing.assert_allclose(s1, s2, rtol=1e-14, atol=0)
             np.testing.assert_allclose(h1, h2, rtol=1e-14, atol=0)
+
+
+def test_known_pencils_hold_their_eigenpairs():
+    """The refinement tests' pencils: H C = S C diag(w), C^T S C = I, S symmetric
+    with the stated conditioning, eigenvalues ascending at least half their spacing
+    apart; seeded (the same seed gives the same pencils)."""
+    H, S, C, w = T.known_pencils(2, 33, seed=7)
+    H2, _, _, _ = T.known_pencils(2, 33, seed=7)
+    assert np.array_equal(H, H2)
+    for p in range(2):
+        assert np.max(np.abs(H[p] @ C[p] - S[p] @ C[p] * w[p])) <= 1e-13
+        assert np.max(np.abs(C[p].T @ S[p] @ C[p] - np.eye(33))) <= 1e-13
+        assert np.array_equal(S[p], S[p].T) and np.array_equal(H[p], H[p].T)
+        ev = np.linalg.eigvalsh(S[p])
+        assert abs(ev[-1] / ev[0] - 100.0) <= 1e-8
+        assert np.min(np.diff(w[p])) >= 0.5 * 4.0 / 32
